@@ -1,0 +1,70 @@
+// Kernel parameter blocks shared by the host launchers and the kernels.  They
+// are passed by value (__grid_constant__), so every constant a kernel needs
+// sits in the constant bank and warp-uniform reads of it are broadcasts.
+#pragma once
+
+#include <cstdint>
+
+namespace pl {
+
+constexpr int kMaxL = 96;                 // limbs of n for the largest key (3072-bit)
+constexpr int kMaxLh = kMaxL / 2;         // limbs of p, q
+constexpr int kMaxDigits = 3072 / 2 + 1;  // exponent windows at the smallest window (w = 2)
+
+// Device status word bits (OR-ed by kernels, read by paillier_sync)
+constexpr int kStatusBadBin = 1;       // bin >= K
+constexpr int kStatusBadNode = 2;      // node >= num_nodes
+constexpr int kStatusRange = 4;        // plaintext does not fit the output type
+constexpr int kStatusEncode = 8;       // value outside the encodable range
+constexpr int kStatusTimeout = 16;     // a bounded wait ran out
+constexpr int kStatusCapacity = 32;    // a work list was larger than its buffer
+
+// One half of the key holder's CRT split: arithmetic mod N = p^2 (or q^2),
+// L limbs, R = 2^(32 L).
+struct HalfConst {
+  uint32_t N[kMaxL];    // p^2
+  uint32_t R1[kMaxL];   // R mod N (Montgomery one)
+  uint32_t R2[kMaxL];   // R^2 mod N
+  uint32_t R3[kMaxL];   // R^3 mod N (reduces a 2L-limb value into Montgomery form)
+  uint32_t nR[kMaxL];   // n R mod N (so that mont(m, nR) = m n mod N)
+  uint32_t np;          // -N^-1 mod 2^32
+  uint32_t pad[3];
+};
+
+// Batched fixed-window modular exponentiation over both halves.
+struct ModexpParams {
+  HalfConst half[2];
+  uint8_t dig[2][kMaxDigits];  // window digits of the exponent, least significant first
+  int ndig[2];
+  int w;                       // window width in bits
+  int pad;
+};
+
+// Montgomery arithmetic mod n^2 (2L limbs, R = 2^(64 L)).
+struct N2Const {
+  uint32_t N[2 * kMaxL];
+  uint32_t R2[2 * kMaxL];   // R^2 mod n^2
+  uint32_t np;
+  uint32_t pad[3];
+};
+
+// Single-thread finishing step of encrypt (CRT recombination mod n^2).
+struct EncCrtParams {
+  uint32_t p2[kMaxL], q2[kMaxL];
+  uint32_t QinvR[kMaxL];    // (q^2)^-1 R mod p^2
+  uint32_t p2_np;
+  int L;
+};
+
+// Single-thread finishing step of CRT decryption.
+struct DecCrtParams {
+  uint32_t p[kMaxLh], q[kMaxLh];
+  uint32_t pinv[kMaxLh], qinv2k[kMaxLh];  // p^-1, q^-1 mod 2^(32 Lh) (exact division)
+  uint32_t hpR[kMaxLh], hqR[kMaxLh];      // h_p Rh mod p, h_q Rh mod q
+  uint32_t qinvR[kMaxLh];                 // q^-1 Rh mod p
+  uint32_t p_np, q_np;
+  int Lh;
+  int pad;
+};
+
+}  // namespace pl
