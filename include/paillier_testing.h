@@ -1,0 +1,30 @@
+/*
+ * paillier_testing.h -- entry points that expose the library's multi-precision
+ * core on its own, so that tests can check it limb for limb against plain
+ * integer arithmetic.  The paper has no counterpart: they exist for testing.
+ */
+#ifndef PAILLIER_B300_TESTING_H
+#define PAILLIER_B300_TESTING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Montgomery product of the warp-cooperative kernel core:
+ *   d_out[i] = d_a[i] * d_b[i] * 2^(-32 limbs) mod N     (canonical)
+ * for `count` pairs; d_a, d_b, d_out are [count][limbs] uint32 on the device,
+ * h_N is the odd modulus (host, `limbs` limbs, top limb non-zero).
+ * Requires d_a[i] * d_b[i] < N * 2^(32 limbs) (e.g. both < N).
+ * (limbs, lanes) must be one of the compiled pairs: (32,2) (32,4) (64,2)
+ * (64,4) (64,8) (96,4) (96,8) (128,4) (128,8) (192,8) (192,16). */
+int paillier_test_mont_mul(int limbs, int lanes, const uint32_t* h_N, const uint32_t* d_a,
+                           const uint32_t* d_b, size_t count, uint32_t* d_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAILLIER_B300_TESTING_H */

@@ -1,0 +1,214 @@
+// C-ABI entry points: argument checks, then the launchers.
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+
+namespace pl {
+
+namespace {
+thread_local std::string g_err;
+std::mutex g_status_mu;
+std::map<int, int*> g_status;
+}  // namespace
+
+void set_error(const std::string& msg) { g_err = msg; }
+void clear_error() { g_err.clear(); }
+pl_status fail(pl_status code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+pl_status cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? PL_ENOMEM : PL_ECUDA;
+}
+
+int* status_word(int device) {
+  std::lock_guard<std::mutex> lock(g_status_mu);
+  auto it = g_status.find(device);
+  if (it != g_status.end()) return it->second;
+  int* p = nullptr;
+  if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+  if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+  g_status[device] = p;
+  return p;
+}
+
+Scratch::~Scratch() {
+  if (ptr) {
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    cudaDeviceSynchronize();
+    cudaFree(ptr);
+    cudaSetDevice(prev);
+  }
+}
+
+void* Scratch::get(size_t bytes) {
+  if (bytes <= cap && ptr) return ptr;
+  if (ptr) {
+    cudaDeviceSynchronize();
+    cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+  }
+  size_t want = bytes + bytes / 4 + (1 << 20);
+  if (cudaMalloc(&ptr, want) != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+    if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ptr = nullptr;
+      return nullptr;
+    }
+    want = bytes;
+  }
+  cap = want;
+  return ptr;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  }
+  return n;
+}
+
+static int* current_status() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  return status_word(dev);
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace pl
+
+using namespace pl;
+
+extern "C" {
+
+const char* paillier_last_error(void) { return pl::g_err.c_str(); }
+
+pl_status paillier_sync(void* stream, int* device_status) {
+  if (device_status) *device_status = 0;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int* sw = current_status();
+  if (!sw) return fail(PL_ECUDA, "status word unavailable");
+  int v = 0;
+  e = cudaMemcpy(&v, sw, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
+  if (v) {
+    e = cudaMemset(sw, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+  }
+  if (device_status) *device_status = v;
+  if (v & kStatusTimeout) return fail(PL_ETIMEDOUT, "a bounded device wait ran out");
+  if (v & kStatusRange) return fail(PL_ERANGE, "a decrypted value does not fit 64 bits");
+  if (v & (kStatusBadBin | kStatusBadNode | kStatusEncode | kStatusCapacity)) {
+    std::string m = "device reported bad input:";
+    if (v & kStatusBadBin) m += " bin >= K;";
+    if (v & kStatusBadNode) m += " node >= num_nodes;";
+    if (v & kStatusEncode) m += " value outside [-1, 2^15];";
+    if (v & kStatusCapacity) m += " work list over capacity;";
+    return fail(PL_EDEVICE, m);
+  }
+  return PL_OK;
+}
+
+pl_status paillier_encode(const float* d_v, size_t count, uint64_t* d_m, void* stream) {
+  clear_error();
+  if (count && (!d_v || !d_m)) return fail(PL_EINVAL, "NULL buffer");
+  int* st = current_status();
+  if (!st) return fail(PL_ECUDA, "status word unavailable");
+  return launch_encode(d_v, count, d_m, st, static_cast<cudaStream_t>(stream));
+}
+
+pl_status paillier_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t count, double* d_out, void* stream) {
+  clear_error();
+  if (count && (!d_s || !d_cnt || !d_out)) return fail(PL_EINVAL, "NULL buffer");
+  return launch_decode(d_s, d_cnt, count, d_out, static_cast<cudaStream_t>(stream));
+}
+
+pl_status paillier_encrypt(const pl_key* key, const uint64_t* d_m, const uint32_t* d_r, size_t count,
+                           uint32_t* d_ct, void* stream) {
+  clear_error();
+  if (!key) return fail(PL_EINVAL, "key is NULL");
+  if (!key->priv) return fail(PL_EINVAL, "encryption here needs the private key (CRT split of r^n)");
+  if (count == 0) return PL_OK;
+  if (!d_m || !d_r || !d_ct) return fail(PL_EINVAL, "NULL buffer");
+  if (!aligned16(d_r) || !aligned16(d_ct)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
+  if (count > (size_t)1 << 30) return fail(PL_EINVAL, "count too large");
+  if (!current_status()) return fail(PL_ECUDA, "no usable CUDA device");
+  return launch_encrypt(const_cast<pl_key*>(key), d_m, d_r, count, d_ct, static_cast<cudaStream_t>(stream));
+}
+
+pl_status paillier_ct_prepare(const pl_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_ctm,
+                              void* stream) {
+  clear_error();
+  if (!key) return fail(PL_EINVAL, "key is NULL");
+  if (count == 0) return PL_OK;
+  if (!d_ct || !d_ctm) return fail(PL_EINVAL, "NULL buffer");
+  if (!aligned16(d_ct) || !aligned16(d_ctm)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
+  if (!current_status()) return fail(PL_ECUDA, "no usable CUDA device");
+  return launch_ct_prepare(const_cast<pl_key*>(key), d_ct, count, d_ctm, static_cast<cudaStream_t>(stream));
+}
+
+static pl_status hist_common(const pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t* d_bins, int F,
+                             int K, const int32_t* d_node, int num_nodes, uint32_t* d_hist, int32_t* d_count,
+                             void* stream, bool per_node) {
+  clear_error();
+  if (!key) return fail(PL_EINVAL, "key is NULL");
+  if (F < 1 || K < 1 || K > 256 || num_nodes < 1) return fail(PL_EINVAL, "need F >= 1, 1 <= K <= 256, num_nodes >= 1");
+  if ((long long)num_nodes * K > (1ll << 20)) return fail(PL_EINVAL, "num_nodes * K must be <= 2^20");
+  if ((long long)F * num_nodes * K > (1ll << 28)) return fail(PL_EINVAL, "F * num_nodes * K too large");
+  if (M > (size_t)1 << 30) return fail(PL_EINVAL, "M too large");
+  if (!d_hist) return fail(PL_EINVAL, "NULL histogram buffer");
+  if (M && (!d_ctm || !d_bins || !d_node)) return fail(PL_EINVAL, "NULL input buffer");
+  if (!aligned16(d_hist) || (d_ctm && !aligned16(d_ctm))) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
+  int* st = current_status();
+  if (!st) return fail(PL_ECUDA, "no usable CUDA device");
+  return launch_hist(const_cast<pl_key*>(key), d_ctm, M, d_bins, F, K, d_node, num_nodes, d_hist, d_count,
+                     per_node, st, static_cast<cudaStream_t>(stream));
+}
+
+pl_status paillier_hist_aggregate(const pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t* d_bins, int F,
+                                  int K, const int32_t* d_node, int num_nodes, uint32_t* d_hist, int32_t* d_count,
+                                  void* stream) {
+  return hist_common(key, d_ctm, M, d_bins, F, K, d_node, num_nodes, d_hist, d_count, stream, false);
+}
+
+pl_status paillier_hist_aggregate_per_node(const pl_key* key, const uint32_t* d_ctm, size_t M,
+                                           const uint8_t* d_bins, int F, int K, const int32_t* d_node,
+                                           int num_nodes, uint32_t* d_hist, int32_t* d_count, void* stream) {
+  return hist_common(key, d_ctm, M, d_bins, F, K, d_node, num_nodes, d_hist, d_count, stream, true);
+}
+
+static pl_status decrypt_common(const pl_key* key, const uint32_t* d_ct, size_t count, void* d_m, bool u64,
+                                void* stream) {
+  clear_error();
+  if (!key) return fail(PL_EINVAL, "key is NULL");
+  if (!key->priv) return fail(PL_EINVAL, "decryption needs the private key");
+  if (count == 0) return PL_OK;
+  if (!d_ct || !d_m) return fail(PL_EINVAL, "NULL buffer");
+  if (!aligned16(d_ct) || !aligned16(d_m)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
+  if (count > (size_t)1 << 30) return fail(PL_EINVAL, "count too large");
+  int* st = current_status();
+  if (!st) return fail(PL_ECUDA, "no usable CUDA device");
+  return launch_decrypt(const_cast<pl_key*>(key), d_ct, count, d_m, u64, st, static_cast<cudaStream_t>(stream));
+}
+
+pl_status paillier_decrypt(const pl_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_m, void* stream) {
+  return decrypt_common(key, d_ct, count, d_m, false, stream);
+}
+
+pl_status paillier_decrypt_u64(const pl_key* key, const uint32_t* d_ct, size_t count, uint64_t* d_m, void* stream) {
+  return decrypt_common(key, d_ct, count, d_m, true, stream);
+}
+
+}  // extern "C"

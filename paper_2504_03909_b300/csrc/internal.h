@@ -1,0 +1,104 @@
+// Library-internal declarations shared by the host translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/paillier.h"
+#include "hostmp.h"
+#include "kparams.h"
+
+namespace pl {
+
+// ---- errors ---------------------------------------------------------------
+void set_error(const std::string& msg);
+void clear_error();
+pl_status fail(pl_status code, const std::string& msg);
+pl_status cuda_fail(cudaError_t e, const char* what);
+
+#define PL_CUDA_TRY(call)                                   \
+  do {                                                      \
+    cudaError_t _e = (call);                                \
+    if (_e != cudaSuccess) return ::pl::cuda_fail(_e, #call); \
+  } while (0)
+
+// ---- device status word (one per device, allocated on first use) ---------
+int* status_word(int device);
+
+// ---- scratch: one device buffer per key and device, grown on demand -------
+struct Scratch {
+  int device = -1;
+  void* ptr = nullptr;
+  size_t cap = 0;
+  ~Scratch();
+  // returns a buffer of at least `bytes` (reallocates, synchronising the
+  // device, when it is too small); nullptr on failure
+  void* get(size_t bytes);
+};
+
+// bump allocation inside one scratch request
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  }
+};
+
+// ---- launch configuration (set by the autotuner or by the caller) --------
+struct ModexpCfg {
+  int T = 4;  // lanes per instance
+  int w = 5;  // window bits
+};
+struct AggCfg {
+  int T = 8;      // lanes per instance (mod n^2)
+  int tile = 64;  // ciphertexts per work item of the segmented product
+};
+
+}  // namespace pl
+
+// The key object behind the opaque C handle.
+struct pl_key {
+  int n_bits = 0, L = 0, Lh = 0;
+  bool priv = false;
+  plh::Big n, n2, p, q;
+  pl::N2Const n2c{};
+  // private part
+  pl::HalfConst half[2]{};
+  plh::Big e_enc;        // exponent of r: n
+  plh::Big e_dec[2];     // p - 1, q - 1
+  pl::EncCrtParams enc{};
+  pl::DecCrtParams dec{};
+  // launch configuration
+  pl::ModexpCfg enc_cfg, dec_cfg;
+  pl::AggCfg agg_cfg;
+  // per-window exponent digit tables (built on demand)
+  std::map<int, std::unique_ptr<pl::ModexpParams>> enc_params, dec_params;
+  std::mutex mu;
+  // scratch per device
+  std::map<int, std::unique_ptr<pl::Scratch>> scratch;
+
+  const pl::ModexpParams* modexp_params(bool dec, int w);
+  pl::Scratch* scratch_for_current_device();
+};
+
+namespace pl {
+// launchers (kernels translation units)
+pl_status launch_encode(const float* d_v, size_t count, uint64_t* d_m, int* st, cudaStream_t s);
+pl_status launch_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t count, double* d_out, cudaStream_t s);
+pl_status launch_encrypt(pl_key* key, const uint64_t* d_m, const uint32_t* d_r, size_t count, uint32_t* d_ct,
+                         cudaStream_t s);
+pl_status launch_decrypt(pl_key* key, const uint32_t* d_ct, size_t count, void* d_out, bool u64, int* st,
+                         cudaStream_t s);
+pl_status launch_ct_prepare(pl_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_ctm, cudaStream_t s);
+pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t* d_bins, int F, int K,
+                      const int32_t* d_node, int num_nodes, uint32_t* d_hist, int32_t* d_count, bool per_node,
+                      int* st, cudaStream_t s);
+int sm_count();
+}  // namespace pl

@@ -1,0 +1,437 @@
+// Passive-party kernels: the encrypted histogram (Sec. III.B: the encrypted
+// gradients are accumulated by feature bin; Sec. III.C: each "addition" of
+// Paillier ciphertexts is a product mod n^2).
+//
+// Pipeline for one tree level (all nodes at once):
+//   k_hist_count   counts per (feature, node*K + bin)
+//   k_hist_scan    per-feature offsets, and the number of work items (chunks of
+//                  at most `tile` samples) per cell
+//   k_feat_scan    offsets of each feature's chunks in the global work list
+//   k_hist_scatter sample ids grouped by cell (a counting sort)
+//   k_seg_product  persistent: each group of T lanes multiplies the Montgomery
+//                  ciphertexts of one chunk (product of up to `tile` values)
+//   k_combine      per cell: product of its chunk partials, leave Montgomery
+//                  form, write the canonical cell (1 when empty) and the count
+// The product is commutative, so the order in which the scatter places equal
+// keys does not change any output bit.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "mp.cuh"
+
+namespace pl {
+namespace {
+
+constexpr int kBlock = 128;
+constexpr int kScanBlock = 1024;
+
+// key of sample i in feature f, or -1 if skipped; only_node >= 0 restricts to
+// that node (then the key is the bin alone)
+__device__ __forceinline__ int hist_key(int v, int b, int K, int num_nodes, int only_node, int* status) {
+  if (v < 0) return -1;
+  if (v >= num_nodes) { atomicOr(status, kStatusBadNode); return -1; }
+  if (b >= K) { atomicOr(status, kStatusBadBin); return -1; }
+  if (only_node >= 0) return v == only_node ? b : -1;
+  return v * K + b;
+}
+
+__global__ void k_hist_count(const uint8_t* __restrict__ bins, const int32_t* __restrict__ node, size_t M, int K,
+                             int num_nodes, int only_node, int NK, int* __restrict__ cnt, int* status) {
+  const int f = blockIdx.y;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
+    const int key = hist_key(node[i], bins[(size_t)f * M + i], K, num_nodes, only_node, status);
+    if (key >= 0) atomicAdd(&cnt[(size_t)f * NK + key], 1);
+  }
+}
+
+__global__ void k_hist_scatter(const uint8_t* __restrict__ bins, const int32_t* __restrict__ node, size_t M, int K,
+                               int num_nodes, int only_node, int NK, const int* __restrict__ off,
+                               int* __restrict__ cursor, int* __restrict__ idx, int* status) {
+  const int f = blockIdx.y;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
+    const int key = hist_key(node[i], bins[(size_t)f * M + i], K, num_nodes, only_node, status);
+    if (key >= 0) {
+      const int pos = off[(size_t)f * (NK + 1) + key] + atomicAdd(&cursor[(size_t)f * NK + key], 1);
+      idx[(size_t)f * M + pos] = (int)i;
+    }
+  }
+}
+
+// exclusive scan of (a, b) pairs over the block; returns the totals in *ta, *tb
+__device__ void block_scan2(long long& a, long long& b, long long* ta, long long* tb) {
+  __shared__ long long wa[32], wb[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long xa = __shfl_up_sync(kFull, ia, o), xb = __shfl_up_sync(kFull, ib, o);
+    if (lane >= o) { ia += xa; ib += xb; }
+  }
+  if (lane == 31) { wa[wid] = ia; wb[wid] = ib; }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    long long va = lane < nw ? wa[lane] : 0, vb = lane < nw ? wb[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long xa = __shfl_up_sync(kFull, va, o), xb = __shfl_up_sync(kFull, vb, o);
+      if (lane >= o) { va += xa; vb += xb; }
+    }
+    if (lane < nw) { wa[lane] = va; wb[lane] = vb; }
+  }
+  __syncthreads();
+  const long long pa = wid ? wa[wid - 1] : 0, pb = wid ? wb[wid - 1] : 0;
+  *ta = wa[(blockDim.x >> 5) - 1];
+  *tb = wb[(blockDim.x >> 5) - 1];
+  a = pa + ia - a;
+  b = pb + ib - b;
+  __syncthreads();
+}
+
+// one block per feature: off[f][0..NK] (sample offsets), choff[f][0..NK]
+// (chunk offsets within the feature), featch[f] (chunks of the feature)
+__global__ void __launch_bounds__(kScanBlock) k_hist_scan(const int* __restrict__ cnt, int NK, int tile,
+                                                          int* __restrict__ off, int* __restrict__ choff,
+                                                          int* __restrict__ featch) {
+  const int f = blockIdx.x;
+  const int* c = cnt + (size_t)f * NK;
+  const int per = (NK + blockDim.x - 1) / blockDim.x;
+  const int j0 = min(NK, (int)threadIdx.x * per), j1 = min(NK, j0 + per);
+  long long s1 = 0, s2 = 0;
+  for (int j = j0; j < j1; ++j) { s1 += c[j]; s2 += (c[j] + tile - 1) / tile; }
+  long long t1, t2;
+  block_scan2(s1, s2, &t1, &t2);
+  int* o = off + (size_t)f * (NK + 1);
+  int* co = choff + (size_t)f * (NK + 1);
+  for (int j = j0; j < j1; ++j) {
+    o[j] = (int)s1;
+    co[j] = (int)s2;
+    s1 += c[j];
+    s2 += (c[j] + tile - 1) / tile;
+  }
+  if (threadIdx.x == 0) {
+    o[NK] = (int)t1;
+    co[NK] = (int)t2;
+    featch[f] = (int)t2;
+  }
+}
+
+// single block: featoff[0..F] = exclusive scan of featch; featoff[F] = total chunks
+__global__ void __launch_bounds__(kScanBlock) k_feat_scan(const int* __restrict__ featch, int F,
+                                                          int* __restrict__ featoff) {
+  const int per = (F + blockDim.x - 1) / blockDim.x;
+  const int j0 = min(F, (int)threadIdx.x * per), j1 = min(F, j0 + per);
+  long long s = 0, z = 0;
+  for (int j = j0; j < j1; ++j) s += featch[j];
+  long long t, tz;
+  block_scan2(s, z, &t, &tz);
+  for (int j = j0; j < j1; ++j) { featoff[j] = (int)s; s += featch[j]; }
+  if (threadIdx.x == 0) featoff[F] = (int)t;
+}
+
+// last index i in [0, n) with a[i] <= x (a non-decreasing, a[0] <= x)
+__device__ __forceinline__ int last_le(const int* a, int n, int x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// x R mod n^2 for every ciphertext (R^2 staged once per block)
+template <int S, int T>
+__global__ void __launch_bounds__(kBlock) k_to_mont(const __grid_constant__ N2Const P, const uint32_t* __restrict__ ct,
+                                                    size_t count, uint32_t* __restrict__ ctm) {
+  constexpr int NL = S * T;
+  constexpr int IPW = 32 / T;
+  __shared__ uint32_t r2[NL];
+  for (int j = threadIdx.x; j < NL; j += blockDim.x) r2[j] = P.R2[j];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, k = lane % T, gw = lane / T;
+  uint32_t n[S], a[S], t[S];
+  const_slice<S>(n, P.N, k);
+  const size_t nchunk = (count + IPW - 1) / IPW;
+  const size_t warp0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t c = warp0; c < nchunk; c += nwarps) {
+    const size_t i = c * IPW + gw;
+    const bool valid = i < count;
+    const size_t ii = valid ? i : count - 1;
+    load_slice<S>(a, ct + ii * NL, k);
+    mont_mul<S, T>(t, a, r2, 1, n, P.np, k);
+    if (valid) store_slice<S>(ctm + ii * NL, t, k);
+  }
+}
+
+// Segmented product over the work list of chunks.  Item = (chunk, g/h).
+template <int S, int T>
+__global__ void __launch_bounds__(kBlock) k_seg_product(const __grid_constant__ N2Const P,
+                                                        const uint32_t* __restrict__ ctm, size_t M,
+                                                        const int* __restrict__ idx, const int* __restrict__ off,
+                                                        const int* __restrict__ choff,
+                                                        const int* __restrict__ featoff, int F, int NK, int tile,
+                                                        uint32_t* __restrict__ partial) {
+  constexpr int NL = S * T;
+  constexpr int IPW = 32 / T;
+  extern __shared__ uint32_t smem[];
+  const int ipb = blockDim.x / T;
+  const int lane = threadIdx.x & 31, k = lane % T, gw = lane / T, g = threadIdx.x / T;
+  uint32_t* bs = smem + g;
+  const int st = ipb;
+  uint32_t n[S], a[S], t[S];
+  const_slice<S>(n, P.N, k);
+  const uint32_t np = P.np;
+  const long long total = 2ll * featoff[F];
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp0 * IPW; base < total; base += nwarps * IPW) {
+    const long long item = base + gw;
+    const bool valid = item < total;
+    int len = 0;
+    const uint32_t* src = ctm;
+    const int* ids = idx;
+    if (valid) {
+      const int c = (int)(item >> 1), gh = (int)(item & 1);
+      const int f = last_le(featoff, F, c);
+      const int local = c - featoff[f];
+      const int* co = choff + (size_t)f * (NK + 1);
+      const int key = last_le(co, NK, local);
+      const int* o = off + (size_t)f * (NK + 1);
+      const int j0 = o[key] + (local - co[key]) * tile;
+      len = min(tile, o[key + 1] - j0);
+      src = ctm + (size_t)gh * M * NL;
+      ids = idx + (size_t)f * M + j0;
+    }
+    const int maxlen = __reduce_max_sync(kFull, len);
+    if (len > 0) load_slice<S>(a, src + (size_t)ids[0] * NL, k);
+    for (int j = 1; j < maxlen; ++j) {
+      const bool act = j < len;
+      const unsigned mask = __ballot_sync(kFull, act);
+      if (act) {
+        load_slice<S>(t, src + (size_t)ids[j] * NL, k);
+        __syncwarp(mask);
+        stage<S>(bs, st, t, k);
+        __syncwarp(mask);
+        mont_mul<S, T>(t, a, bs, st, n, np, k, mask);
+#pragma unroll
+        for (int q = 0; q < S; ++q) a[q] = t[q];
+      }
+      __syncwarp();
+    }
+    if (valid && len > 0) store_slice<S>(partial + (size_t)item * NL, a, k);
+  }
+}
+
+// Per cell and g/h: product of the chunk partials, out of Montgomery form.
+template <int S, int T>
+__global__ void __launch_bounds__(kBlock) k_combine(const __grid_constant__ N2Const P,
+                                                    const uint32_t* __restrict__ partial,
+                                                    const int* __restrict__ off, const int* __restrict__ choff,
+                                                    const int* __restrict__ featoff, int F, int NK, int K,
+                                                    int only_node, uint32_t* __restrict__ hist,
+                                                    int32_t* __restrict__ count_out) {
+  constexpr int NL = S * T;
+  constexpr int IPW = 32 / T;
+  extern __shared__ uint32_t smem[];
+  const int ipb = blockDim.x / T;
+  const int lane = threadIdx.x & 31, k = lane % T, gw = lane / T, g = threadIdx.x / T;
+  uint32_t* bs = smem + g;
+  const int st = ipb;
+  uint32_t n[S], a[S], t[S];
+  const_slice<S>(n, P.N, k);
+  const uint32_t np = P.np;
+  const long long total = 2ll * F * NK;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp0 * IPW; base < total; base += nwarps * IPW) {
+    const long long item = base + gw;
+    const bool valid = item < total;
+    int nch = 0, first = 0, gh = 0, f = 0, key = 0;
+    if (valid) {
+      const long long cell = item >> 1;
+      gh = (int)(item & 1);
+      f = (int)(cell / NK);
+      key = (int)(cell % NK);
+      const int* co = choff + (size_t)f * (NK + 1);
+      nch = co[key + 1] - co[key];
+      first = featoff[f] + co[key];
+    }
+    const int maxn = __reduce_max_sync(kFull, nch);
+    if (nch > 0) load_slice_rw<S>(a, partial + ((size_t)first * 2 + gh) * NL, k);
+    for (int j = 1; j < maxn; ++j) {
+      const bool act = j < nch;
+      const unsigned mask = __ballot_sync(kFull, act);
+      if (act) {
+        load_slice_rw<S>(t, partial + ((size_t)(first + j) * 2 + gh) * NL, k);
+        __syncwarp(mask);
+        stage<S>(bs, st, t, k);
+        __syncwarp(mask);
+        mont_mul<S, T>(t, a, bs, st, n, np, k, mask);
+#pragma unroll
+        for (int q = 0; q < S; ++q) a[q] = t[q];
+      }
+      __syncwarp();
+    }
+    // leave Montgomery form (times 1); an empty cell is the ciphertext 1
+    {
+      const bool act = nch > 0;
+      const unsigned mask = __ballot_sync(kFull, act);
+      if (act) {
+#pragma unroll
+        for (int q = 0; q < S; ++q) bs[(k * S + q) * st] = (k * S + q == 0) ? 1u : 0u;
+        __syncwarp(mask);
+        mont_mul<S, T>(t, a, bs, st, n, np, k, mask);
+      } else {
+#pragma unroll
+        for (int q = 0; q < S; ++q) t[q] = (k * S + q == 0) ? 1u : 0u;
+      }
+      __syncwarp();
+    }
+    if (valid) {
+      const int v = only_node >= 0 ? only_node : key / K;
+      const int b = only_node >= 0 ? key : key % K;
+      const size_t cellrow = ((size_t)v * F + f) * K + b;
+      store_slice<S>(hist + (cellrow * 2 + gh) * NL, t, k);
+      if (count_out && gh == 0 && k == 0) {
+        const int* o = off + (size_t)f * (NK + 1);
+        count_out[cellrow] = o[key + 1] - o[key];
+      }
+    }
+  }
+}
+
+template <int S, int T>
+int occupancy_grid(const void* fn, size_t smem) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kBlock, smem) != cudaSuccess || b < 1) b = 1;
+  return b * sm_count();
+}
+
+struct HistBufs {
+  int* cnt;
+  int* off;
+  int* choff;
+  int* featch;
+  int* featoff;
+  int* idx;
+  uint32_t* partial;
+};
+
+template <int S, int T>
+pl_status run_prepare(const N2Const& P, const uint32_t* ct, size_t count, uint32_t* ctm, cudaStream_t s) {
+  static int grid = 0;
+  if (!grid) grid = occupancy_grid<S, T>((const void*)k_to_mont<S, T>, 0);
+  const size_t ipw = 32 / T;
+  const size_t blocks_needed = ((count + ipw - 1) / ipw + (kBlock / 32) - 1) / (kBlock / 32);
+  const int g = (int)std::min<size_t>((size_t)grid, blocks_needed);
+  k_to_mont<S, T><<<g, kBlock, 0, s>>>(P, ct, count, ctm);
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
+
+template <int S, int T>
+pl_status run_hist_products(const N2Const& P, const uint32_t* ctm, size_t M, const HistBufs& B, int F, int NK, int K,
+                            int tile, int only_node, uint32_t* hist, int32_t* count_out, cudaStream_t s) {
+  const size_t smem = (size_t)S * T * (kBlock / T) * sizeof(uint32_t);
+  static int grid_seg = 0, grid_comb = 0;
+  if (!grid_seg) grid_seg = occupancy_grid<S, T>((const void*)k_seg_product<S, T>, smem);
+  if (!grid_comb) grid_comb = occupancy_grid<S, T>((const void*)k_combine<S, T>, smem);
+  k_seg_product<S, T><<<grid_seg, kBlock, smem, s>>>(P, ctm, M, B.idx, B.off, B.choff, B.featoff, F, NK, tile,
+                                                     B.partial);
+  PL_CUDA_TRY(cudaGetLastError());
+  const size_t ipw = 32 / T;
+  const size_t items = 2ull * F * NK;
+  const size_t blocks_needed = ((items + ipw - 1) / ipw + (kBlock / 32) - 1) / (kBlock / 32);
+  const int gc = (int)std::min<size_t>((size_t)grid_comb, blocks_needed);
+  k_combine<S, T><<<gc, kBlock, smem, s>>>(P, B.partial, B.off, B.choff, B.featoff, F, NK, K, only_node, hist,
+                                           count_out);
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
+
+#define PL_N2_CASES(X) X(64, 4) X(64, 8) X(128, 4) X(128, 8) X(192, 8) X(192, 16)
+
+pl_status dispatch_prepare(int NL, int T, const N2Const& P, const uint32_t* ct, size_t count, uint32_t* ctm,
+                           cudaStream_t s) {
+#define PL_CASE(LL, TT) \
+  if (NL == LL && T == TT) return run_prepare<LL / TT, TT>(P, ct, count, ctm, s);
+  PL_N2_CASES(PL_CASE)
+#undef PL_CASE
+  return fail(PL_EINVAL, "no mod n^2 kernel for this (limbs, lanes) pair");
+}
+
+pl_status dispatch_products(int NL, int T, const N2Const& P, const uint32_t* ctm, size_t M, const HistBufs& B, int F,
+                            int NK, int K, int tile, int only_node, uint32_t* hist, int32_t* count_out,
+                            cudaStream_t s) {
+#define PL_CASE(LL, TT)                                                                                   \
+  if (NL == LL && T == TT)                                                                                \
+    return run_hist_products<LL / TT, TT>(P, ctm, M, B, F, NK, K, tile, only_node, hist, count_out, s);
+  PL_N2_CASES(PL_CASE)
+#undef PL_CASE
+  return fail(PL_EINVAL, "no mod n^2 kernel for this (limbs, lanes) pair");
+}
+
+// One group-by + segmented product + combine over the node selection.
+pl_status hist_pass(pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t* d_bins, int F, int K,
+                    const int32_t* d_node, int num_nodes, int only_node, const HistBufs& B, uint32_t* d_hist,
+                    int32_t* d_count, int* st, cudaStream_t s) {
+  const int NK = only_node >= 0 ? K : num_nodes * K;
+  const int tile = key->agg_cfg.tile;
+  PL_CUDA_TRY(cudaMemsetAsync(B.cnt, 0, sizeof(int) * (size_t)F * NK, s));
+  const int gx = (int)std::min<size_t>((M + 255) / 256, 1024);
+  dim3 grid(gx > 0 ? gx : 1, F);
+  k_hist_count<<<grid, 256, 0, s>>>(d_bins, d_node, M, K, num_nodes, only_node, NK, B.cnt, st);
+  PL_CUDA_TRY(cudaGetLastError());
+  k_hist_scan<<<F, kScanBlock, 0, s>>>(B.cnt, NK, tile, B.off, B.choff, B.featch);
+  PL_CUDA_TRY(cudaGetLastError());
+  k_feat_scan<<<1, kScanBlock, 0, s>>>(B.featch, F, B.featoff);
+  PL_CUDA_TRY(cudaGetLastError());
+  PL_CUDA_TRY(cudaMemsetAsync(B.cnt, 0, sizeof(int) * (size_t)F * NK, s));
+  k_hist_scatter<<<grid, 256, 0, s>>>(d_bins, d_node, M, K, num_nodes, only_node, NK, B.off, B.cnt, B.idx, st);
+  PL_CUDA_TRY(cudaGetLastError());
+  return dispatch_products(2 * key->L, key->agg_cfg.T, key->n2c, d_ctm, M, B, F, NK, K, tile, only_node, d_hist,
+                           d_count, s);
+}
+
+}  // namespace
+
+pl_status launch_ct_prepare(pl_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_ctm, cudaStream_t s) {
+  if (count == 0) return PL_OK;
+  return dispatch_prepare(2 * key->L, key->agg_cfg.T, key->n2c, d_ct, count, d_ctm, s);
+}
+
+pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t* d_bins, int F, int K,
+                      const int32_t* d_node, int num_nodes, uint32_t* d_hist, int32_t* d_count, bool per_node,
+                      int* st, cudaStream_t s) {
+  const int NK = per_node ? K : num_nodes * K;
+  const int tile = key->agg_cfg.tile;
+  const size_t NL = 2 * (size_t)key->L;
+  // chunks per feature <= M / tile + (non-empty cells)
+  const size_t max_chunks = (size_t)F * ((M + tile - 1) / tile + std::min<size_t>((size_t)NK, M));
+  Carve cv;
+  const size_t o_cnt = cv.take(sizeof(int) * (size_t)F * NK);
+  const size_t o_off = cv.take(sizeof(int) * (size_t)F * (NK + 1));
+  const size_t o_choff = cv.take(sizeof(int) * (size_t)F * (NK + 1));
+  const size_t o_featch = cv.take(sizeof(int) * (size_t)F);
+  const size_t o_featoff = cv.take(sizeof(int) * ((size_t)F + 1));
+  const size_t o_idx = cv.take(sizeof(int) * (size_t)F * (M ? M : 1));
+  const size_t o_part = cv.take(sizeof(uint32_t) * NL * 2 * (max_chunks ? max_chunks : 1));
+  Scratch* sc = key->scratch_for_current_device();
+  if (!sc) return fail(PL_ECUDA, "no current device");
+  char* base = static_cast<char*>(sc->get(cv.off));
+  if (!base) return fail(PL_ENOMEM, "scratch allocation failed");
+  HistBufs B{reinterpret_cast<int*>(base + o_cnt),     reinterpret_cast<int*>(base + o_off),
+              reinterpret_cast<int*>(base + o_choff),  reinterpret_cast<int*>(base + o_featch),
+              reinterpret_cast<int*>(base + o_featoff), reinterpret_cast<int*>(base + o_idx),
+              reinterpret_cast<uint32_t*>(base + o_part)};
+  if (!per_node)
+    return hist_pass(key, d_ctm, M, d_bins, F, K, d_node, num_nodes, -1, B, d_hist, d_count, st, s);
+  for (int v = 0; v < num_nodes; ++v) {
+    pl_status rc = hist_pass(key, d_ctm, M, d_bins, F, K, d_node, num_nodes, v, B, d_hist, d_count, st, s);
+    if (rc) return rc;
+  }
+  return PL_OK;
+}
+
+}  // namespace pl

@@ -1,0 +1,378 @@
+// Key-holder kernels: fixed-point encode/decode, encryption and CRT
+// decryption (Sec. III.B: the active party encrypts g/h and decrypts the
+// returned histograms; Sec. III.C: one single-number encryption per g and h).
+//
+// Both encryption and decryption are dominated by one batched fixed-window
+// exponentiation in the two CRT halves (mod p^2 and mod q^2, L limbs each),
+// run by k_modexp with T lanes per instance.  The once-per-item steps around
+// it (CRT recombination, exact division L_p) are one thread per item.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "mp.cuh"
+
+namespace pl {
+namespace {
+
+constexpr int kBlock = 128;
+
+// m = rint(v 2^24) + 2^24, v in [-1, 2^15] (x 2^24 is exact in float32).
+__global__ void k_encode(const float* __restrict__ v, size_t count, uint64_t* __restrict__ m, int* status) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const float x = v[i];
+    if (x >= -1.0f && x <= 32768.0f) {
+      m[i] = (uint64_t)(__float2ll_rn(x * 16777216.0f) + (1ll << 24));
+    } else {
+      m[i] = 0;
+      atomicOr(status, kStatusEncode);
+    }
+  }
+}
+
+__global__ void k_decode(const uint64_t* __restrict__ s, const int32_t* __restrict__ cnt, size_t count,
+                         double* __restrict__ out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const int64_t d = (int64_t)(s[i] - ((uint64_t)(uint32_t)cnt[i] << 24));
+    out[i] = (double)d * (1.0 / 16777216.0);
+  }
+}
+
+// Batched exponentiation in the CRT halves.  Instance (h, i): half h (p^2 or
+// q^2), item i.  A warp takes 32/T consecutive items of one half, so the
+// exponent digits are warp-uniform.
+//   ENC: y[h][i] = (1 + m_i n) r_i^n mod N_h      (in = r [count][L])
+//   DEC: y[h][i] = c_i^(x_h - 1) mod N_h          (in = c [count][2L])
+// Every value is canonical.  tbl: per-group window table, 2^w entries of L
+// limbs for each group of the grid.
+template <int S, int T, bool DEC>
+__global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ ModexpParams P,
+                                                   const uint32_t* __restrict__ in, const uint64_t* __restrict__ msg,
+                                                   uint32_t* __restrict__ out, uint32_t* __restrict__ tbl,
+                                                   size_t count) {
+  constexpr int NL = S * T;
+  constexpr int IPW = 32 / T;
+  extern __shared__ uint32_t smem[];
+  const int ipb = blockDim.x / T;
+  const int lane = threadIdx.x & 31;
+  const int k = lane % T;
+  const int gw = lane / T;
+  const int g = threadIdx.x / T;
+  uint32_t* bs = smem + g;
+  const int st = ipb;
+  const int w = P.w;
+  const int nent = 1 << w;
+  uint32_t* mytbl = tbl + ((size_t)blockIdx.x * ipb + g) * (size_t)nent * NL;
+  const size_t nchunk = (count + IPW - 1) / IPW;
+  const size_t nitems = 2 * nchunk;
+  const size_t warp0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+
+  for (size_t item = warp0; item < nitems; item += nwarps) {
+    const int h = (int)(item & 1);
+    const size_t i = (item >> 1) * IPW + gw;
+    const bool valid = i < count;
+    const size_t ii = valid ? i : count - 1;
+    const HalfConst& H = P.half[h];
+    uint32_t n[S], a[S], t[S];
+    const_slice<S>(n, H.N, k);
+    const uint32_t np = H.np;
+    uint32_t* yrow = out + ((size_t)h * count + ii) * NL;
+
+    if constexpr (!DEC) {
+      // post-factor (1 + m n) mod N = mont(nR, m) + 1, parked in the output row
+      const uint64_t m = msg[ii];
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const int idx = k * S + j;
+        bs[idx * st] = idx == 0 ? (uint32_t)m : (idx == 1 ? (uint32_t)(m >> 32) : 0u);
+      }
+      __syncwarp();
+      const_slice<S>(a, H.nR, k);
+      mont_mul<S, T>(t, a, bs, st, n, np, k);
+      normalize<S, T>(t, 0u, 1u, n, k, kFull);
+      if (valid) store_slice<S>(yrow, t, k);
+      // base r in Montgomery form: mont(r, R^2) = r R mod N (valid for any r < R)
+      load_slice<S>(a, in + ii * NL, k);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < S; ++j) bs[(k * S + j) * st] = H.R2[k * S + j];
+      __syncwarp();
+      mont_mul<S, T>(t, a, bs, st, n, np, k);
+    } else {
+      // c = c_lo + c_hi R: Montgomery form c R = mont(c_lo, R^2) + mont(c_hi, R^3)
+      load_slice<S>(a, in + ii * 2 * NL, k);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < S; ++j) bs[(k * S + j) * st] = H.R2[k * S + j];
+      __syncwarp();
+      mont_mul<S, T>(t, a, bs, st, n, np, k);
+      store_slice<S>(mytbl, t, k);
+      load_slice<S>(a, in + ii * 2 * NL + NL, k);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < S; ++j) bs[(k * S + j) * st] = H.R3[k * S + j];
+      __syncwarp();
+      mont_mul<S, T>(t, a, bs, st, n, np, k);
+      load_slice_rw<S>(a, mytbl, k);
+      add_cc(t[0], a[0]);
+#pragma unroll
+      for (int j = 1; j < S; ++j) addc_cc(t[j], a[j]);
+      const uint32_t c = carry_out();
+      normalize<S, T>(t, c, 0u, n, k, kFull);
+    }
+
+    // window table: tbl[e] = x^e in Montgomery form, e < 2^w
+    const_slice<S>(a, H.R1, k);
+    store_slice<S>(mytbl, a, k);
+    store_slice<S>(mytbl + NL, t, k);
+    __syncwarp();
+    stage<S>(bs, st, t, k);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < S; ++j) a[j] = t[j];
+    for (int e = 2; e < nent; ++e) {
+      mont_mul<S, T>(t, a, bs, st, n, np, k);
+      store_slice<S>(mytbl + e * NL, t, k);
+#pragma unroll
+      for (int j = 0; j < S; ++j) a[j] = t[j];
+    }
+
+    // left-to-right fixed-window exponentiation
+    const int nd = P.ndig[h];
+    const uint8_t* dg = P.dig[h];
+    load_slice_rw<S>(a, mytbl + (size_t)dg[nd - 1] * NL, k);
+    for (int di = nd - 2; di >= 0; --di) {
+      const int d = dg[di];
+      for (int s = 0; s <= w; ++s) {
+        __syncwarp();
+        if (s < w) {
+          stage<S>(bs, st, a, k);
+        } else {
+          load_slice_rw<S>(t, mytbl + (size_t)d * NL, k);
+          stage<S>(bs, st, t, k);
+        }
+        __syncwarp();
+        mont_mul<S, T>(t, a, bs, st, n, np, k);
+#pragma unroll
+        for (int j = 0; j < S; ++j) a[j] = t[j];
+      }
+    }
+
+    // leave Montgomery form: times the post factor (ENC) or times 1 (DEC)
+    __syncwarp();
+    if constexpr (!DEC) {
+      load_slice_rw<S>(t, yrow, k);
+      stage<S>(bs, st, t, k);
+    } else {
+#pragma unroll
+      for (int j = 0; j < S; ++j) bs[(k * S + j) * st] = (k * S + j == 0) ? 1u : 0u;
+    }
+    __syncwarp();
+    mont_mul<S, T>(t, a, bs, st, n, np, k);
+    if (valid) store_slice<S>(yrow, t, k);
+  }
+}
+
+// c = y_q + q^2 ((y_p - y_q) (q^2)^-1 mod p^2), one thread per ciphertext.
+__global__ void __launch_bounds__(kBlock) k_enc_crt(const __grid_constant__ EncCrtParams P,
+                                                    const uint32_t* __restrict__ y, size_t count,
+                                                    uint32_t* __restrict__ ct) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int L = P.L;
+  const uint32_t* yp = y + i * L;
+  const uint32_t* yq = y + (count + i) * L;
+  uint32_t d[kMaxL], u[kMaxL], c[2 * kMaxL];
+  for (int j = 0; j < L; ++j) d[j] = yp[j];
+  if (sub_1t(d, yq, L)) {  // y_q may exceed y_p (and p^2): add p^2 until non-negative
+    if (!add_1t(d, P.p2, L)) add_1t(d, P.p2, L);
+  }
+  mm_1t(u, d, P.QinvR, P.p2, P.p2_np, L);
+  mul_1t(c, P.q2, L, u, L);
+  uint64_t cy = 0;
+  for (int j = 0; j < 2 * L; ++j) {
+    cy += (uint64_t)c[j] + (j < L ? yq[j] : 0u);
+    c[j] = (uint32_t)cy;
+    cy >>= 32;
+  }
+  uint32_t* o = ct + i * 2 * L;
+  for (int j = 0; j < 2 * L; j += 4) *reinterpret_cast<uint4*>(o + j) = make_uint4(c[j], c[j + 1], c[j + 2], c[j + 3]);
+}
+
+// m_p = L_p(y_p) h_p mod p (L_p an exact division done as a product with
+// p^-1 mod 2^(32 Lh)), m_q likewise, m = m_q + q ((m_p - m_q) q^-1 mod p).
+template <bool U64>
+__global__ void __launch_bounds__(kBlock) k_dec_crt(const __grid_constant__ DecCrtParams P,
+                                                    const uint32_t* __restrict__ y, size_t count, int L,
+                                                    void* __restrict__ outp, int* status) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int Lh = P.Lh;
+  uint32_t x[kMaxLh], lx[kMaxLh], mp[kMaxLh], mq[kMaxLh], u[kMaxLh], m[kMaxL];
+  for (int half = 0; half < 2; ++half) {
+    const uint32_t* yr = y + ((size_t)half * count + i) * L;
+    for (int j = 0; j < Lh; ++j) x[j] = yr[j];
+    // x - 1 mod 2^(32 Lh)
+    for (int j = 0; j < Lh; ++j) {
+      const uint32_t old = x[j];
+      x[j] = old - 1u;
+      if (old != 0) break;
+    }
+    mul_lo_1t(lx, x, half ? P.qinv2k : P.pinv, Lh);
+    if (half == 0)
+      mm_1t(mp, lx, P.hpR, P.p, P.p_np, Lh);
+    else
+      mm_1t(mq, lx, P.hqR, P.q, P.q_np, Lh);
+  }
+  // (m_p - m_q) mod p, with m_q < q < 2p
+  for (int j = 0; j < Lh; ++j) x[j] = mp[j];
+  if (sub_1t(x, mq, Lh)) {
+    if (!add_1t(x, P.p, Lh)) add_1t(x, P.p, Lh);
+  }
+  mm_1t(u, x, P.qinvR, P.p, P.p_np, Lh);
+  mul_1t(m, P.q, Lh, u, Lh);
+  uint64_t cy = 0;
+  for (int j = 0; j < L; ++j) {
+    cy += (uint64_t)m[j] + (j < Lh ? mq[j] : 0u);
+    m[j] = (uint32_t)cy;
+    cy >>= 32;
+  }
+  if constexpr (U64) {
+    uint32_t hi = 0;
+    for (int j = 2; j < L; ++j) hi |= m[j];
+    uint64_t* o = reinterpret_cast<uint64_t*>(outp);
+    if (hi) {
+      o[i] = ~0ull;
+      atomicOr(status, kStatusRange);
+    } else {
+      o[i] = (uint64_t)m[0] | ((uint64_t)m[1] << 32);
+    }
+  } else {
+    uint32_t* o = reinterpret_cast<uint32_t*>(outp) + i * L;
+    for (int j = 0; j < L; j += 4) *reinterpret_cast<uint4*>(o + j) = make_uint4(m[j], m[j + 1], m[j + 2], m[j + 3]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+
+template <int S, int T, bool DEC>
+pl_status run_modexp(const ModexpParams* P, const uint32_t* in, const uint64_t* msg, uint32_t* y, uint32_t* tbl,
+                     int grid, size_t count, cudaStream_t s) {
+  const int ipb = kBlock / T;
+  const size_t smem = (size_t)S * T * ipb * sizeof(uint32_t);
+  k_modexp<S, T, DEC><<<grid, kBlock, smem, s>>>(*P, in, msg, y, tbl, count);
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
+
+template <int S, int T, bool DEC>
+int modexp_grid() {
+  static int blocks_per_sm = -1;
+  if (blocks_per_sm < 0) {
+    const int ipb = kBlock / T;
+    const size_t smem = (size_t)S * T * ipb * sizeof(uint32_t);
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_modexp<S, T, DEC>, kBlock, smem) != cudaSuccess || b < 1)
+      b = 1;
+    blocks_per_sm = b;
+  }
+  return blocks_per_sm * sm_count();
+}
+
+// dispatch on (limbs per half L, lanes per instance T)
+template <bool DEC>
+pl_status modexp_dispatch(int L, int T, int* grid_out, bool launch, const ModexpParams* P, const uint32_t* in,
+                          const uint64_t* msg, uint32_t* y, uint32_t* tbl, size_t count, cudaStream_t s) {
+#define PL_CASE(LL, TT)                                                            \
+  if (L == LL && T == TT) {                                                        \
+    if (!launch) { *grid_out = modexp_grid<LL / TT, TT, DEC>(); return PL_OK; }     \
+    return run_modexp<LL / TT, TT, DEC>(P, in, msg, y, tbl, *grid_out, count, s);   \
+  }
+  PL_CASE(32, 2)
+  PL_CASE(32, 4)
+  PL_CASE(64, 2)
+  PL_CASE(64, 4)
+  PL_CASE(64, 8)
+  PL_CASE(96, 4)
+  PL_CASE(96, 8)
+#undef PL_CASE
+  return fail(PL_EINVAL, "no exponentiation kernel for this (limbs, lanes) pair");
+}
+
+}  // namespace
+
+pl_status launch_encode(const float* d_v, size_t count, uint64_t* d_m, int* st, cudaStream_t s) {
+  if (count == 0) return PL_OK;
+  const int grid = (int)std::min<size_t>((count + 255) / 256, (size_t)sm_count() * 8);
+  k_encode<<<grid, 256, 0, s>>>(d_v, count, d_m, st);
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
+
+pl_status launch_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t count, double* d_out, cudaStream_t s) {
+  if (count == 0) return PL_OK;
+  const int grid = (int)std::min<size_t>((count + 255) / 256, (size_t)sm_count() * 8);
+  k_decode<<<grid, 256, 0, s>>>(d_s, d_cnt, count, d_out);
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
+
+// Shared by encrypt and decrypt: scratch = y [2][count][L] + window tables.
+template <bool DEC>
+static pl_status modexp_phase(pl_key* key, const ModexpCfg& cfg, const uint32_t* in, const uint64_t* msg,
+                              size_t count, uint32_t** y_out, cudaStream_t s) {
+  const ModexpParams* P = key->modexp_params(DEC, cfg.w);
+  if (!P) return fail(PL_EINVAL, "unsupported window width");
+  const int L = key->L;
+  int grid = 0;
+  pl_status rc = modexp_dispatch<DEC>(L, cfg.T, &grid, false, P, nullptr, nullptr, nullptr, nullptr, 0, s);
+  if (rc) return rc;
+  // no more blocks than items need
+  const size_t ipw = 32 / (size_t)cfg.T;
+  const size_t warps_needed = 2 * ((count + ipw - 1) / ipw);
+  const size_t blocks_needed = (warps_needed + (kBlock / 32) - 1) / (kBlock / 32);
+  if ((size_t)grid > blocks_needed) grid = (int)blocks_needed;
+  const size_t ipb = kBlock / cfg.T;
+  Carve cv;
+  const size_t off_y = cv.take((size_t)2 * count * L * sizeof(uint32_t));
+  const size_t off_t = cv.take((size_t)grid * ipb * ((size_t)1 << cfg.w) * L * sizeof(uint32_t));
+  Scratch* sc = key->scratch_for_current_device();
+  if (!sc) return fail(PL_ECUDA, "no current device");
+  char* base = static_cast<char*>(sc->get(cv.off));
+  if (!base) return fail(PL_ENOMEM, "scratch allocation failed");
+  uint32_t* y = reinterpret_cast<uint32_t*>(base + off_y);
+  uint32_t* tbl = reinterpret_cast<uint32_t*>(base + off_t);
+  rc = modexp_dispatch<DEC>(L, cfg.T, &grid, true, P, in, msg, y, tbl, count, s);
+  *y_out = y;
+  return rc;
+}
+
+pl_status launch_encrypt(pl_key* key, const uint64_t* d_m, const uint32_t* d_r, size_t count, uint32_t* d_ct,
+                         cudaStream_t s) {
+  if (count == 0) return PL_OK;
+  uint32_t* y = nullptr;
+  pl_status rc = modexp_phase<false>(key, key->enc_cfg, d_r, d_m, count, &y, s);
+  if (rc) return rc;
+  k_enc_crt<<<(unsigned)((count + kBlock - 1) / kBlock), kBlock, 0, s>>>(key->enc, y, count, d_ct);
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
+
+pl_status launch_decrypt(pl_key* key, const uint32_t* d_ct, size_t count, void* d_out, bool u64, int* st,
+                         cudaStream_t s) {
+  if (count == 0) return PL_OK;
+  uint32_t* y = nullptr;
+  pl_status rc = modexp_phase<true>(key, key->dec_cfg, d_ct, nullptr, count, &y, s);
+  if (rc) return rc;
+  const unsigned grid = (unsigned)((count + kBlock - 1) / kBlock);
+  if (u64)
+    k_dec_crt<true><<<grid, kBlock, 0, s>>>(key->dec, y, count, key->L, d_out, st);
+  else
+    k_dec_crt<false><<<grid, kBlock, 0, s>>>(key->dec, y, count, key->L, d_out, st);
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
+
+}  // namespace pl

@@ -1,0 +1,99 @@
+"""ctypes binding of the C ABI in ``include/paillier.h`` (argument marshalling only).
+
+The shared library is built in-tree by ``python -m paper_2504_03909_b300.build``.
+Loading fails loudly when it is missing: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpaillier_b300.so")
+HEADER_DIR = os.path.join(os.path.dirname(HERE), "include")
+
+PL_OK, PL_EINVAL, PL_ENOMEM, PL_ECUDA, PL_ERANGE, PL_ETIMEDOUT, PL_EBUSY, PL_EDEVICE = range(8)
+STATUS_NAMES = {0: "PL_OK", 1: "PL_EINVAL", 2: "PL_ENOMEM", 3: "PL_ECUDA", 4: "PL_ERANGE",
+                5: "PL_ETIMEDOUT", 6: "PL_EBUSY", 7: "PL_EDEVICE"}
+
+_u32p = C.c_void_p
+_vp = C.c_void_p
+_sz = C.c_size_t
+_i = C.c_int
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "paillier_keygen": (_i, [_i, C.c_uint64, C.POINTER(C.c_void_p)]),
+    "paillier_key_import": (_i, [_i, _vp, _vp, C.POINTER(C.c_void_p)]),
+    "paillier_key_import_public": (_i, [_i, _vp, C.POINTER(C.c_void_p)]),
+    "paillier_key_export": (_i, [_vp, _vp, _vp, _vp]),
+    "paillier_key_bits": (_i, [_vp]),
+    "paillier_key_is_private": (_i, [_vp]),
+    "paillier_key_free": (None, [_vp]),
+    "paillier_encode": (_i, [_vp, _sz, _vp, _vp]),
+    "paillier_decode": (_i, [_vp, _vp, _sz, _vp, _vp]),
+    "paillier_encrypt": (_i, [_vp, _vp, _vp, _sz, _vp, _vp]),
+    "paillier_ct_prepare": (_i, [_vp, _vp, _sz, _vp, _vp]),
+    "paillier_hist_aggregate": (_i, [_vp, _vp, _sz, _vp, _i, _i, _vp, _i, _vp, _vp, _vp]),
+    "paillier_hist_aggregate_per_node": (_i, [_vp, _vp, _sz, _vp, _i, _i, _vp, _i, _vp, _vp, _vp]),
+    "paillier_decrypt": (_i, [_vp, _vp, _sz, _vp, _vp]),
+    "paillier_decrypt_u64": (_i, [_vp, _vp, _sz, _vp, _vp]),
+    "paillier_sync": (_i, [_vp, C.POINTER(_i)]),
+    "paillier_last_error": (C.c_char_p, []),
+    "paillier_test_mont_mul": (_i, [_i, _i, _vp, _vp, _vp, _sz, _vp, _vp]),
+}
+
+_lib = None
+
+
+class PaillierError(RuntimeError):
+    def __init__(self, code: int, fn: str, msg: str):
+        super().__init__(f"{fn} failed with {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def header_functions() -> list:
+    """Function names declared in include/*.h (for the export check)."""
+    names = []
+    for fn in sorted(os.listdir(HEADER_DIR)):
+        if fn.endswith(".h"):
+            text = open(os.path.join(HEADER_DIR, fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^\s*(?:[A-Za-z_][\w ]*?[\s\*]+)(\w+)\s*\(", text, flags=re.M)
+    return [n for n in names if not n.startswith("PL_") and n not in ("if", "while", "defined")]
+
+
+def lib():
+    """Load the library once (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"native library missing: {LIB_PATH}; run python -m paper_2504_03909_b300.build")
+        l = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(l, name, None)
+            if f is None:
+                continue
+            f.restype = res
+            f.argtypes = args
+        _lib = l
+    return _lib
+
+
+def last_error() -> str:
+    m = lib().paillier_last_error()
+    return m.decode() if m else ""
+
+
+def check(code: int, fn: str):
+    if code != PL_OK:
+        raise PaillierError(code, fn, last_error())
+
+
+def call(fn: str, *args):
+    """Call a status-returning entry point; raise PaillierError on failure."""
+    rc = getattr(lib(), fn)(*args)
+    check(rc, fn)
+    return rc

@@ -1,0 +1,185 @@
+"""Python face of the C ABI, over torch device tensors.
+
+Every function here only checks shapes, takes ``data_ptr()`` and the current
+CUDA stream, and calls the native library; all arithmetic runs in the CUDA
+kernels.  Multi-precision arrays are held in int32 tensors whose bits are the
+uint32 limbs (little-endian limbs, one row per value); uint64 values are held
+in int64 tensors.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import native
+from .native import call, lib
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _ptr(t: torch.Tensor) -> int:
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return t.data_ptr()
+
+
+def _limbs_from_int(x: int, limbs: int) -> np.ndarray:
+    return np.frombuffer(int(x).to_bytes(4 * limbs, "little"), dtype="<u4").copy()
+
+
+def _int_from_limbs(a) -> int:
+    return int.from_bytes(np.asarray(a, dtype="<u4").tobytes(), "little")
+
+
+class Key:
+    """A Paillier key held by the library (private: p, q; public: n)."""
+
+    def __init__(self, handle: int):
+        self._h = C.c_void_p(handle)
+        self.n_bits = lib().paillier_key_bits(self._h)
+        self.L = self.n_bits // 32
+        self.is_private = bool(lib().paillier_key_is_private(self._h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    @classmethod
+    def generate(cls, n_bits: int, seed: int) -> "Key":
+        out = C.c_void_p()
+        call("paillier_keygen", n_bits, C.c_uint64(seed), C.byref(out))
+        return cls(out.value)
+
+    @classmethod
+    def from_primes(cls, n_bits: int, p: int, q: int) -> "Key":
+        lh = n_bits // 64
+        pa, qa = _limbs_from_int(p, lh), _limbs_from_int(q, lh)
+        out = C.c_void_p()
+        call("paillier_key_import", n_bits, pa.ctypes.data, qa.ctypes.data, C.byref(out))
+        return cls(out.value)
+
+    @classmethod
+    def public(cls, n_bits: int, n: int) -> "Key":
+        na = _limbs_from_int(n, n_bits // 32)
+        out = C.c_void_p()
+        call("paillier_key_import_public", n_bits, na.ctypes.data, C.byref(out))
+        return cls(out.value)
+
+    def export(self):
+        """(n, p, q) as Python ints (p, q None for a public key)."""
+        na = np.zeros(self.L, dtype=np.uint32)
+        if self.is_private:
+            pa = np.zeros(self.L // 2, dtype=np.uint32)
+            qa = np.zeros(self.L // 2, dtype=np.uint32)
+            call("paillier_key_export", self._h, na.ctypes.data, pa.ctypes.data, qa.ctypes.data)
+            return _int_from_limbs(na), _int_from_limbs(pa), _int_from_limbs(qa)
+        call("paillier_key_export", self._h, na.ctypes.data, None, None)
+        return _int_from_limbs(na), None, None
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().paillier_key_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def encode(v: torch.Tensor, stream=None) -> torch.Tensor:
+    """Fixed-point plaintexts of float32 values (int64 tensor of uint64 bits)."""
+    assert v.dtype == torch.float32
+    out = torch.empty(v.shape, dtype=torch.int64, device=v.device)
+    call("paillier_encode", _ptr(v), v.numel(), _ptr(out), _stream(stream))
+    return out
+
+
+def decode(s: torch.Tensor, cnt: torch.Tensor, stream=None) -> torch.Tensor:
+    assert s.dtype == torch.int64 and cnt.dtype == torch.int32 and s.numel() == cnt.numel()
+    out = torch.empty(s.shape, dtype=torch.float64, device=s.device)
+    call("paillier_decode", _ptr(s), _ptr(cnt), s.numel(), _ptr(out), _stream(stream))
+    return out
+
+
+def encrypt(key: Key, m: torch.Tensor, r: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """Ciphertexts [count, 2L] (int32 bits) of plaintexts m [count] (int64 bits)
+    under randomness r [count, L] (int32 bits)."""
+    count = m.numel()
+    assert m.dtype == torch.int64 and r.dtype == torch.int32 and r.shape == (count, key.L)
+    if out is None:
+        out = torch.empty((count, 2 * key.L), dtype=torch.int32, device=m.device)
+    call("paillier_encrypt", key.handle, _ptr(m), _ptr(r), count, _ptr(out), _stream(stream))
+    return out
+
+
+def ct_prepare(key: Key, ct: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """Montgomery form (mod n^2) of ciphertexts [..., 2L]."""
+    assert ct.dtype == torch.int32 and ct.shape[-1] == 2 * key.L
+    count = ct.numel() // (2 * key.L)
+    if out is None:
+        out = torch.empty_like(ct)
+    call("paillier_ct_prepare", key.handle, _ptr(ct), count, _ptr(out), _stream(stream))
+    return out
+
+
+def hist_aggregate(key: Key, ctm: torch.Tensor, bins: torch.Tensor, node: torch.Tensor, num_nodes: int, K: int,
+                   hist: torch.Tensor | None = None, count: torch.Tensor | None = None, per_node: bool = False,
+                   stream=None):
+    """Encrypted histogram [num_nodes, F, K, 2, 2L] and counts [num_nodes, F, K]
+    from Montgomery-form ciphertexts ctm [2, M, 2L], bins [F, M] uint8, node [M] int32."""
+    M = node.numel()
+    F = bins.shape[0]
+    assert ctm.dtype == torch.int32 and ctm.shape == (2, M, 2 * key.L)
+    assert bins.dtype == torch.uint8 and bins.shape == (F, M) and node.dtype == torch.int32
+    if hist is None:
+        hist = torch.empty((num_nodes, F, K, 2, 2 * key.L), dtype=torch.int32, device=ctm.device)
+    if count is None:
+        count = torch.empty((num_nodes, F, K), dtype=torch.int32, device=ctm.device)
+    fn = "paillier_hist_aggregate_per_node" if per_node else "paillier_hist_aggregate"
+    call(fn, key.handle, _ptr(ctm), M, _ptr(bins), F, K, _ptr(node), num_nodes, _ptr(hist), _ptr(count),
+         _stream(stream))
+    return hist, count
+
+
+def decrypt(key: Key, ct: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """Plaintexts [count, L] (int32 bits) of ciphertexts [..., 2L]."""
+    assert ct.dtype == torch.int32 and ct.shape[-1] == 2 * key.L
+    count = ct.numel() // (2 * key.L)
+    if out is None:
+        out = torch.empty((count, key.L), dtype=torch.int32, device=ct.device)
+    call("paillier_decrypt", key.handle, _ptr(ct), count, _ptr(out), _stream(stream))
+    return out
+
+
+def decrypt_u64(key: Key, ct: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """Plaintexts as uint64 (int64 tensor) of ciphertexts [..., 2L]."""
+    assert ct.dtype == torch.int32 and ct.shape[-1] == 2 * key.L
+    count = ct.numel() // (2 * key.L)
+    if out is None:
+        out = torch.empty(ct.shape[:-1], dtype=torch.int64, device=ct.device)
+    call("paillier_decrypt_u64", key.handle, _ptr(ct), count, _ptr(out), _stream(stream))
+    return out
+
+
+def sync(stream=None) -> int:
+    """Synchronise the stream and raise on a device-reported error; returns the raw status word."""
+    st = C.c_int(0)
+    call("paillier_sync", _stream(stream), C.byref(st))
+    return st.value
+
+
+def to_limb_tensor(arr: np.ndarray, device="cuda") -> torch.Tensor:
+    """uint32 numpy limbs -> int32 torch tensor on the device (bit copy)."""
+    return torch.from_numpy(np.ascontiguousarray(arr, dtype=np.uint32).view(np.int32)).to(device)
+
+
+def from_limb_tensor(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint32)

@@ -220,3 +220,25 @@ def feature_split(F: int, parties: int = 2):
 def rng_misc(seed: int) -> np.random.Generator:
     """A spare stream for tests that need extra seeded draws."""
     return _rng(seed, _TAG_MISC)
+
+
+# ----------------------------------------------------------------------------
+# the five workloads (Sec. III.C worked sizes; Sec. IV.B tree parameters)
+
+CONFIGS = {
+    # plain method, toy: 1,000 samples, 8 uniform pre-binned features x 16 bins, 1024-bit n, root node
+    "toy": dict(M=1_000, F=8, K=16, n_bits=1024, seed=1, bins="uniform", depth=1),
+    # plain method, one tree level: 250k samples, 30 N(0,1) features quantile-binned to 256, 2048-bit n
+    "level": dict(M=250_000, F=30, K=256, n_bits=2048, seed=2, bins="normal", depth=1),
+    # batched: the "level" data, a depth-6 tree with Beta(0.5, 0.5) splits
+    "batched": dict(M=250_000, F=30, K=256, n_bits=2048, seed=3, data_seed=2, bins="normal", depth=6),
+    # large: 1M samples x 64 log-normal features x 256 bins, 3072-bit n, depth 8
+    "large": dict(M=1_000_000, F=64, K=256, n_bits=3072, seed=5, bins="lognormal", depth=8),
+}
+
+
+def make_bins(cfg: dict) -> np.ndarray:
+    seed = cfg.get("data_seed", cfg["seed"])
+    if cfg["bins"] == "uniform":
+        return gen_bins_uniform(cfg["F"], cfg["M"], cfg["K"], seed)
+    return gen_bins_quantile(cfg["F"], cfg["M"], cfg["K"], seed, dist=cfg["bins"])
