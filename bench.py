@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""Benchmark of the vertical secure-XGBoost Paillier hot path on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config level] [--impl ours|reference]
+
+One step is one pass of the whole hot path over one batch of synthetic input
+(Sec. III.B's vertical pattern at Sec. III.C's worked scale):
+  encode g/h -> encrypt (2M values) -> Montgomery form at the passive party ->
+  encrypted histogram of every node of the level -> CRT decrypt of every cell ->
+  decode.
+Inputs are resident in HBM when the timed region starts; a second timed loop
+(`e2e`) goes through the same public API from pinned host buffers, with the
+host->device copies of the step's inputs and the device->host copy of the
+decoded histogram inside the timed region.
+
+Prints ONE JSON line on rank 0.  Under torchrun (N > 1) every rank runs an
+independent replica of the workload (the path shards by sample and feature
+with no exchange; weak scaling) and the slowest rank's time is used.
+
+--impl reference runs the CPU oracle (plain Python integers) on a bounded
+sample of the same workload on the host cores, rank 0 only.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2504_03909_b300 import synth  # noqa: E402
+
+METRIC = "2048-bit Paillier enc/s & encrypted-hist ct-mults/s; p50/p99 request ms"
+
+
+# ----------------------------------------------------------------------------
+# algorithmic work (integer multiply-add halves; a 32x32->64 limb product = 2)
+
+def mont_imad(nl: int) -> int:
+    """One CIOS Montgomery product on nl limbs: 2 nl^2 limb products + nl mul.lo."""
+    return 4 * nl * nl + nl
+
+
+def modexp_montmuls(exp_bits: int, w: int, dec: bool) -> int:
+    """Montgomery products of one half-size exponentiation as the kernel runs it."""
+    nd = (exp_bits + w - 1) // w
+    pre = 2  # ENC: m n and r R; DEC: c_lo R and c_hi R^2
+    return pre + ((1 << w) - 2) + (nd - 1) * (w + 1) + 1
+
+
+def enc_imad(n_bits: int, w: int) -> int:
+    L = n_bits // 32
+    return 2 * modexp_montmuls(n_bits, w, False) * mont_imad(L)
+
+
+def dec_imad(n_bits: int, w: int) -> int:
+    L = n_bits // 32
+    return 2 * modexp_montmuls(n_bits // 2, w, True) * mont_imad(L)
+
+
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_inputs(cfg: dict):
+    p, q = synth.gen_primes(cfg["n_bits"], cfg["seed"])
+    n = p * q
+    gh = synth.gen_gh(cfg["M"], cfg.get("data_seed", cfg["seed"]))
+    r = synth.gen_r(n, cfg["n_bits"], 2 * cfg["M"], cfg["seed"], p, q)
+    bins = synth.make_bins(cfg)
+    return p, q, gh, r, bins
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle arm (reference and cpu_baseline)
+
+def _oracle_sample_work(args):
+    """The oracle's share of one step for a few samples: their encryptions,
+    their histogram products, and a proportional number of decryptions."""
+    import oracle
+    n, p, q, ms, rs, ndec, F = args
+    pub, priv = oracle.keypair(p, q)
+    cts = [oracle.encrypt(pub, m, r) for m, r in zip(ms, rs)]
+    acc = 1
+    for _ in range(F):
+        for c in cts:
+            acc = oracle.add(pub, acc, c)
+    for j in range(ndec):
+        oracle.decrypt(priv, cts[j % len(cts)])
+    return len(cts)
+
+
+def oracle_rate(cfg, p, q, gh, r, samples: int, steps: int = 1):
+    """Runs the oracle over `samples` samples per step on all host cores;
+    returns (enc/s, wall seconds, cores)."""
+    import multiprocessing as mp
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    n = p * q
+    M, F, K = cfg["M"], cfg["F"], cfg["K"]
+    cells = F * K * 2
+    ms = [oracle.encode(x) for x in np.concatenate([gh[0][:samples], gh[1][:samples]])]
+    rs = synth.limbs_to_ints(np.concatenate([r[:samples], r[M:M + samples]]))
+    ndec = max(1, round(cells * samples / M))
+    nw = min(cores, 2 * samples)
+    chunks = [list(range(i, 2 * samples, nw)) for i in range(nw)]
+    per = [(n, p, q, [ms[i] for i in c], [rs[i] for i in c], (ndec if k == 0 else 0), F)
+           for k, c in enumerate(chunks) if c]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(per)) as pool:
+        pool.map(_oracle_sample_work, [(n, p, q, [ms[0]], [rs[0]], 0, 1)] * len(per))  # warm the workers
+        t0 = time.perf_counter()
+        done = 0
+        for _ in range(steps):
+            done += sum(pool.map(_oracle_sample_work, per))
+        wall = time.perf_counter() - t0
+    return done / wall, wall, len(per), ndec
+
+
+def run_reference(args, cfg):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    p, q, gh, r, bins = make_inputs(cfg)
+    samples = 16
+    _ = oracle_rate(cfg, p, q, gh, r, 2, 1)  # warm-up run
+    rate, wall, cores, ndec = oracle_rate(cfg, p, q, gh, r, samples, args.steps)
+    sample = (f"per step {samples} samples of the '{args.config}' workload: {2 * samples} encryptions, "
+              f"{2 * samples * cfg['F']} histogram products, {ndec} decryptions (lambda form)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "enc/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "python-int",
+        "data": "synthetic", "config": workload_config(args.config, cfg),
+        "cpu_baseline": {"value": rate, "unit": "enc/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": "enc/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(name, cfg):
+    desc = {
+        "level": "one tree level: 250,000 samples x 30 features (N(0,1), quantile-binned) x 256 bins, 2048-bit n, "
+                 "root node; encrypt 500k g/h, histogram 30x256x2, CRT-decrypt 15,360 cells",
+        "toy": "toy: 1,000 samples x 8 features x 16 bins, 1024-bit n, root node",
+    }.get(name, name)
+    return {"workload": desc, "M": cfg["M"], "F": cfg["F"], "K": cfg["K"], "n_bits": cfg["n_bits"],
+            "nodes": 1, "l2": "inputs larger than L2 (r 128 MB, ciphertexts 256 MB at 2048-bit)",
+            "parallelism": "replica per GPU"}
+
+
+# ----------------------------------------------------------------------------
+
+def run_ours(args, cfg):
+    import torch
+    from paper_2504_03909_b300 import native, paillier as P
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    M, F, K, n_bits = cfg["M"], cfg["F"], cfg["K"], cfg["n_bits"]
+    L = n_bits // 32
+    p, q, gh, r, bins = make_inputs(cfg)
+    key = P.Key.from_primes(n_bits, p, q)
+
+    # host (pinned) and device copies of the inputs
+    h_v = torch.from_numpy(gh.reshape(-1).copy()).pin_memory()
+    h_r = torch.from_numpy(r.view(np.int32)).pin_memory()
+    h_bins = torch.from_numpy(bins).pin_memory()
+    h_node = torch.zeros(M, dtype=torch.int32).pin_memory()
+    v = h_v.to(dev)
+    r_d = h_r.to(dev)
+    bins_d = h_bins.to(dev)
+    node = h_node.to(dev)
+    ct = torch.empty((2 * M, 2 * L), dtype=torch.int32, device=dev)
+    ctm = torch.empty_like(ct)
+    hist = torch.empty((1, F, K, 2, 2 * L), dtype=torch.int32, device=dev)
+    cnt = torch.empty((1, F, K), dtype=torch.int32, device=dev)
+    sums = torch.empty((1, F, K, 2), dtype=torch.int64, device=dev)
+    cnt2 = torch.empty((1, F, K, 2), dtype=torch.int32, device=dev)
+    out = torch.empty((1, F, K, 2), dtype=torch.float64, device=dev)
+    h_out = torch.empty(out.shape, dtype=torch.float64).pin_memory()
+
+    def step():
+        m = P.encode(v)
+        P.encrypt(key, m, r_d, out=ct)
+        P.ct_prepare(key, ct, out=ctm)
+        P.hist_aggregate(key, ctm.view(2, M, 2 * L), bins_d, node, 1, K, hist=hist, count=cnt)
+        P.decrypt_u64(key, hist.view(-1, 2 * L), out=sums.view(-1))
+        cnt2.copy_(cnt.unsqueeze(-1).expand(1, F, K, 2))
+        P.decode(sums, cnt2, out=out)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # measured integer multiply-add peaks (same process, same clocks)
+    peaks = {}
+    for mix, name in ((0, "carry_rows"), (1, "mad_wide")):
+        rate = native.C.c_double(0)
+        el = native.C.c_double(0)
+        native.call("paillier_imad_peak", mix, 1500.0, native.C.byref(rate), native.C.byref(el),
+                    torch.cuda.current_stream().cuda_stream)
+        peaks[name] = rate.value
+
+    for _ in range(args.warmup):
+        step()
+    P.sync()
+
+    native.call("paillier_profile", 1)
+    n0 = native.lib().paillier_launch_count()
+    barrier()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        barrier()
+    launches = native.lib().paillier_launch_count() - n0
+    elapsed = e0.elapsed_time(e1) / 1e3
+    prof = {}
+    for kname in ("encode", "modexp_enc", "enc_crt", "to_mont", "hist_count", "hist_scan", "feat_scan",
+                  "hist_scatter", "seg_product", "combine", "modexp_dec", "dec_crt", "decode"):
+        tot = native.C.c_double(0)
+        cntl = native.C.c_longlong(0)
+        native.call("paillier_profile_read", kname.encode(), native.C.byref(tot), native.C.byref(cntl))
+        prof[kname] = (tot.value, cntl.value)
+    native.call("paillier_profile", 0)
+    P.sync()
+    if dist is not None:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+
+    # end to end through the public API with pinned host buffers
+    h2d = h_v.numel() * 4 + h_r.numel() * 4 + h_bins.numel() + h_node.numel() * 4
+    d2h = h_out.numel() * 8
+    e2e_steps = max(1, args.steps)
+    barrier()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for _ in range(e2e_steps):
+        v.copy_(h_v, non_blocking=True)
+        r_d.copy_(h_r, non_blocking=True)
+        bins_d.copy_(h_bins, non_blocking=True)
+        node.copy_(h_node, non_blocking=True)
+        step()
+        h_out.copy_(out, non_blocking=True)
+    e3.record()
+    barrier()
+    e2e_s = e2.elapsed_time(e3) / 1e3
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    P.sync()
+
+    units = 2 * M  # g and h values through the whole path per step and GPU
+    value = units * args.steps * world / elapsed
+    def ms(k):
+        return prof[k][0]
+
+    phase = {
+        "encode": ms("encode"),
+        "encrypt": ms("modexp_enc") + ms("enc_crt"),
+        "prepare": ms("to_mont"),
+        "aggregate": sum(ms(k) for k in ("hist_count", "hist_scan", "feat_scan", "hist_scatter", "seg_product",
+                                         "combine")),
+        "decrypt": ms("modexp_dec") + ms("dec_crt"),
+        "decode": ms("decode"),
+    }
+    phase = {k: v_ / args.steps for k, v_ in phase.items()}  # ms per step
+    w = 5
+    enc_launch_ms = prof["modexp_enc"][0] / max(1, prof["modexp_enc"][1])
+    imad_launch = units * enc_imad(n_bits, w)
+    achieved = imad_launch / (enc_launch_ms * 1e-3)
+    peak = max(peaks.values())
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "enc/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic (seeded: logistic g/h, Bernoulli(0.3) labels, N(0,1) features quantile-binned)",
+        "config": workload_config(args.config, cfg),
+        "phases_ms_per_step": phase,
+        "enc_per_s": units / (phase["encrypt"] * 1e-3),
+        "ct_mults_per_s": M * F * 2 / (phase["aggregate"] * 1e-3),
+        "ct_mults_strict_per_step": 2 * F * (M - K),
+        "decrypts_per_s": F * K * 2 / (phase["decrypt"] * 1e-3),
+        "roofline": {
+            "bound": "alu",
+            "kernel": "k_modexp (encrypt)",
+            "achieved": achieved / 1e12,
+            "peak": peak / 1e12,
+            "unit": "TIMAD/s",
+            "frac": achieved / peak,
+            "traffic": None,
+            "peak_source": "project microbenchmark paillier_imad_peak, best mix, same run",
+            "peaks_measured_TIMAD_s": {k: v_ / 1e12 for k, v_ in peaks.items()},
+            "imad_per_launch": imad_launch,
+            "launch_ms": enc_launch_ms,
+        },
+        "clocks": clk.summary(),
+        "e2e": {"value": units * e2e_steps * world / e2e_s, "unit": "enc/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        samples = 48
+        rate, wall, cores, ndec = oracle_rate(cfg, p, q, gh, r, samples, 1)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": "enc/s", "cores": cores, "kind": "oracle",
+            "sample": f"{samples} samples of the workload: {2 * samples} encryptions, {2 * samples * F} histogram "
+                      f"products, {ndec} decryptions (lambda form); {wall:.1f} s wall"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default="level", choices=["level", "toy"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    cfg = synth.CONFIGS[args.config]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+    else:
+        run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    main()

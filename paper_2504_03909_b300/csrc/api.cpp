@@ -1,4 +1,5 @@
 // C-ABI entry points: argument checks, then the launchers.
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -84,6 +85,49 @@ static int* current_status() {
   return status_word(dev);
 }
 
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+std::atomic<bool> g_prof_on{false};
+std::mutex g_prof_mu;
+struct Pending { std::string name; cudaEvent_t e0, e1; };
+std::vector<Pending> g_pending;
+std::map<std::string, std::pair<double, long long>> g_prof_acc;
+
+void drain_pending() {  // caller holds g_prof_mu
+  for (auto& p : g_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.e1) == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+      auto& a = g_prof_acc[p.name];
+      a.first += ms;
+      a.second += 1;
+    }
+    cudaEventDestroy(p.e0);
+    cudaEventDestroy(p.e1);
+  }
+  g_pending.clear();
+}
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ProfScope::ProfScope(const char* kernel, cudaStream_t stream) : name(kernel), s(stream) {
+  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+  if (cudaEventCreate(&e0) != cudaSuccess) { e0 = nullptr; return; }
+  cudaEventRecord(e0, s);
+}
+
+ProfScope::~ProfScope() {
+  note_launch();
+  if (!e0) return;
+  cudaEvent_t e1;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return; }
+  cudaEventRecord(e1, s);
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  g_pending.push_back({name, e0, e1});
+}
+
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 }  // namespace pl
@@ -93,6 +137,27 @@ using namespace pl;
 extern "C" {
 
 const char* paillier_last_error(void) { return pl::g_err.c_str(); }
+
+unsigned long long paillier_launch_count(void) { return pl::g_launches.load(); }
+
+pl_status paillier_profile(int enable) {
+  std::lock_guard<std::mutex> lock(pl::g_prof_mu);
+  pl::drain_pending();
+  pl::g_prof_acc.clear();
+  pl::g_prof_on.store(enable != 0);
+  return PL_OK;
+}
+
+pl_status paillier_profile_read(const char* kernel, double* total_ms, long long* launches) {
+  clear_error();
+  if (!kernel || !total_ms) return fail(PL_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lock(pl::g_prof_mu);
+  pl::drain_pending();
+  auto it = pl::g_prof_acc.find(kernel);
+  *total_ms = it == pl::g_prof_acc.end() ? 0.0 : it->second.first;
+  if (launches) *launches = it == pl::g_prof_acc.end() ? 0 : it->second.second;
+  return PL_OK;
+}
 
 pl_status paillier_sync(void* stream, int* device_status) {
   if (device_status) *device_status = 0;

@@ -101,4 +101,15 @@ pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_
                       const int32_t* d_node, int num_nodes, uint32_t* d_hist, int32_t* d_count, bool per_node,
                       int* st, cudaStream_t s);
 int sm_count();
+
+// ---- tracing: launch counter and optional per-kernel CUDA-event timing ----
+void note_launch();
+// Records CUDA events around one launch on `s` when profiling is on.
+struct ProfScope {
+  const char* name;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr;
+  ProfScope(const char* kernel, cudaStream_t stream);
+  ~ProfScope();
+};
 }  // namespace pl

@@ -325,7 +325,10 @@ pl_status run_prepare(const N2Const& P, const uint32_t* ct, size_t count, uint32
   const size_t ipw = 32 / T;
   const size_t blocks_needed = ((count + ipw - 1) / ipw + (kBlock / 32) - 1) / (kBlock / 32);
   const int g = (int)std::min<size_t>((size_t)grid, blocks_needed);
-  k_to_mont<S, T><<<g, kBlock, 0, s>>>(P, ct, count, ctm);
+  {
+    ProfScope _ps("to_mont", s);
+    k_to_mont<S, T><<<g, kBlock, 0, s>>>(P, ct, count, ctm);
+  }
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
 }
@@ -337,15 +340,21 @@ pl_status run_hist_products(const N2Const& P, const uint32_t* ctm, size_t M, con
   static int grid_seg = 0, grid_comb = 0;
   if (!grid_seg) grid_seg = occupancy_grid<S, T>((const void*)k_seg_product<S, T>, smem);
   if (!grid_comb) grid_comb = occupancy_grid<S, T>((const void*)k_combine<S, T>, smem);
-  k_seg_product<S, T><<<grid_seg, kBlock, smem, s>>>(P, ctm, M, B.idx, B.off, B.choff, B.featoff, F, NK, tile,
-                                                     B.partial);
+  {
+    ProfScope _ps("seg_product", s);
+    k_seg_product<S, T><<<grid_seg, kBlock, smem, s>>>(P, ctm, M, B.idx, B.off, B.choff, B.featoff, F, NK, tile,
+                                                       B.partial);
+  }
   PL_CUDA_TRY(cudaGetLastError());
   const size_t ipw = 32 / T;
   const size_t items = 2ull * F * NK;
   const size_t blocks_needed = ((items + ipw - 1) / ipw + (kBlock / 32) - 1) / (kBlock / 32);
   const int gc = (int)std::min<size_t>((size_t)grid_comb, blocks_needed);
-  k_combine<S, T><<<gc, kBlock, smem, s>>>(P, B.partial, B.off, B.choff, B.featoff, F, NK, K, only_node, hist,
-                                           count_out);
+  {
+    ProfScope _ps("combine", s);
+    k_combine<S, T><<<gc, kBlock, smem, s>>>(P, B.partial, B.off, B.choff, B.featoff, F, NK, K, only_node, hist,
+                                             count_out);
+  }
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
 }
@@ -381,14 +390,26 @@ pl_status hist_pass(pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t*
   PL_CUDA_TRY(cudaMemsetAsync(B.cnt, 0, sizeof(int) * (size_t)F * NK, s));
   const int gx = (int)std::min<size_t>((M + 255) / 256, 1024);
   dim3 grid(gx > 0 ? gx : 1, F);
-  k_hist_count<<<grid, 256, 0, s>>>(d_bins, d_node, M, K, num_nodes, only_node, NK, B.cnt, st);
+  {
+    ProfScope _ps("hist_count", s);
+    k_hist_count<<<grid, 256, 0, s>>>(d_bins, d_node, M, K, num_nodes, only_node, NK, B.cnt, st);
+  }
   PL_CUDA_TRY(cudaGetLastError());
-  k_hist_scan<<<F, kScanBlock, 0, s>>>(B.cnt, NK, tile, B.off, B.choff, B.featch);
+  {
+    ProfScope _ps("hist_scan", s);
+    k_hist_scan<<<F, kScanBlock, 0, s>>>(B.cnt, NK, tile, B.off, B.choff, B.featch);
+  }
   PL_CUDA_TRY(cudaGetLastError());
-  k_feat_scan<<<1, kScanBlock, 0, s>>>(B.featch, F, B.featoff);
+  {
+    ProfScope _ps("feat_scan", s);
+    k_feat_scan<<<1, kScanBlock, 0, s>>>(B.featch, F, B.featoff);
+  }
   PL_CUDA_TRY(cudaGetLastError());
   PL_CUDA_TRY(cudaMemsetAsync(B.cnt, 0, sizeof(int) * (size_t)F * NK, s));
-  k_hist_scatter<<<grid, 256, 0, s>>>(d_bins, d_node, M, K, num_nodes, only_node, NK, B.off, B.cnt, B.idx, st);
+  {
+    ProfScope _ps("hist_scatter", s);
+    k_hist_scatter<<<grid, 256, 0, s>>>(d_bins, d_node, M, K, num_nodes, only_node, NK, B.off, B.cnt, B.idx, st);
+  }
   PL_CUDA_TRY(cudaGetLastError());
   return dispatch_products(2 * key->L, key->agg_cfg.T, key->n2c, d_ctm, M, B, F, NK, K, tile, only_node, d_hist,
                            d_count, s);

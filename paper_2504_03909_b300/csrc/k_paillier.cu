@@ -262,7 +262,10 @@ pl_status run_modexp(const ModexpParams* P, const uint32_t* in, const uint64_t* 
                      int grid, size_t count, cudaStream_t s) {
   const int ipb = kBlock / T;
   const size_t smem = (size_t)S * T * ipb * sizeof(uint32_t);
-  k_modexp<S, T, DEC><<<grid, kBlock, smem, s>>>(*P, in, msg, y, tbl, count);
+  {
+    ProfScope _ps((DEC ? "modexp_dec" : "modexp_enc"), s);
+    k_modexp<S, T, DEC><<<grid, kBlock, smem, s>>>(*P, in, msg, y, tbl, count);
+  }
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
 }
@@ -306,7 +309,10 @@ pl_status modexp_dispatch(int L, int T, int* grid_out, bool launch, const Modexp
 pl_status launch_encode(const float* d_v, size_t count, uint64_t* d_m, int* st, cudaStream_t s) {
   if (count == 0) return PL_OK;
   const int grid = (int)std::min<size_t>((count + 255) / 256, (size_t)sm_count() * 8);
-  k_encode<<<grid, 256, 0, s>>>(d_v, count, d_m, st);
+  {
+    ProfScope _ps("encode", s);
+    k_encode<<<grid, 256, 0, s>>>(d_v, count, d_m, st);
+  }
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
 }
@@ -314,7 +320,10 @@ pl_status launch_encode(const float* d_v, size_t count, uint64_t* d_m, int* st, 
 pl_status launch_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t count, double* d_out, cudaStream_t s) {
   if (count == 0) return PL_OK;
   const int grid = (int)std::min<size_t>((count + 255) / 256, (size_t)sm_count() * 8);
-  k_decode<<<grid, 256, 0, s>>>(d_s, d_cnt, count, d_out);
+  {
+    ProfScope _ps("decode", s);
+    k_decode<<<grid, 256, 0, s>>>(d_s, d_cnt, count, d_out);
+  }
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
 }
@@ -355,7 +364,10 @@ pl_status launch_encrypt(pl_key* key, const uint64_t* d_m, const uint32_t* d_r, 
   uint32_t* y = nullptr;
   pl_status rc = modexp_phase<false>(key, key->enc_cfg, d_r, d_m, count, &y, s);
   if (rc) return rc;
-  k_enc_crt<<<(unsigned)((count + kBlock - 1) / kBlock), kBlock, 0, s>>>(key->enc, y, count, d_ct);
+  {
+    ProfScope _ps("enc_crt", s);
+    k_enc_crt<<<(unsigned)((count + kBlock - 1) / kBlock), kBlock, 0, s>>>(key->enc, y, count, d_ct);
+  }
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
 }
@@ -368,9 +380,15 @@ pl_status launch_decrypt(pl_key* key, const uint32_t* d_ct, size_t count, void* 
   if (rc) return rc;
   const unsigned grid = (unsigned)((count + kBlock - 1) / kBlock);
   if (u64)
-    k_dec_crt<true><<<grid, kBlock, 0, s>>>(key->dec, y, count, key->L, d_out, st);
+    {
+      ProfScope _ps("dec_crt", s);
+      k_dec_crt<true><<<grid, kBlock, 0, s>>>(key->dec, y, count, key->L, d_out, st);
+    }
   else
-    k_dec_crt<false><<<grid, kBlock, 0, s>>>(key->dec, y, count, key->L, d_out, st);
+    {
+      ProfScope _ps("dec_crt", s);
+      k_dec_crt<false><<<grid, kBlock, 0, s>>>(key->dec, y, count, key->L, d_out, st);
+    }
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
 }

@@ -43,6 +43,10 @@ SIGNATURES = {
     "paillier_sync": (_i, [_vp, C.POINTER(_i)]),
     "paillier_last_error": (C.c_char_p, []),
     "paillier_test_mont_mul": (_i, [_i, _i, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "paillier_imad_peak": (_i, [_i, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
+    "paillier_launch_count": (C.c_ulonglong, []),
+    "paillier_profile": (_i, [_i]),
+    "paillier_profile_read": (_i, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
 }
 
 _lib = None

@@ -102,9 +102,11 @@ def encode(v: torch.Tensor, stream=None) -> torch.Tensor:
     return out
 
 
-def decode(s: torch.Tensor, cnt: torch.Tensor, stream=None) -> torch.Tensor:
+def decode(s: torch.Tensor, cnt: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Float64 values of fixed-point sums s (int64 bits) of cnt encoded values each."""
     assert s.dtype == torch.int64 and cnt.dtype == torch.int32 and s.numel() == cnt.numel()
-    out = torch.empty(s.shape, dtype=torch.float64, device=s.device)
+    if out is None:
+        out = torch.empty(s.shape, dtype=torch.float64, device=s.device)
     call("paillier_decode", _ptr(s), _ptr(cnt), s.numel(), _ptr(out), _stream(stream))
     return out
 
