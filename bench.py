@@ -271,7 +271,7 @@ def run_ours(args, cfg):
 
     # measured integer multiply-add peaks (same process, same clocks)
     peaks = {}
-    for mix, name in ((0, "carry_rows"), (1, "mad_wide")):
+    for mix, name in ((0, "carry_rows"), (1, "mad_wide"), (2, "lo_hi")):
         rate = native.C.c_double(0)
         el = native.C.c_double(0)
         native.call("paillier_imad_peak", mix, 1500.0, native.C.byref(rate), native.C.byref(el),

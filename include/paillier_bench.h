@@ -17,7 +17,8 @@ extern "C" {
  * target_ms milliseconds on `stream` with one instruction mix:
  *   mix 0: 16-limb rows as even/odd PTX carry chains (mad.lo.cc/madc.hi.cc),
  *          the pattern of the Montgomery rows;
- *   mix 1: mad.wide.u32 into 64-bit accumulators.
+ *   mix 1: mad.wide.u32 into 64-bit accumulators;
+ *   mix 2: independent mad.lo / mad.hi halves without carries.
  * Unit: IMAD/s, one IMAD being one 32-bit half (lo or hi) of a 32x32 -> 64
  * limb product.  *elapsed_ms (may be NULL) gets the timed duration.  The call
  * allocates and frees a small device buffer and synchronises the stream. */

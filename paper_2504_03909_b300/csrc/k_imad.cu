@@ -8,7 +8,9 @@
 //          chains (mad.lo.cc / madc.hi.cc), plus one mul.lo per row pair --
 //          the exact pattern of the CIOS rows;
 //   mix 1 "wide": mad.wide.u32 into independent 64-bit accumulators (one
-//          instruction per limb product, counted as 2).
+//          instruction per limb product, counted as 2);
+//   mix 2 "lo/hi": independent mad.lo and mad.hi halves, no carries.
+// Every product has distinct operands, so the compiler cannot fold them.
 #include <cuda_runtime.h>
 
 #include "../../include/paillier_bench.h"
@@ -36,28 +38,50 @@ __global__ void __launch_bounds__(256) k_imad_rows(uint32_t* out, int iters, uin
   out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = x;
 }
 
+// 16 independent 64-bit accumulators += a_j * b with distinct a_j (every
+// product is a different pair of operands, so nothing can be folded).
 __global__ void __launch_bounds__(256) k_imad_wide(uint32_t* out, int iters, uint32_t seed) {
-  uint64_t x[8];
-  uint32_t a = seed ^ threadIdx.x, b = seed * 3 + 1;
+  uint64_t acc[16];
+  uint32_t a[16];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) x[j] = seed + j * 77 + threadIdx.x;
+  for (int j = 0; j < 16; ++j) { a[j] = seed * (j + 7) + threadIdx.x; acc[j] = a[j]; }
+  uint32_t b = seed ^ threadIdx.x;
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(x[j]) : "r"(a), "r"(b + j));
-    a ^= (uint32_t)x[0];
+    for (int j = 0; j < 16; ++j) asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[j]) : "r"(a[j]), "r"(b));
+    b = (uint32_t)acc[it & 15] * 0x01000193u + it;
   }
   uint64_t y = 0;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) y ^= x[j];
+  for (int j = 0; j < 16; ++j) y ^= acc[j];
   out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = (uint32_t)(y ^ (y >> 32));
+}
+
+// 16 independent lo and hi halves (mad.lo / mad.hi, no carries)
+__global__ void __launch_bounds__(256) k_imad_lohi(uint32_t* out, int iters, uint32_t seed) {
+  uint32_t lo[16], hi[16], a[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) { a[j] = seed * (j + 7) + threadIdx.x; lo[j] = a[j]; hi[j] = ~a[j]; }
+  uint32_t b = seed ^ threadIdx.x;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      asm volatile("mad.lo.u32 %0, %1, %2, %0;" : "+r"(lo[j]) : "r"(a[j]), "r"(b));
+      asm volatile("mad.hi.u32 %0, %1, %2, %0;" : "+r"(hi[j]) : "r"(a[j]), "r"(b));
+    }
+    b = lo[it & 15] * 0x01000193u + it;
+  }
+  uint32_t y = 0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) y ^= lo[j] ^ hi[j];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = y;
 }
 
 constexpr int kRowS = 16;
 // IMAD per iteration and thread: 2 rows x 2 S multiply-add halves + 2 mul.lo
 constexpr double kRowsImadPerIter = 2.0 * 2 * kRowS + 2;
-constexpr double kWideImadPerIter = 2.0 * 32;  // 32 mad.wide, 2 IMAD each
+constexpr double kWideImadPerIter = 2.0 * 16;  // 16 mad.wide (+1 mul.lo ignored), 2 IMAD each
+constexpr double kLoHiImadPerIter = 2.0 * 16;  // 16 mad.lo + 16 mad.hi
 
 }  // namespace
 }  // namespace pl
@@ -66,7 +90,7 @@ extern "C" pl_status paillier_imad_peak(int mix, double target_ms, double* imad_
                                         void* stream) {
   using namespace pl;
   clear_error();
-  if (!imad_per_s || (mix != 0 && mix != 1) || !(target_ms > 0)) return fail(PL_EINVAL, "bad argument");
+  if (!imad_per_s || mix < 0 || mix > 2 || !(target_ms > 0)) return fail(PL_EINVAL, "bad argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int blocks = sm_count() * 8, threads = 256;
   uint32_t* out = nullptr;
@@ -77,8 +101,10 @@ extern "C" pl_status paillier_imad_peak(int mix, double target_ms, double* imad_
   auto launch = [&](int iters, uint32_t seed) {
     if (mix == 0)
       k_imad_rows<kRowS><<<blocks, threads, 0, s>>>(out, iters, seed);
-    else
+    else if (mix == 1)
       k_imad_wide<<<blocks, threads, 0, s>>>(out, iters, seed);
+    else
+      k_imad_lohi<<<blocks, threads, 0, s>>>(out, iters, seed);
   };
   // calibrate
   int iters = 2000;
@@ -103,7 +129,7 @@ extern "C" pl_status paillier_imad_peak(int mix, double target_ms, double* imad_
   cudaEventDestroy(e1);
   cudaFree(out);
   if (e != cudaSuccess) return cuda_fail(e, "imad peak kernel");
-  const double per = mix == 0 ? kRowsImadPerIter : kWideImadPerIter;
+  const double per = mix == 0 ? kRowsImadPerIter : (mix == 1 ? kWideImadPerIter : kLoHiImadPerIter);
   *imad_per_s = per * iters * (double)blocks * threads / (ms * 1e-3);
   if (elapsed_ms) *elapsed_ms = ms;
   return PL_OK;
