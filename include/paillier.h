@@ -161,6 +161,31 @@ pl_status paillier_decrypt(const pl_key* key, const uint32_t* d_ct, size_t count
 pl_status paillier_decrypt_u64(const pl_key* key, const uint32_t* d_ct, size_t count,
                                uint64_t* d_m, void* stream);
 
+/* As paillier_decrypt_u64, for callers that cannot allocate device memory.
+ * The paper has no counterpart; it exists because some callers may not call
+ * cudaMalloc at all: a process whose device memory is owned by another
+ * allocator (a framework's caching pool that has reserved the GPU), a
+ * latency-critical loop where cudaMalloc's implicit device synchronisation is
+ * not acceptable, or an embedding application that forbids allocation after
+ * start-up.  This call allocates nothing: its scratch (the CRT half results
+ * and the window tables) is one fixed device array inside the library, about
+ * 35 MB, which every GPU that loads the library holds until the process exits.
+ *   - count must be <= 8192 ciphertexts per call (else PL_EINVAL, nothing is
+ *     launched); every supported key size is accepted.
+ *   - The first call on a device looks up the array's device address on that
+ *     device (the device must be current).  Make that first call before any
+ *     stream capture.
+ *   - All calls share the one array, which keeps the last call's contents;
+ *     nothing in it needs to start at zero.  Calls whose kernels overlap on
+ *     the GPU (different streams, or different host threads) race on it and
+ *     give wrong results: serialise them.
+ *   - A plaintext >= 2^64 is written as UINT64_MAX (the device status word of
+ *     paillier_sync is not set by this call).
+ *   - It uses a 4-bit window, so it is somewhat slower than
+ *     paillier_decrypt_u64; results are identical. */
+pl_status paillier_decrypt_u64_noalloc(const pl_key* key, const uint32_t* d_ct, size_t count, uint64_t* d_m,
+                                       void* stream);
+
 /* ------------------------------------------------------------ status -- */
 
 /* Synchronises `stream`, then returns the first CUDA error or the device

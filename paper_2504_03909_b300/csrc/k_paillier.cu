@@ -8,6 +8,8 @@
 // it (CRT recombination, exact division L_p) are one thread per item.
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "internal.h"
 #include "mp.cuh"
 
@@ -394,3 +396,109 @@ pl_status launch_decrypt(pl_key* key, const uint32_t* d_ct, size_t count, void* 
 }
 
 }  // namespace pl
+
+// ---------------------------------------------------------------------------
+// Allocation-free CRT decryption to uint64 (paillier_decrypt_u64_noalloc).
+//
+// For callers that must not allocate device memory, the scratch this path
+// needs (the two CRT half results and the per-instance window tables) lives in
+// one file-scope device array instead of the key's scratch buffer.  The array
+// is part of the library's device image: every GPU that loads the library
+// holds it (about 35 MB) until the process exits.
+namespace pl {
+namespace {
+
+constexpr size_t kNaMaxCount = 8192;  // ciphertexts per call
+constexpr int kNaWindow = 4;          // window bits: 16 table entries per instance
+constexpr size_t kNaYWords = 2 * kNaMaxCount * kMaxL;                       // y[2][count][L]
+constexpr size_t kNaTblWords = (size_t)148 * 32 * (1u << kNaWindow) * kMaxL;  // 4736 slots at L = 96
+constexpr int kNaMaxDevices = 64;
+
+static __device__ __align__(256) uint32_t g_na_scratch[kNaYWords + kNaTblWords];
+static __device__ int g_na_status;  // range errors of this path (write-only sink)
+
+std::mutex g_na_mu;
+uint32_t* g_na_scratch_ptr[kNaMaxDevices] = {};
+int* g_na_status_ptr[kNaMaxDevices] = {};
+
+// Once per device, with that device current: device addresses of the arrays.
+pl_status na_setup(int dev, uint32_t** scratch, int** status) {
+  if (dev < 0 || dev >= kNaMaxDevices) return fail(PL_EINVAL, "device ordinal out of range for the allocation-free path");
+  std::lock_guard<std::mutex> lock(g_na_mu);
+  if (!g_na_scratch_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    void* q = nullptr;
+    e = cudaGetSymbolAddress(&q, g_na_status);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(status)");
+    g_na_scratch_ptr[dev] = static_cast<uint32_t*>(p);
+    g_na_status_ptr[dev] = static_cast<int*>(q);
+  }
+  *scratch = g_na_scratch_ptr[dev];
+  *status = g_na_status_ptr[dev];
+  return PL_OK;
+}
+
+}  // namespace
+}  // namespace pl
+
+extern "C" pl_status paillier_decrypt_u64_noalloc(const pl_key* key, const uint32_t* d_ct, size_t count,
+                                                  uint64_t* d_m, void* stream) {
+  using namespace pl;
+  clear_error();
+  if (!key) return fail(PL_EINVAL, "key is NULL");
+  if (!key->priv) return fail(PL_EINVAL, "decryption needs the private key");
+  if (count == 0) return PL_OK;
+  if (count > kNaMaxCount)
+    return fail(PL_EINVAL, "count exceeds the allocation-free maximum of 8192 ciphertexts per call");
+  if (!d_ct || !d_m) return fail(PL_EINVAL, "NULL buffer");
+  if ((reinterpret_cast<uintptr_t>(d_ct) & 15u) || (reinterpret_cast<uintptr_t>(d_m) & 15u))
+    return fail(PL_EINVAL, "buffers must be 16-byte aligned");
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+  uint32_t* scratch = nullptr;
+  int* status = nullptr;
+  pl_status rc = na_setup(dev, &scratch, &status);
+  if (rc) return rc;
+  const int L = key->L;
+  const int T = key->dec_cfg.T;
+  // exponent digits of p - 1 and q - 1 at the fixed window, built on the stack
+  ModexpParams P;
+  std::memset(&P, 0, sizeof(P));
+  for (int h = 0; h < 2; ++h) {
+    P.half[h] = key->half[h];
+    const plh::Big& e = key->e_dec[h];
+    const int nd = (e.bits() + kNaWindow - 1) / kNaWindow;
+    for (int i = 0; i < nd; ++i) {
+      int d = 0;
+      for (int b = 0; b < kNaWindow; ++b) d |= (int)e.bit(i * kNaWindow + b) << b;
+      P.dig[h][i] = (uint8_t)d;
+    }
+    P.ndig[h] = nd;
+  }
+  P.w = kNaWindow;
+  int grid = 0;
+  rc = modexp_dispatch<true>(L, T, &grid, false, &P, nullptr, nullptr, nullptr, nullptr, 0, nullptr);
+  if (rc) return rc;
+  // the table slots the array holds for this key size bound the grid
+  const size_t ipb = kBlock / T;
+  const size_t slots = kNaTblWords / (((size_t)1 << kNaWindow) * L);
+  const size_t ipw = 32 / (size_t)T;
+  const size_t warps_needed = 2 * ((count + ipw - 1) / ipw);
+  const size_t blocks_needed = (warps_needed + (kBlock / 32) - 1) / (kBlock / 32);
+  size_t g = std::min<size_t>((size_t)grid, slots / ipb);
+  g = std::min(g, blocks_needed);
+  grid = (int)std::max<size_t>(g, 1);
+  uint32_t* y = scratch;
+  uint32_t* tbl = scratch + kNaYWords;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = modexp_dispatch<true>(L, T, &grid, true, &P, d_ct, nullptr, y, tbl, count, s);
+  if (rc) return rc;
+  k_dec_crt<true><<<(unsigned)((count + kBlock - 1) / kBlock), kBlock, 0, s>>>(key->dec, y, count, L, d_m, status);
+  note_launch();
+  ce = cudaGetLastError();
+  if (ce != cudaSuccess) return cuda_fail(ce, "k_dec_crt");
+  return PL_OK;
+}

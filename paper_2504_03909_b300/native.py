@@ -40,6 +40,7 @@ SIGNATURES = {
     "paillier_hist_aggregate_per_node": (_i, [_vp, _vp, _sz, _vp, _i, _i, _vp, _i, _vp, _vp, _vp]),
     "paillier_decrypt": (_i, [_vp, _vp, _sz, _vp, _vp]),
     "paillier_decrypt_u64": (_i, [_vp, _vp, _sz, _vp, _vp]),
+    "paillier_decrypt_u64_noalloc": (_i, [_vp, _vp, _sz, _vp, _vp]),
     "paillier_sync": (_i, [_vp, C.POINTER(_i)]),
     "paillier_last_error": (C.c_char_p, []),
     "paillier_test_mont_mul": (_i, [_i, _i, _vp, _vp, _vp, _sz, _vp, _vp]),
