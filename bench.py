@@ -212,6 +212,7 @@ def workload_config(name, cfg):
         "level": "one tree level: 250,000 samples x 30 features (N(0,1), quantile-binned) x 256 bins, 2048-bit n, "
                  "root node; encrypt 500k g/h, histogram 30x256x2, CRT-decrypt 15,360 cells",
         "toy": "toy: 1,000 samples x 8 features x 16 bins, 1024-bit n, root node",
+        "level_small": "small case of the level kernels: 8,192 samples x 30 features x 256 bins, 2048-bit n, root",
     }.get(name, name)
     return {"workload": desc, "M": cfg["M"], "F": cfg["F"], "K": cfg["K"], "n_bits": cfg["n_bits"],
             "nodes": 1, "l2": "inputs larger than L2 (r 128 MB, ciphertexts 256 MB at 2048-bit)",
@@ -408,7 +409,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="level", choices=["level", "toy"])
+    ap.add_argument("--config", default="level", choices=["level", "toy", "level_small"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -230,6 +230,8 @@ CONFIGS = {
     "toy": dict(M=1_000, F=8, K=16, n_bits=1024, seed=1, bins="uniform", depth=1),
     # plain method, one tree level: 250k samples, 30 N(0,1) features quantile-binned to 256, 2048-bit n
     "level": dict(M=250_000, F=30, K=256, n_bits=2048, seed=2, bins="normal", depth=1),
+    # a small case of the level workload's kernels (same key size and shapes), for profiling
+    "level_small": dict(M=8_192, F=30, K=256, n_bits=2048, seed=2, bins="normal", depth=1),
     # batched: the "level" data, a depth-6 tree with Beta(0.5, 0.5) splits
     "batched": dict(M=250_000, F=30, K=256, n_bits=2048, seed=3, data_seed=2, bins="normal", depth=6),
     # large: 1M samples x 64 log-normal features x 256 bins, 3072-bit n, depth 8
