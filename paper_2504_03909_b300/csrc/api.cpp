@@ -109,6 +109,7 @@ void drain_pending() {  // caller holds g_prof_mu
 }  // namespace
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void adjust_launch_count(long long delta) { g_launches.fetch_add((unsigned long long)delta, std::memory_order_relaxed); }
 
 ProfScope::ProfScope(const char* kernel, cudaStream_t stream) : name(kernel), s(stream) {
   if (!g_prof_on.load(std::memory_order_relaxed)) return;

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/paillier.h"
+#include "../../include/paillier_bench.h"
 #include "hostmp.h"
 #include "kparams.h"
 
@@ -102,8 +103,33 @@ pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_
                       int* st, cudaStream_t s);
 int sm_count();
 
+// ---- histogram pass pieces shared with the level plan ----------------------
+struct HistBufs {
+  int* cnt;
+  int* off;
+  int* choff;
+  int* featch;
+  int* featoff;
+  HistDesc* desc;
+  int* idx;
+  uint32_t* partial;
+};
+struct HistLayout {
+  size_t o_cnt, o_off, o_choff, o_featch, o_featoff, o_desc, o_idx, o_part, bytes;
+};
+bool agg_supported(int NL, int T);
+HistLayout hist_layout(size_t M, int F, int NK_max, int tile, int NL);
+HistBufs hist_bufs(const HistLayout& h, void* base);
+pl_status launch_set_desc(HistDesc* D, int num_nodes, int NK, int only_node, cudaStream_t s);
+pl_status hist_enqueue(const pl_key* key, const AggCfg& cfg, const HistBufs& B, int NK_max, const uint32_t* d_ctm,
+                       size_t M, const uint8_t* d_bins, int F, int K, const int32_t* d_node, uint32_t* d_hist,
+                       int32_t* d_count, int* st, cudaStream_t s);
+
 // ---- tracing: launch counter and optional per-kernel CUDA-event timing ----
 void note_launch();
+void adjust_launch_count(long long delta);
+bool modexp_supported(int L, int T);
+pl_status launch_fill_random(uint32_t* p, size_t rows, int row_limbs, int zero_top, uint64_t seed, cudaStream_t s);
 // Records CUDA events around one launch on `s` when profiling is on.
 struct ProfScope {
   const char* name;

@@ -35,9 +35,17 @@ __device__ __forceinline__ int hist_key(int v, int b, int K, int num_nodes, int 
   return v * K + b;
 }
 
+__global__ void k_set_desc(HistDesc* D, int num_nodes, int NK, int only_node) {
+  D->num_nodes = num_nodes;
+  D->NK = NK;
+  D->only_node = only_node;
+  D->pad = 0;
+}
+
 __global__ void k_hist_count(const uint8_t* __restrict__ bins, const int32_t* __restrict__ node, size_t M, int K,
-                             int num_nodes, int only_node, int NK, int* __restrict__ cnt, int* status) {
+                             const HistDesc* __restrict__ D, int* __restrict__ cnt, int* status) {
   const int f = blockIdx.y;
+  const int num_nodes = D->num_nodes, only_node = D->only_node, NK = D->NK;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
     const int key = hist_key(node[i], bins[(size_t)f * M + i], K, num_nodes, only_node, status);
     if (key >= 0) atomicAdd(&cnt[(size_t)f * NK + key], 1);
@@ -45,9 +53,10 @@ __global__ void k_hist_count(const uint8_t* __restrict__ bins, const int32_t* __
 }
 
 __global__ void k_hist_scatter(const uint8_t* __restrict__ bins, const int32_t* __restrict__ node, size_t M, int K,
-                               int num_nodes, int only_node, int NK, const int* __restrict__ off,
+                               const HistDesc* __restrict__ D, const int* __restrict__ off,
                                int* __restrict__ cursor, int* __restrict__ idx, int* status) {
   const int f = blockIdx.y;
+  const int num_nodes = D->num_nodes, only_node = D->only_node, NK = D->NK;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
     const int key = hist_key(node[i], bins[(size_t)f * M + i], K, num_nodes, only_node, status);
     if (key >= 0) {
@@ -90,10 +99,12 @@ __device__ void block_scan2(long long& a, long long& b, long long* ta, long long
 
 // one block per feature: off[f][0..NK] (sample offsets), choff[f][0..NK]
 // (chunk offsets within the feature), featch[f] (chunks of the feature)
-__global__ void __launch_bounds__(kScanBlock) k_hist_scan(const int* __restrict__ cnt, int NK, int tile,
+__global__ void __launch_bounds__(kScanBlock) k_hist_scan(const int* __restrict__ cnt,
+                                                          const HistDesc* __restrict__ D, int tile,
                                                           int* __restrict__ off, int* __restrict__ choff,
                                                           int* __restrict__ featch) {
   const int f = blockIdx.x;
+  const int NK = D->NK;
   const int* c = cnt + (size_t)f * NK;
   const int per = (NK + blockDim.x - 1) / blockDim.x;
   const int j0 = min(NK, (int)threadIdx.x * per), j1 = min(NK, j0 + per);
@@ -170,9 +181,11 @@ __global__ void __launch_bounds__(kBlock) k_seg_product(const __grid_constant__ 
                                                         const uint32_t* __restrict__ ctm, size_t M,
                                                         const int* __restrict__ idx, const int* __restrict__ off,
                                                         const int* __restrict__ choff,
-                                                        const int* __restrict__ featoff, int F, int NK, int tile,
+                                                        const int* __restrict__ featoff, int F,
+                                                        const HistDesc* __restrict__ D, int tile,
                                                         uint32_t* __restrict__ partial) {
   constexpr int NL = S * T;
+  const int NK = D->NK;
   constexpr int IPW = 32 / T;
   extern __shared__ uint32_t smem[];
   const int ipb = blockDim.x / T;
@@ -228,10 +241,11 @@ template <int S, int T>
 __global__ void __launch_bounds__(kBlock) k_combine(const __grid_constant__ N2Const P,
                                                     const uint32_t* __restrict__ partial,
                                                     const int* __restrict__ off, const int* __restrict__ choff,
-                                                    const int* __restrict__ featoff, int F, int NK, int K,
-                                                    int only_node, uint32_t* __restrict__ hist,
-                                                    int32_t* __restrict__ count_out) {
+                                                    const int* __restrict__ featoff, int F,
+                                                    const HistDesc* __restrict__ D, int K,
+                                                    uint32_t* __restrict__ hist, int32_t* __restrict__ count_out) {
   constexpr int NL = S * T;
+  const int NK = D->NK, only_node = D->only_node;
   constexpr int IPW = 32 / T;
   extern __shared__ uint32_t smem[];
   const int ipb = blockDim.x / T;
@@ -308,16 +322,6 @@ int occupancy_grid(const void* fn, size_t smem) {
   return b * sm_count();
 }
 
-struct HistBufs {
-  int* cnt;
-  int* off;
-  int* choff;
-  int* featch;
-  int* featoff;
-  int* idx;
-  uint32_t* partial;
-};
-
 template <int S, int T>
 pl_status run_prepare(const N2Const& P, const uint32_t* ct, size_t count, uint32_t* ctm, cudaStream_t s) {
   static int grid = 0;
@@ -334,26 +338,25 @@ pl_status run_prepare(const N2Const& P, const uint32_t* ct, size_t count, uint32
 }
 
 template <int S, int T>
-pl_status run_hist_products(const N2Const& P, const uint32_t* ctm, size_t M, const HistBufs& B, int F, int NK, int K,
-                            int tile, int only_node, uint32_t* hist, int32_t* count_out, cudaStream_t s) {
+pl_status run_hist_products(const N2Const& P, const uint32_t* ctm, size_t M, const HistBufs& B, const HistDesc* D,
+                            int F, int NK_max, int K, int tile, uint32_t* hist, int32_t* count_out, cudaStream_t s) {
   const size_t smem = (size_t)S * T * (kBlock / T) * sizeof(uint32_t);
   static int grid_seg = 0, grid_comb = 0;
   if (!grid_seg) grid_seg = occupancy_grid<S, T>((const void*)k_seg_product<S, T>, smem);
   if (!grid_comb) grid_comb = occupancy_grid<S, T>((const void*)k_combine<S, T>, smem);
   {
     ProfScope _ps("seg_product", s);
-    k_seg_product<S, T><<<grid_seg, kBlock, smem, s>>>(P, ctm, M, B.idx, B.off, B.choff, B.featoff, F, NK, tile,
+    k_seg_product<S, T><<<grid_seg, kBlock, smem, s>>>(P, ctm, M, B.idx, B.off, B.choff, B.featoff, F, D, tile,
                                                        B.partial);
   }
   PL_CUDA_TRY(cudaGetLastError());
   const size_t ipw = 32 / T;
-  const size_t items = 2ull * F * NK;
+  const size_t items = 2ull * F * NK_max;
   const size_t blocks_needed = ((items + ipw - 1) / ipw + (kBlock / 32) - 1) / (kBlock / 32);
   const int gc = (int)std::min<size_t>((size_t)grid_comb, blocks_needed);
   {
     ProfScope _ps("combine", s);
-    k_combine<S, T><<<gc, kBlock, smem, s>>>(P, B.partial, B.off, B.choff, B.featoff, F, NK, K, only_node, hist,
-                                             count_out);
+    k_combine<S, T><<<gc, kBlock, smem, s>>>(P, B.partial, B.off, B.choff, B.featoff, F, D, K, hist, count_out);
   }
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
@@ -370,34 +373,75 @@ pl_status dispatch_prepare(int NL, int T, const N2Const& P, const uint32_t* ct, 
   return fail(PL_EINVAL, "no mod n^2 kernel for this (limbs, lanes) pair");
 }
 
-pl_status dispatch_products(int NL, int T, const N2Const& P, const uint32_t* ctm, size_t M, const HistBufs& B, int F,
-                            int NK, int K, int tile, int only_node, uint32_t* hist, int32_t* count_out,
-                            cudaStream_t s) {
+pl_status dispatch_products(int NL, int T, const N2Const& P, const uint32_t* ctm, size_t M, const HistBufs& B,
+                            const HistDesc* D, int F, int NK_max, int K, int tile, uint32_t* hist,
+                            int32_t* count_out, cudaStream_t s) {
 #define PL_CASE(LL, TT)                                                                                   \
   if (NL == LL && T == TT)                                                                                \
-    return run_hist_products<LL / TT, TT>(P, ctm, M, B, F, NK, K, tile, only_node, hist, count_out, s);
+    return run_hist_products<LL / TT, TT>(P, ctm, M, B, D, F, NK_max, K, tile, hist, count_out, s);
   PL_N2_CASES(PL_CASE)
 #undef PL_CASE
   return fail(PL_EINVAL, "no mod n^2 kernel for this (limbs, lanes) pair");
 }
 
-// One group-by + segmented product + combine over the node selection.
-pl_status hist_pass(pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t* d_bins, int F, int K,
-                    const int32_t* d_node, int num_nodes, int only_node, const HistBufs& B, uint32_t* d_hist,
-                    int32_t* d_count, int* st, cudaStream_t s) {
-  const int NK = only_node >= 0 ? K : num_nodes * K;
-  const int tile = key->agg_cfg.tile;
-  PL_CUDA_TRY(cudaMemsetAsync(B.cnt, 0, sizeof(int) * (size_t)F * NK, s));
+}  // namespace
+
+bool agg_supported(int NL, int T) {
+#define PL_CASE(LL, TT) \
+  if (NL == LL && T == TT) return true;
+  PL_N2_CASES(PL_CASE)
+#undef PL_CASE
+  return false;
+}
+
+HistLayout hist_layout(size_t M, int F, int NK_max, int tile, int NL) {
+  HistLayout h{};
+  const size_t max_chunks = (size_t)F * ((M + tile - 1) / tile + std::min<size_t>((size_t)NK_max, M));
+  Carve cv;
+  h.o_cnt = cv.take(sizeof(int) * (size_t)F * NK_max);
+  h.o_off = cv.take(sizeof(int) * (size_t)F * (NK_max + 1));
+  h.o_choff = cv.take(sizeof(int) * (size_t)F * (NK_max + 1));
+  h.o_featch = cv.take(sizeof(int) * (size_t)F);
+  h.o_featoff = cv.take(sizeof(int) * ((size_t)F + 1));
+  h.o_desc = cv.take(sizeof(HistDesc));
+  h.o_idx = cv.take(sizeof(int) * (size_t)F * (M ? M : 1));
+  h.o_part = cv.take(sizeof(uint32_t) * (size_t)NL * 2 * (max_chunks ? max_chunks : 1));
+  h.bytes = cv.off;
+  return h;
+}
+
+HistBufs hist_bufs(const HistLayout& h, void* base) {
+  char* b = static_cast<char*>(base);
+  return HistBufs{reinterpret_cast<int*>(b + h.o_cnt),     reinterpret_cast<int*>(b + h.o_off),
+                  reinterpret_cast<int*>(b + h.o_choff),   reinterpret_cast<int*>(b + h.o_featch),
+                  reinterpret_cast<int*>(b + h.o_featoff), reinterpret_cast<HistDesc*>(b + h.o_desc),
+                  reinterpret_cast<int*>(b + h.o_idx),     reinterpret_cast<uint32_t*>(b + h.o_part)};
+}
+
+pl_status launch_set_desc(HistDesc* D, int num_nodes, int NK, int only_node, cudaStream_t s) {
+  k_set_desc<<<1, 1, 0, s>>>(D, num_nodes, NK, only_node);
+  note_launch();
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
+
+// One group-by + segmented product + combine; the node selection and NK come
+// from B.desc on the device, buffers are sized for NK_max.
+pl_status hist_enqueue(const pl_key* key, const AggCfg& cfg, const HistBufs& B, int NK_max, const uint32_t* d_ctm,
+                       size_t M, const uint8_t* d_bins, int F, int K, const int32_t* d_node, uint32_t* d_hist,
+                       int32_t* d_count, int* st, cudaStream_t s) {
+  const int tile = cfg.tile;
+  PL_CUDA_TRY(cudaMemsetAsync(B.cnt, 0, sizeof(int) * (size_t)F * NK_max, s));
   const int gx = (int)std::min<size_t>((M + 255) / 256, 1024);
   dim3 grid(gx > 0 ? gx : 1, F);
   {
     ProfScope _ps("hist_count", s);
-    k_hist_count<<<grid, 256, 0, s>>>(d_bins, d_node, M, K, num_nodes, only_node, NK, B.cnt, st);
+    k_hist_count<<<grid, 256, 0, s>>>(d_bins, d_node, M, K, B.desc, B.cnt, st);
   }
   PL_CUDA_TRY(cudaGetLastError());
   {
     ProfScope _ps("hist_scan", s);
-    k_hist_scan<<<F, kScanBlock, 0, s>>>(B.cnt, NK, tile, B.off, B.choff, B.featch);
+    k_hist_scan<<<F, kScanBlock, 0, s>>>(B.cnt, B.desc, tile, B.off, B.choff, B.featch);
   }
   PL_CUDA_TRY(cudaGetLastError());
   {
@@ -405,17 +449,14 @@ pl_status hist_pass(pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t*
     k_feat_scan<<<1, kScanBlock, 0, s>>>(B.featch, F, B.featoff);
   }
   PL_CUDA_TRY(cudaGetLastError());
-  PL_CUDA_TRY(cudaMemsetAsync(B.cnt, 0, sizeof(int) * (size_t)F * NK, s));
+  PL_CUDA_TRY(cudaMemsetAsync(B.cnt, 0, sizeof(int) * (size_t)F * NK_max, s));
   {
     ProfScope _ps("hist_scatter", s);
-    k_hist_scatter<<<grid, 256, 0, s>>>(d_bins, d_node, M, K, num_nodes, only_node, NK, B.off, B.cnt, B.idx, st);
+    k_hist_scatter<<<grid, 256, 0, s>>>(d_bins, d_node, M, K, B.desc, B.off, B.cnt, B.idx, st);
   }
   PL_CUDA_TRY(cudaGetLastError());
-  return dispatch_products(2 * key->L, key->agg_cfg.T, key->n2c, d_ctm, M, B, F, NK, K, tile, only_node, d_hist,
-                           d_count, s);
+  return dispatch_products(2 * key->L, cfg.T, key->n2c, d_ctm, M, B, B.desc, F, NK_max, K, tile, d_hist, d_count, s);
 }
-
-}  // namespace
 
 pl_status launch_ct_prepare(pl_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_ctm, cudaStream_t s) {
   if (count == 0) return PL_OK;
@@ -425,31 +466,23 @@ pl_status launch_ct_prepare(pl_key* key, const uint32_t* d_ct, size_t count, uin
 pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t* d_bins, int F, int K,
                       const int32_t* d_node, int num_nodes, uint32_t* d_hist, int32_t* d_count, bool per_node,
                       int* st, cudaStream_t s) {
-  const int NK = per_node ? K : num_nodes * K;
-  const int tile = key->agg_cfg.tile;
-  const size_t NL = 2 * (size_t)key->L;
-  // chunks per feature <= M / tile + (non-empty cells)
-  const size_t max_chunks = (size_t)F * ((M + tile - 1) / tile + std::min<size_t>((size_t)NK, M));
-  Carve cv;
-  const size_t o_cnt = cv.take(sizeof(int) * (size_t)F * NK);
-  const size_t o_off = cv.take(sizeof(int) * (size_t)F * (NK + 1));
-  const size_t o_choff = cv.take(sizeof(int) * (size_t)F * (NK + 1));
-  const size_t o_featch = cv.take(sizeof(int) * (size_t)F);
-  const size_t o_featoff = cv.take(sizeof(int) * ((size_t)F + 1));
-  const size_t o_idx = cv.take(sizeof(int) * (size_t)F * (M ? M : 1));
-  const size_t o_part = cv.take(sizeof(uint32_t) * NL * 2 * (max_chunks ? max_chunks : 1));
+  const AggCfg cfg = key->agg_cfg;
+  const int NK_max = per_node ? K : num_nodes * K;
+  const HistLayout h = hist_layout(M, F, NK_max, cfg.tile, 2 * key->L);
   Scratch* sc = key->scratch_for_current_device();
   if (!sc) return fail(PL_ECUDA, "no current device");
-  char* base = static_cast<char*>(sc->get(cv.off));
+  void* base = sc->get(h.bytes);
   if (!base) return fail(PL_ENOMEM, "scratch allocation failed");
-  HistBufs B{reinterpret_cast<int*>(base + o_cnt),     reinterpret_cast<int*>(base + o_off),
-              reinterpret_cast<int*>(base + o_choff),  reinterpret_cast<int*>(base + o_featch),
-              reinterpret_cast<int*>(base + o_featoff), reinterpret_cast<int*>(base + o_idx),
-              reinterpret_cast<uint32_t*>(base + o_part)};
-  if (!per_node)
-    return hist_pass(key, d_ctm, M, d_bins, F, K, d_node, num_nodes, -1, B, d_hist, d_count, st, s);
+  const HistBufs B = hist_bufs(h, base);
+  if (!per_node) {
+    pl_status rc = launch_set_desc(B.desc, num_nodes, num_nodes * K, -1, s);
+    if (rc) return rc;
+    return hist_enqueue(key, cfg, B, NK_max, d_ctm, M, d_bins, F, K, d_node, d_hist, d_count, st, s);
+  }
   for (int v = 0; v < num_nodes; ++v) {
-    pl_status rc = hist_pass(key, d_ctm, M, d_bins, F, K, d_node, num_nodes, v, B, d_hist, d_count, st, s);
+    pl_status rc = launch_set_desc(B.desc, num_nodes, K, v, s);
+    if (rc) return rc;
+    rc = hist_enqueue(key, cfg, B, NK_max, d_ctm, M, d_bins, F, K, d_node, d_hist, d_count, st, s);
     if (rc) return rc;
   }
   return PL_OK;

@@ -308,6 +308,11 @@ pl_status modexp_dispatch(int L, int T, int* grid_out, bool launch, const Modexp
 
 }  // namespace
 
+bool modexp_supported(int L, int T) {
+  return (L == 32 && (T == 2 || T == 4)) || (L == 64 && (T == 2 || T == 4 || T == 8)) ||
+         (L == 96 && (T == 4 || T == 8));
+}
+
 pl_status launch_encode(const float* d_v, size_t count, uint64_t* d_m, int* st, cudaStream_t s) {
   if (count == 0) return PL_OK;
   const int grid = (int)std::min<size_t>((count + 255) / 256, (size_t)sm_count() * 8);

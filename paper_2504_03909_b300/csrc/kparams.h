@@ -67,4 +67,13 @@ struct DecCrtParams {
   int pad;
 };
 
+// Size of one histogram pass, read by the kernels from device memory so that a
+// captured launch set can be replayed for levels with different node counts.
+struct HistDesc {
+  int num_nodes;  // nodes of the level (valid node ids are 0 .. num_nodes-1)
+  int NK;         // keys per feature: num_nodes * K, or K when only_node >= 0
+  int only_node;  // -1: all nodes; otherwise only this node (per-node comparator)
+  int pad;
+};
+
 }  // namespace pl

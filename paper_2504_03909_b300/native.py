@@ -48,7 +48,16 @@ SIGNATURES = {
     "paillier_launch_count": (C.c_ulonglong, []),
     "paillier_profile": (_i, [_i]),
     "paillier_profile_read": (_i, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "paillier_level_plan_create": (_i, [_vp, _sz, _i, _i, _i, C.POINTER(C.c_void_p)]),
+    "paillier_level_run": (_i, [_vp, _vp, _vp, _vp, _i, _vp, _vp, _vp]),
+    "paillier_level_plan_stats": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)]),
+    "paillier_level_plan_free": (None, [_vp]),
+    "paillier_get_config": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_i)]),
+    "paillier_set_config": (_i, [_vp, _i, _i, _i]),
+    "paillier_autotune": (_i, [_vp, _i, C.c_char_p, _vp, C.POINTER(_i), C.POINTER(_i)]),
 }
+
+OP_ENCRYPT, OP_DECRYPT, OP_HIST = 0, 1, 2
 
 _lib = None
 

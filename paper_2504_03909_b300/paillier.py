@@ -171,6 +171,62 @@ def decrypt_u64(key: Key, ct: torch.Tensor, out: torch.Tensor | None = None, str
     return out
 
 
+class LevelPlan:
+    """Batched tree-level path: one pass over all nodes of a level, captured
+    into a CUDA graph on the first run and replayed for later levels."""
+
+    def __init__(self, key: Key, M: int, F: int, K: int, max_nodes: int):
+        out = C.c_void_p()
+        call("paillier_level_plan_create", key.handle, M, F, K, max_nodes, C.byref(out))
+        self._h = out
+        self.key, self.M, self.F, self.K, self.max_nodes = key, M, F, K, max_nodes
+
+    def run(self, ctm: torch.Tensor, bins: torch.Tensor, node: torch.Tensor, num_nodes: int,
+            hist: torch.Tensor | None = None, count: torch.Tensor | None = None, stream=None):
+        L = self.key.L
+        assert ctm.shape == (2, self.M, 2 * L) and bins.shape == (self.F, self.M) and node.numel() == self.M
+        if hist is None:
+            hist = torch.empty((num_nodes, self.F, self.K, 2, 2 * L), dtype=torch.int32, device=ctm.device)
+        if count is None:
+            count = torch.empty((num_nodes, self.F, self.K), dtype=torch.int32, device=ctm.device)
+        call("paillier_level_run", self._h, _ptr(ctm), _ptr(bins), _ptr(node), num_nodes, _ptr(hist), _ptr(count),
+             _stream(stream))
+        return hist, count
+
+    def stats(self):
+        c, r, k = C.c_int(), C.c_int(), C.c_int()
+        call("paillier_level_plan_stats", self._h, C.byref(c), C.byref(r), C.byref(k))
+        return {"captures": c.value, "replays": r.value, "kernels": k.value}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().paillier_level_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def get_config(key: Key, op: int):
+    la, pa = C.c_int(), C.c_int()
+    call("paillier_get_config", key.handle, op, C.byref(la), C.byref(pa))
+    return la.value, pa.value
+
+
+def set_config(key: Key, op: int, lanes: int, param: int):
+    call("paillier_set_config", key.handle, op, lanes, param)
+
+
+def autotune(key: Key, op: int, cache_path: str | None = None, stream=None):
+    la, pa = C.c_int(), C.c_int()
+    call("paillier_autotune", key.handle, op, cache_path.encode() if cache_path else None, _stream(stream),
+         C.byref(la), C.byref(pa))
+    return la.value, pa.value
+
+
 def sync(stream=None) -> int:
     """Synchronise the stream and raise on a device-reported error; returns the raw status word."""
     st = C.c_int(0)
