@@ -142,8 +142,11 @@ pl_status paillier_hist_aggregate(const pl_key* key, const uint32_t* d_ctm, size
                                   uint32_t* d_hist, int32_t* d_count, void* stream);
 
 /* The same histogram computed the plain way: one set of launches per tree
- * node, each over the whole sample range with the other nodes masked out.
- * The comparator of the batched level path; results are identical. */
+ * node (each over the whole sample range with the other nodes masked out),
+ * and one work item -- one lane group multiplying all the cell's ciphertexts
+ * in sequence -- per cell.  The comparator of the batched level path, which
+ * splits cells into fixed-size chunks and runs all nodes in one pass; results
+ * are identical. */
 pl_status paillier_hist_aggregate_per_node(const pl_key* key, const uint32_t* d_ctm, size_t M,
                                            const uint8_t* d_bins, int F, int K,
                                            const int32_t* d_node, int num_nodes,

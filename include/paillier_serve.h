@@ -1,0 +1,96 @@
+/*
+ * paillier_serve.h -- a continuous-batching request loop for histogram +
+ * decryption jobs (the paper's secure vertical round, Sec. III.B: a passive
+ * party's encrypted histogram followed by the active party's decryption; the
+ * processor interface of Sec. III.D hands such buffers between parties).
+ *
+ * A server owns `slots` CUDA streams.  Submitted requests wait in a FIFO queue;
+ * a scheduler thread admits the head of the queue when a slot is free AND the
+ * request's device memory (outputs + scratch, allocated stream-ordered from
+ * the device's memory pool) fits under the HBM budget next to the requests
+ * already running.  Admitted requests run concurrently on their slots' streams
+ * and overlap on the GPU; a request's result is bit-identical whether it runs
+ * alone or in a mix.  Latency is measured from submit to the completion of the
+ * request's last copy (host clock, polled every few tens of microseconds).
+ *
+ * Ciphertexts stay resident on the device: a request points at Montgomery-form
+ * ciphertexts ([.., 2L], from paillier_ct_prepare) and bins already there.
+ */
+#ifndef PAILLIER_B300_SERVE_H
+#define PAILLIER_B300_SERVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "paillier.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pl_server pl_server;
+
+typedef struct pl_request {
+  /* Private key: the request covers the passive party's aggregation and the
+   * active party's decryption, both simulated in this process. */
+  const pl_key* key;
+  /* g rows at d_ctm[i * 2L], h rows at d_ctm[(gh_stride + i) * 2L], i < M
+   * (gh_stride >= M rows: a request may use the first M samples of a larger
+   * resident array). */
+  const uint32_t* d_ctm;
+  size_t gh_stride;
+  size_t M;
+  int F, K;                 /* 1 <= K <= 256 */
+  const uint8_t* d_bins;    /* bin of sample i in feature f at d_bins[f * bins_stride + i] */
+  size_t bins_stride;       /* >= M */
+  const int32_t* d_node;    /* [M] node ids (-1 skips), or NULL: every sample in node 0 */
+  int num_nodes;            /* >= 1 (1 when d_node is NULL) */
+  /* Host outputs (page-locked memory keeps the copies asynchronous):
+   * decrypted fixed-point sums [num_nodes][F][K][2] and counts [num_nodes][F][K]. */
+  uint64_t* h_sums;
+  int32_t* h_counts;
+} pl_request;
+
+#define PL_REQ_QUEUED    0
+#define PL_REQ_RUNNING   1
+#define PL_REQ_DONE      2
+#define PL_REQ_FAILED    3
+#define PL_REQ_CANCELLED 4
+
+/* Creates a server on the current device: `slots` >= 1 concurrent requests,
+ * at most hbm_budget bytes of request memory in flight. */
+pl_status pl_server_create(int slots, size_t hbm_budget, pl_server** out);
+
+/* Queues a request (arguments are checked here; PL_EBUSY if it can never fit
+ * the budget).  *ticket identifies it.  The request's device inputs and host
+ * outputs must stay valid until it completes. */
+pl_status pl_server_submit(pl_server* srv, const pl_request* req, uint64_t* ticket);
+
+/* State of a request (PL_REQ_*), its latency in ms once done (else -1) and,
+ * for a failed request, its error code in *error (may be NULL). */
+pl_status pl_server_poll(pl_server* srv, uint64_t ticket, int* state, double* latency_ms, int* error);
+
+/* Waits until the request is no longer queued or running, at most timeout_ms
+ * (PL_ETIMEDOUT if it still is).  *state and *latency_ms as in poll (may be NULL). */
+pl_status pl_server_wait(pl_server* srv, uint64_t ticket, int timeout_ms, int* state, double* latency_ms);
+
+/* Device memory the server reserves against its budget while the request
+ * runs (outputs and scratch), for sizing budgets. */
+pl_status pl_server_request_bytes(const pl_request* req, size_t* bytes);
+
+/* Cancels a request that is still queued (PL_EINVAL if it was admitted). */
+pl_status pl_server_cancel(pl_server* srv, uint64_t ticket);
+
+/* Counters: submitted, completed, failed, cancelled, peak concurrently
+ * running requests, peak bytes in flight. */
+pl_status pl_server_stats(pl_server* srv, long long* submitted, long long* completed, long long* failed,
+                          long long* cancelled, int* peak_running, size_t* peak_bytes);
+
+/* Waits for running requests, cancels queued ones and frees the server. */
+void pl_server_destroy(pl_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAILLIER_B300_SERVE_H */

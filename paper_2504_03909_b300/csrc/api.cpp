@@ -46,8 +46,20 @@ Scratch::~Scratch() {
   }
 }
 
-void* Scratch::get(size_t bytes) {
+void* Scratch::get(size_t bytes, cudaStream_t s) {
   if (bytes <= cap && ptr) return ptr;
+  if (async) {
+    if (ptr) cudaFreeAsync(ptr, s);
+    ptr = nullptr;
+    cap = 0;
+    if (cudaMallocAsync(&ptr, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      ptr = nullptr;
+      return nullptr;
+    }
+    cap = bytes;
+    return ptr;
+  }
   if (ptr) {
     cudaDeviceSynchronize();
     cudaFree(ptr);
@@ -67,6 +79,13 @@ void* Scratch::get(size_t bytes) {
   }
   cap = want;
   return ptr;
+}
+
+void Scratch::release(cudaStream_t s) {
+  if (ptr && async) cudaFreeAsync(ptr, s);
+  if (!async) return;
+  ptr = nullptr;
+  cap = 0;
 }
 
 int sm_count() {
@@ -239,7 +258,7 @@ static pl_status hist_common(const pl_key* key, const uint32_t* d_ctm, size_t M,
   if (!aligned16(d_hist) || (d_ctm && !aligned16(d_ctm))) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
   int* st = current_status();
   if (!st) return fail(PL_ECUDA, "no usable CUDA device");
-  return launch_hist(const_cast<pl_key*>(key), d_ctm, M, d_bins, F, K, d_node, num_nodes, d_hist, d_count,
+  return launch_hist(const_cast<pl_key*>(key), d_ctm, M, M, d_bins, M, F, K, d_node, num_nodes, d_hist, d_count,
                      per_node, st, static_cast<cudaStream_t>(stream));
 }
 

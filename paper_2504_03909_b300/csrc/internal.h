@@ -36,10 +36,16 @@ struct Scratch {
   int device = -1;
   void* ptr = nullptr;
   size_t cap = 0;
+  // stream-ordered mode (serving slots): grows with cudaFreeAsync /
+  // cudaMallocAsync on the caller's stream instead of synchronising the device
+  bool async = false;
+  cudaStream_t astream = nullptr;
   ~Scratch();
-  // returns a buffer of at least `bytes` (reallocates, synchronising the
-  // device, when it is too small); nullptr on failure
-  void* get(size_t bytes);
+  // returns a buffer of at least `bytes` (reallocates when it is too small);
+  // nullptr on failure
+  void* get(size_t bytes, cudaStream_t s = nullptr);
+  // stream-ordered release (async mode)
+  void release(cudaStream_t s);
 };
 
 // bump allocation inside one scratch request
@@ -57,6 +63,8 @@ struct ModexpCfg {
   int T = 4;  // lanes per instance
   int w = 5;  // window bits
 };
+// a tile this large never splits a cell: one work item per non-empty cell
+constexpr int kWholeCell = 1 << 30;
 struct AggCfg {
   int T = 8;      // lanes per instance (mod n^2)
   int tile = 64;  // ciphertexts per work item of the segmented product
@@ -94,13 +102,14 @@ namespace pl {
 pl_status launch_encode(const float* d_v, size_t count, uint64_t* d_m, int* st, cudaStream_t s);
 pl_status launch_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t count, double* d_out, cudaStream_t s);
 pl_status launch_encrypt(pl_key* key, const uint64_t* d_m, const uint32_t* d_r, size_t count, uint32_t* d_ct,
-                         cudaStream_t s);
+                         cudaStream_t s, Scratch* scratch = nullptr);
 pl_status launch_decrypt(pl_key* key, const uint32_t* d_ct, size_t count, void* d_out, bool u64, int* st,
-                         cudaStream_t s);
+                         cudaStream_t s, Scratch* scratch = nullptr);
+size_t decrypt_scratch_bytes(const pl_key* key, size_t count);
 pl_status launch_ct_prepare(pl_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_ctm, cudaStream_t s);
-pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t* d_bins, int F, int K,
-                      const int32_t* d_node, int num_nodes, uint32_t* d_hist, int32_t* d_count, bool per_node,
-                      int* st, cudaStream_t s);
+pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, size_t ghs, const uint8_t* d_bins,
+                      size_t bstride, int F, int K, const int32_t* d_node, int num_nodes, uint32_t* d_hist,
+                      int32_t* d_count, bool per_node, int* st, cudaStream_t s, Scratch* scratch = nullptr);
 int sm_count();
 
 // ---- histogram pass pieces shared with the level plan ----------------------
@@ -122,8 +131,8 @@ HistLayout hist_layout(size_t M, int F, int NK_max, int tile, int NL);
 HistBufs hist_bufs(const HistLayout& h, void* base);
 pl_status launch_set_desc(HistDesc* D, int num_nodes, int NK, int only_node, cudaStream_t s);
 pl_status hist_enqueue(const pl_key* key, const AggCfg& cfg, const HistBufs& B, int NK_max, const uint32_t* d_ctm,
-                       size_t M, const uint8_t* d_bins, int F, int K, const int32_t* d_node, uint32_t* d_hist,
-                       int32_t* d_count, int* st, cudaStream_t s);
+                       size_t M, size_t ghs, const uint8_t* d_bins, size_t bstride, int F, int K,
+                       const int32_t* d_node, uint32_t* d_hist, int32_t* d_count, int* st, cudaStream_t s);
 
 // ---- tracing: launch counter and optional per-kernel CUDA-event timing ----
 void note_launch();

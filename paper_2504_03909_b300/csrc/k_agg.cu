@@ -42,23 +42,23 @@ __global__ void k_set_desc(HistDesc* D, int num_nodes, int NK, int only_node) {
   D->pad = 0;
 }
 
-__global__ void k_hist_count(const uint8_t* __restrict__ bins, const int32_t* __restrict__ node, size_t M, int K,
-                             const HistDesc* __restrict__ D, int* __restrict__ cnt, int* status) {
+__global__ void k_hist_count(const uint8_t* __restrict__ bins, size_t bstride, const int32_t* __restrict__ node,
+                             size_t M, int K, const HistDesc* __restrict__ D, int* __restrict__ cnt, int* status) {
   const int f = blockIdx.y;
   const int num_nodes = D->num_nodes, only_node = D->only_node, NK = D->NK;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
-    const int key = hist_key(node[i], bins[(size_t)f * M + i], K, num_nodes, only_node, status);
+    const int key = hist_key(node[i], bins[(size_t)f * bstride + i], K, num_nodes, only_node, status);
     if (key >= 0) atomicAdd(&cnt[(size_t)f * NK + key], 1);
   }
 }
 
-__global__ void k_hist_scatter(const uint8_t* __restrict__ bins, const int32_t* __restrict__ node, size_t M, int K,
-                               const HistDesc* __restrict__ D, const int* __restrict__ off,
+__global__ void k_hist_scatter(const uint8_t* __restrict__ bins, size_t bstride, const int32_t* __restrict__ node,
+                               size_t M, int K, const HistDesc* __restrict__ D, const int* __restrict__ off,
                                int* __restrict__ cursor, int* __restrict__ idx, int* status) {
   const int f = blockIdx.y;
   const int num_nodes = D->num_nodes, only_node = D->only_node, NK = D->NK;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
-    const int key = hist_key(node[i], bins[(size_t)f * M + i], K, num_nodes, only_node, status);
+    const int key = hist_key(node[i], bins[(size_t)f * bstride + i], K, num_nodes, only_node, status);
     if (key >= 0) {
       const int pos = off[(size_t)f * (NK + 1) + key] + atomicAdd(&cursor[(size_t)f * NK + key], 1);
       idx[(size_t)f * M + pos] = (int)i;
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kBlock) k_to_mont(const __grid_constant__ N2Co
 // Segmented product over the work list of chunks.  Item = (chunk, g/h).
 template <int S, int T>
 __global__ void __launch_bounds__(kBlock) k_seg_product(const __grid_constant__ N2Const P,
-                                                        const uint32_t* __restrict__ ctm, size_t M,
+                                                        const uint32_t* __restrict__ ctm, size_t M, size_t ghs,
                                                         const int* __restrict__ idx, const int* __restrict__ off,
                                                         const int* __restrict__ choff,
                                                         const int* __restrict__ featoff, int F,
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kBlock) k_seg_product(const __grid_constant__ 
       const int* o = off + (size_t)f * (NK + 1);
       const int j0 = o[key] + (local - co[key]) * tile;
       len = min(tile, o[key + 1] - j0);
-      src = ctm + (size_t)gh * M * NL;
+      src = ctm + (size_t)gh * ghs * NL;
       ids = idx + (size_t)f * M + j0;
     }
     const int maxlen = __reduce_max_sync(kFull, len);
@@ -338,15 +338,16 @@ pl_status run_prepare(const N2Const& P, const uint32_t* ct, size_t count, uint32
 }
 
 template <int S, int T>
-pl_status run_hist_products(const N2Const& P, const uint32_t* ctm, size_t M, const HistBufs& B, const HistDesc* D,
-                            int F, int NK_max, int K, int tile, uint32_t* hist, int32_t* count_out, cudaStream_t s) {
+pl_status run_hist_products(const N2Const& P, const uint32_t* ctm, size_t M, size_t ghs, const HistBufs& B,
+                            const HistDesc* D, int F, int NK_max, int K, int tile, uint32_t* hist, int32_t* count_out,
+                            cudaStream_t s) {
   const size_t smem = (size_t)S * T * (kBlock / T) * sizeof(uint32_t);
   static int grid_seg = 0, grid_comb = 0;
   if (!grid_seg) grid_seg = occupancy_grid<S, T>((const void*)k_seg_product<S, T>, smem);
   if (!grid_comb) grid_comb = occupancy_grid<S, T>((const void*)k_combine<S, T>, smem);
   {
     ProfScope _ps("seg_product", s);
-    k_seg_product<S, T><<<grid_seg, kBlock, smem, s>>>(P, ctm, M, B.idx, B.off, B.choff, B.featoff, F, D, tile,
+    k_seg_product<S, T><<<grid_seg, kBlock, smem, s>>>(P, ctm, M, ghs, B.idx, B.off, B.choff, B.featoff, F, D, tile,
                                                        B.partial);
   }
   PL_CUDA_TRY(cudaGetLastError());
@@ -373,12 +374,12 @@ pl_status dispatch_prepare(int NL, int T, const N2Const& P, const uint32_t* ct, 
   return fail(PL_EINVAL, "no mod n^2 kernel for this (limbs, lanes) pair");
 }
 
-pl_status dispatch_products(int NL, int T, const N2Const& P, const uint32_t* ctm, size_t M, const HistBufs& B,
-                            const HistDesc* D, int F, int NK_max, int K, int tile, uint32_t* hist,
+pl_status dispatch_products(int NL, int T, const N2Const& P, const uint32_t* ctm, size_t M, size_t ghs,
+                            const HistBufs& B, const HistDesc* D, int F, int NK_max, int K, int tile, uint32_t* hist,
                             int32_t* count_out, cudaStream_t s) {
 #define PL_CASE(LL, TT)                                                                                   \
   if (NL == LL && T == TT)                                                                                \
-    return run_hist_products<LL / TT, TT>(P, ctm, M, B, D, F, NK_max, K, tile, hist, count_out, s);
+    return run_hist_products<LL / TT, TT>(P, ctm, M, ghs, B, D, F, NK_max, K, tile, hist, count_out, s);
   PL_N2_CASES(PL_CASE)
 #undef PL_CASE
   return fail(PL_EINVAL, "no mod n^2 kernel for this (limbs, lanes) pair");
@@ -428,15 +429,15 @@ pl_status launch_set_desc(HistDesc* D, int num_nodes, int NK, int only_node, cud
 // One group-by + segmented product + combine; the node selection and NK come
 // from B.desc on the device, buffers are sized for NK_max.
 pl_status hist_enqueue(const pl_key* key, const AggCfg& cfg, const HistBufs& B, int NK_max, const uint32_t* d_ctm,
-                       size_t M, const uint8_t* d_bins, int F, int K, const int32_t* d_node, uint32_t* d_hist,
-                       int32_t* d_count, int* st, cudaStream_t s) {
+                       size_t M, size_t ghs, const uint8_t* d_bins, size_t bstride, int F, int K,
+                       const int32_t* d_node, uint32_t* d_hist, int32_t* d_count, int* st, cudaStream_t s) {
   const int tile = cfg.tile;
   PL_CUDA_TRY(cudaMemsetAsync(B.cnt, 0, sizeof(int) * (size_t)F * NK_max, s));
   const int gx = (int)std::min<size_t>((M + 255) / 256, 1024);
   dim3 grid(gx > 0 ? gx : 1, F);
   {
     ProfScope _ps("hist_count", s);
-    k_hist_count<<<grid, 256, 0, s>>>(d_bins, d_node, M, K, B.desc, B.cnt, st);
+    k_hist_count<<<grid, 256, 0, s>>>(d_bins, bstride, d_node, M, K, B.desc, B.cnt, st);
   }
   PL_CUDA_TRY(cudaGetLastError());
   {
@@ -452,10 +453,11 @@ pl_status hist_enqueue(const pl_key* key, const AggCfg& cfg, const HistBufs& B, 
   PL_CUDA_TRY(cudaMemsetAsync(B.cnt, 0, sizeof(int) * (size_t)F * NK_max, s));
   {
     ProfScope _ps("hist_scatter", s);
-    k_hist_scatter<<<grid, 256, 0, s>>>(d_bins, d_node, M, K, B.desc, B.off, B.cnt, B.idx, st);
+    k_hist_scatter<<<grid, 256, 0, s>>>(d_bins, bstride, d_node, M, K, B.desc, B.off, B.cnt, B.idx, st);
   }
   PL_CUDA_TRY(cudaGetLastError());
-  return dispatch_products(2 * key->L, cfg.T, key->n2c, d_ctm, M, B, B.desc, F, NK_max, K, tile, d_hist, d_count, s);
+  return dispatch_products(2 * key->L, cfg.T, key->n2c, d_ctm, M, ghs, B, B.desc, F, NK_max, K, tile, d_hist,
+                           d_count, s);
 }
 
 pl_status launch_ct_prepare(pl_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_ctm, cudaStream_t s) {
@@ -463,26 +465,29 @@ pl_status launch_ct_prepare(pl_key* key, const uint32_t* d_ct, size_t count, uin
   return dispatch_prepare(2 * key->L, key->agg_cfg.T, key->n2c, d_ct, count, d_ctm, s);
 }
 
-pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t* d_bins, int F, int K,
-                      const int32_t* d_node, int num_nodes, uint32_t* d_hist, int32_t* d_count, bool per_node,
-                      int* st, cudaStream_t s) {
+pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, size_t ghs, const uint8_t* d_bins,
+                      size_t bstride, int F, int K, const int32_t* d_node, int num_nodes, uint32_t* d_hist,
+                      int32_t* d_count, bool per_node, int* st, cudaStream_t s, Scratch* scratch) {
   const AggCfg cfg = key->agg_cfg;
   const int NK_max = per_node ? K : num_nodes * K;
-  const HistLayout h = hist_layout(M, F, NK_max, cfg.tile, 2 * key->L);
-  Scratch* sc = key->scratch_for_current_device();
+  const HistLayout h = hist_layout(M, F, NK_max, per_node ? kWholeCell : cfg.tile, 2 * key->L);
+  Scratch* sc = scratch ? scratch : key->scratch_for_current_device();
   if (!sc) return fail(PL_ECUDA, "no current device");
-  void* base = sc->get(h.bytes);
+  void* base = sc->get(h.bytes, s);
   if (!base) return fail(PL_ENOMEM, "scratch allocation failed");
   const HistBufs B = hist_bufs(h, base);
   if (!per_node) {
     pl_status rc = launch_set_desc(B.desc, num_nodes, num_nodes * K, -1, s);
     if (rc) return rc;
-    return hist_enqueue(key, cfg, B, NK_max, d_ctm, M, d_bins, F, K, d_node, d_hist, d_count, st, s);
+    return hist_enqueue(key, cfg, B, NK_max, d_ctm, M, ghs, d_bins, bstride, F, K, d_node, d_hist, d_count, st, s);
   }
+  // the plain per-node method: one set of launches per node and one work
+  // item (one lane group) per whole cell, no splitting of large cells
+  const AggCfg plain{cfg.T, kWholeCell};
   for (int v = 0; v < num_nodes; ++v) {
     pl_status rc = launch_set_desc(B.desc, num_nodes, K, v, s);
     if (rc) return rc;
-    rc = hist_enqueue(key, cfg, B, NK_max, d_ctm, M, d_bins, F, K, d_node, d_hist, d_count, st, s);
+    rc = hist_enqueue(key, plain, B, NK_max, d_ctm, M, ghs, d_bins, bstride, F, K, d_node, d_hist, d_count, st, s);
     if (rc) return rc;
   }
   return PL_OK;

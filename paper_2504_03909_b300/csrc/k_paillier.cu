@@ -338,7 +338,7 @@ pl_status launch_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t count,
 // Shared by encrypt and decrypt: scratch = y [2][count][L] + window tables.
 template <bool DEC>
 static pl_status modexp_phase(pl_key* key, const ModexpCfg& cfg, const uint32_t* in, const uint64_t* msg,
-                              size_t count, uint32_t** y_out, cudaStream_t s) {
+                              size_t count, uint32_t** y_out, cudaStream_t s, Scratch* scratch) {
   const ModexpParams* P = key->modexp_params(DEC, cfg.w);
   if (!P) return fail(PL_EINVAL, "unsupported window width");
   const int L = key->L;
@@ -354,9 +354,9 @@ static pl_status modexp_phase(pl_key* key, const ModexpCfg& cfg, const uint32_t*
   Carve cv;
   const size_t off_y = cv.take((size_t)2 * count * L * sizeof(uint32_t));
   const size_t off_t = cv.take((size_t)grid * ipb * ((size_t)1 << cfg.w) * L * sizeof(uint32_t));
-  Scratch* sc = key->scratch_for_current_device();
+  Scratch* sc = scratch ? scratch : key->scratch_for_current_device();
   if (!sc) return fail(PL_ECUDA, "no current device");
-  char* base = static_cast<char*>(sc->get(cv.off));
+  char* base = static_cast<char*>(sc->get(cv.off, s));
   if (!base) return fail(PL_ENOMEM, "scratch allocation failed");
   uint32_t* y = reinterpret_cast<uint32_t*>(base + off_y);
   uint32_t* tbl = reinterpret_cast<uint32_t*>(base + off_t);
@@ -366,10 +366,10 @@ static pl_status modexp_phase(pl_key* key, const ModexpCfg& cfg, const uint32_t*
 }
 
 pl_status launch_encrypt(pl_key* key, const uint64_t* d_m, const uint32_t* d_r, size_t count, uint32_t* d_ct,
-                         cudaStream_t s) {
+                         cudaStream_t s, Scratch* scratch) {
   if (count == 0) return PL_OK;
   uint32_t* y = nullptr;
-  pl_status rc = modexp_phase<false>(key, key->enc_cfg, d_r, d_m, count, &y, s);
+  pl_status rc = modexp_phase<false>(key, key->enc_cfg, d_r, d_m, count, &y, s, scratch);
   if (rc) return rc;
   {
     ProfScope _ps("enc_crt", s);
@@ -379,11 +379,29 @@ pl_status launch_encrypt(pl_key* key, const uint64_t* d_m, const uint32_t* d_r, 
   return PL_OK;
 }
 
+size_t decrypt_scratch_bytes(const pl_key* key, size_t count) {
+  // the same carve as modexp_phase<true>: y [2][count][L] plus the window
+  // tables of the grid that launch will use
+  const ModexpCfg cfg = key->dec_cfg;
+  const int L = key->L;
+  int grid = 0;
+  if (modexp_dispatch<true>(L, cfg.T, &grid, false, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr)) return 0;
+  const size_t ipw = 32 / (size_t)cfg.T;
+  const size_t warps_needed = 2 * ((count + ipw - 1) / ipw);
+  const size_t blocks_needed = (warps_needed + (kBlock / 32) - 1) / (kBlock / 32);
+  if ((size_t)grid > blocks_needed) grid = (int)blocks_needed;
+  const size_t ipb = kBlock / cfg.T;
+  Carve cv;
+  cv.take((size_t)2 * count * L * sizeof(uint32_t));
+  cv.take((size_t)grid * ipb * ((size_t)1 << cfg.w) * L * sizeof(uint32_t));
+  return cv.off;
+}
+
 pl_status launch_decrypt(pl_key* key, const uint32_t* d_ct, size_t count, void* d_out, bool u64, int* st,
-                         cudaStream_t s) {
+                         cudaStream_t s, Scratch* scratch) {
   if (count == 0) return PL_OK;
   uint32_t* y = nullptr;
-  pl_status rc = modexp_phase<true>(key, key->dec_cfg, d_ct, nullptr, count, &y, s);
+  pl_status rc = modexp_phase<true>(key, key->dec_cfg, d_ct, nullptr, count, &y, s, scratch);
   if (rc) return rc;
   const unsigned grid = (unsigned)((count + kBlock - 1) / kBlock);
   if (u64)

@@ -93,8 +93,8 @@ pl_status paillier_level_run(pl_level_plan* plan, const uint32_t* d_ctm, const u
     const unsigned long long before = paillier_launch_count();
     e = cudaStreamBeginCapture(plan->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    rc = hist_enqueue(plan->key, plan->cfg, plan->B, plan->NK_max, d_ctm, plan->M, d_bins, plan->F, plan->K, d_node,
-                      d_hist, d_count, st, plan->cap);
+    rc = hist_enqueue(plan->key, plan->cfg, plan->B, plan->NK_max, d_ctm, plan->M, plan->M, d_bins, plan->M,
+                      plan->F, plan->K, d_node, d_hist, d_count, st, plan->cap);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(plan->cap, &g);
     // kernels are counted when a replay launches them, not when they are captured

@@ -177,7 +177,7 @@ pl_status paillier_autotune(pl_key* key, int op, const char* cache_path, void* s
     for (const Cand& c : cands) {
       const AggCfg cfg{c.lanes, c.param};
       auto run = [&] {
-        return hist_enqueue(key, cfg, B, (int)K, ctm, M, bins, (int)F, (int)K, node, hist, nullptr, st, s);
+        return hist_enqueue(key, cfg, B, (int)K, ctm, M, M, bins, M, (int)F, (int)K, node, hist, nullptr, st, s);
       };
       rc = run();
       if (rc) break;

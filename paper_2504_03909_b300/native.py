@@ -59,6 +59,26 @@ SIGNATURES = {
 
 OP_ENCRYPT, OP_DECRYPT, OP_HIST = 0, 1, 2
 
+class Request(C.Structure):
+    """pl_request of include/paillier_serve.h."""
+    _fields_ = [("key", C.c_void_p), ("d_ctm", C.c_void_p), ("gh_stride", C.c_size_t), ("M", C.c_size_t),
+                ("F", C.c_int), ("K", C.c_int), ("d_bins", C.c_void_p), ("bins_stride", C.c_size_t),
+                ("d_node", C.c_void_p), ("num_nodes", C.c_int), ("h_sums", C.c_void_p), ("h_counts", C.c_void_p)]
+
+
+SIGNATURES.update({
+    "pl_server_create": (_i, [_i, _sz, C.POINTER(C.c_void_p)]),
+    "pl_server_submit": (_i, [_vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "pl_server_poll": (_i, [_vp, C.c_uint64, C.POINTER(_i), C.POINTER(C.c_double), C.POINTER(_i)]),
+    "pl_server_wait": (_i, [_vp, C.c_uint64, _i, C.POINTER(_i), C.POINTER(C.c_double)]),
+    "pl_server_cancel": (_i, [_vp, C.c_uint64]),
+    "pl_server_request_bytes": (_i, [C.POINTER(Request), C.POINTER(_sz)]),
+    "pl_server_stats": (_i, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                             C.POINTER(C.c_longlong), C.POINTER(_i), C.POINTER(_sz)]),
+    "pl_server_destroy": (None, [_vp]),
+})
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
+
 _lib = None
 
 

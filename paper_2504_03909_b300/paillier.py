@@ -210,6 +210,76 @@ class LevelPlan:
             pass
 
 
+class Server:
+    """Continuous-batching request loop (histogram + decryption jobs)."""
+
+    def __init__(self, slots: int, hbm_budget: int):
+        out = C.c_void_p()
+        call("pl_server_create", slots, hbm_budget, C.byref(out))
+        self._h = out
+        self._keep = {}
+
+    def submit(self, key: Key, ctm: torch.Tensor, M: int, F: int, K: int, bins: torch.Tensor,
+               node: torch.Tensor | None = None, num_nodes: int = 1, gh_stride: int | None = None,
+               bins_stride: int | None = None):
+        """Queues a request over the first M samples / F features of resident
+        arrays; returns (ticket, host sums [num_nodes, F, K, 2] uint64 (pinned),
+        host counts [num_nodes, F, K] int32 (pinned))."""
+        sums = torch.empty((num_nodes, F, K, 2), dtype=torch.int64).pin_memory()
+        counts = torch.empty((num_nodes, F, K), dtype=torch.int32).pin_memory()
+        req = native.Request(key.handle.value, _ptr(ctm), gh_stride if gh_stride is not None else M, M, F, K,
+                             _ptr(bins), bins_stride if bins_stride is not None else M,
+                             _ptr(node) if node is not None else None, num_nodes, sums.data_ptr(), counts.data_ptr())
+        t = C.c_uint64()
+        call("pl_server_submit", self._h, C.byref(req), C.byref(t))
+        self._keep[t.value] = (sums, counts, ctm, bins, node, key)
+        return t.value, sums, counts
+
+    @staticmethod
+    def request_bytes(key: Key, ctm: torch.Tensor, M: int, F: int, K: int, bins: torch.Tensor,
+                      node: torch.Tensor | None = None, num_nodes: int = 1) -> int:
+        req = native.Request(key.handle.value, _ptr(ctm), M, M, F, K, _ptr(bins), M,
+                             _ptr(node) if node is not None else None, num_nodes, 0, 0)
+        b = C.c_size_t()
+        call("pl_server_request_bytes", C.byref(req), C.byref(b))
+        return b.value
+
+    def poll(self, ticket: int):
+        st, lat, err = C.c_int(), C.c_double(), C.c_int()
+        call("pl_server_poll", self._h, ticket, C.byref(st), C.byref(lat), C.byref(err))
+        return st.value, lat.value, err.value
+
+    def wait(self, ticket: int, timeout_ms: int = 600_000):
+        st, lat = C.c_int(), C.c_double()
+        call("pl_server_wait", self._h, ticket, timeout_ms, C.byref(st), C.byref(lat))
+        return st.value, lat.value
+
+    def cancel(self, ticket: int):
+        call("pl_server_cancel", self._h, ticket)
+
+    def stats(self):
+        a, b, c, d = C.c_longlong(), C.c_longlong(), C.c_longlong(), C.c_longlong()
+        pr, pb = C.c_int(), C.c_size_t()
+        call("pl_server_stats", self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(pr), C.byref(pb))
+        return {"submitted": a.value, "completed": b.value, "failed": c.value, "cancelled": d.value,
+                "peak_running": pr.value, "peak_bytes": pb.value}
+
+    def release(self, ticket: int):
+        self._keep.pop(ticket, None)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().pl_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def get_config(key: Key, op: int):
     la, pa = C.c_int(), C.c_int()
     call("paillier_get_config", key.handle, op, C.byref(la), C.byref(pa))

@@ -1,0 +1,139 @@
+"""GPU tests of the serving loop: concurrent (continuous-batching) execution
+gives every request the same bits as running it alone and as the direct API;
+admission respects the HBM budget; queued requests can be cancelled; a bad
+request fails on its own without disturbing the others."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2504_03909_b300 import native, paillier as P, synth
+
+pytestmark = pytest.mark.gpu
+
+MFULL, FFULL = 3000, 6
+
+
+def _dataset(n_bits, seed):
+    p, q = synth.gen_primes(n_bits, seed)
+    key = P.Key.from_primes(n_bits, p, q)
+    gh = synth.gen_gh(MFULL, seed + 10)
+    r = synth.gen_r(p * q, n_bits, 2 * MFULL, seed + 10, p, q)
+    m = P.encode(torch.from_numpy(gh.reshape(-1)).cuda())
+    ct = P.encrypt(key, m, P.to_limb_tensor(r))
+    ctm = P.ct_prepare(key, ct.view(2, MFULL, -1))
+    bins = {K: torch.from_numpy(synth.gen_bins_uniform(FFULL, MFULL, K, seed + K)).cuda() for K in (8, 16)}
+    node = torch.from_numpy(synth.gen_tree_levels(MFULL, 3, seed)[2]).cuda()
+    P.sync()
+    return dict(key=key, ctm=ctm, bins=bins, node=node, m=m.cpu().numpy().view(np.uint64))
+
+
+@pytest.fixture(scope="module")
+def data():
+    return {1024: _dataset(1024, 1), 2048: _dataset(2048, 2)}
+
+
+REQUESTS = [  # (n_bits, M, F, K, use_node)
+    (1024, 3000, 6, 16, False), (2048, 1200, 4, 8, False), (1024, 17, 2, 8, True), (2048, 3000, 6, 16, True),
+    (1024, 2500, 5, 16, True), (2048, 1, 1, 8, False), (1024, 999, 3, 8, False), (2048, 2047, 6, 16, False),
+]
+
+
+def _submit(srv, data, req):
+    nb, M, F, K, use_node = req
+    d = data[nb]
+    node = d["node"] if use_node else None
+    return srv.submit(d["key"], d["ctm"], M, F, K, d["bins"][K], node=node, num_nodes=4 if use_node else 1,
+                      gh_stride=MFULL, bins_stride=MFULL)
+
+
+def _direct(data, req):
+    nb, M, F, K, use_node = req
+    d = data[nb]
+    ctm = d["ctm"][:, :M].contiguous()
+    bins = d["bins"][K][:F, :M].contiguous()
+    nn = 4 if use_node else 1
+    node = d["node"][:M].contiguous() if use_node else torch.zeros(M, dtype=torch.int32, device="cuda")
+    h, c = P.hist_aggregate(d["key"], ctm, bins, node, nn, K)
+    s = P.decrypt_u64(d["key"], h.reshape(-1, 2 * d["key"].L))
+    P.sync()
+    return s.view(nn, F, K, 2).cpu(), c.cpu()
+
+
+def test_mix_equals_alone_equals_direct(data):
+    mix = P.Server(slots=4, hbm_budget=8 << 30)
+    tickets = [_submit(mix, data, rq) for rq in REQUESTS]
+    got_mix = []
+    for t, s, c in tickets:
+        st, lat = mix.wait(t)
+        assert st == native.REQ_DONE and lat > 0
+        got_mix.append((s.clone(), c.clone()))
+    stats = mix.stats()
+    mix.close()
+    assert stats["completed"] == len(REQUESTS) and stats["peak_running"] >= 2
+    alone = P.Server(slots=1, hbm_budget=8 << 30)
+    for rq, (sm, cm) in zip(REQUESTS, got_mix):
+        t, s, c = _submit(alone, data, rq)
+        assert alone.wait(t)[0] == native.REQ_DONE
+        assert torch.equal(s, sm) and torch.equal(c, cm)
+        sd, cd = _direct(data, rq)
+        assert torch.equal(s, sd) and torch.equal(c, cd)
+    alone.close()
+
+
+def test_served_sums_equal_plaintext_histogram(data):
+    srv = P.Server(slots=2, hbm_budget=4 << 30)
+    rq = (1024, 2500, 5, 16, True)
+    t, s, c = _submit(srv, data, rq)
+    assert srv.wait(t)[0] == native.REQ_DONE
+    d = data[1024]
+    m = d["m"]
+    node = d["node"].cpu().numpy()[:2500]
+    bins = d["bins"][16].cpu().numpy()[:5, :2500]
+    sums, counts = oracle.plain_histogram(m[:MFULL][:2500], m[MFULL:][:2500], bins, node, 4, 16)
+    assert s.numpy().view(np.uint64).reshape(-1).tolist() == [
+        sums[v][f][b][k] for v in range(4) for f in range(5) for b in range(16) for k in range(2)]
+    assert c.numpy().reshape(-1).tolist() == [counts[v][f][b] for v in range(4) for f in range(5) for b in range(16)]
+    srv.close()
+
+
+def test_budget_admission_limits_concurrency(data):
+    # a budget that fits one request of this size but not two
+    big = (1024, 3000, 6, 16, False)
+    d = data[1024]
+    need = P.Server.request_bytes(d["key"], d["ctm"], 3000, 6, 16, d["bins"][16])
+    assert need > 0
+    srv = P.Server(slots=4, hbm_budget=need + need // 2)
+    ts = [_submit(srv, data, big) for _ in range(3)]
+    for t, _, _ in ts:
+        assert srv.wait(t)[0] == native.REQ_DONE
+    assert srv.stats()["peak_running"] == 1
+    srv.close()
+    tiny = P.Server(slots=2, hbm_budget=need // 2)
+    with pytest.raises(native.PaillierError) as e:
+        _submit(tiny, data, big)
+    assert e.value.code == native.PL_EBUSY
+    tiny.close()
+
+
+def test_cancel_and_isolated_failure(data):
+    srv = P.Server(slots=1, hbm_budget=8 << 30)
+    t1, s1, c1 = _submit(srv, data, (2048, 3000, 6, 16, False))
+    t2, _, _ = _submit(srv, data, (2048, 3000, 6, 16, False))
+    srv.cancel(t2)
+    assert srv.poll(t2)[0] == native.REQ_CANCELLED
+    # a request whose bins exceed its K fails alone; the next request is unaffected
+    d = data[1024]
+    t3, _, _ = srv.submit(d["key"], d["ctm"], 500, 3, 8, d["bins"][16], gh_stride=MFULL, bins_stride=MFULL)
+    t4, s4, c4 = _submit(srv, data, (1024, 999, 3, 8, False))
+    assert srv.wait(t1)[0] == native.REQ_DONE
+    st3 = srv.wait(t3)[0]
+    assert st3 == native.REQ_FAILED and srv.poll(t3)[2] == native.PL_EDEVICE
+    assert srv.wait(t4)[0] == native.REQ_DONE
+    sd, cd = _direct(data, (1024, 999, 3, 8, False))
+    assert torch.equal(s4, sd) and torch.equal(c4, cd)
+    st = srv.stats()
+    assert st["failed"] == 1 and st["cancelled"] == 1 and st["completed"] == 2
+    srv.close()
+    P.sync()  # the library's own status word is untouched by served requests
