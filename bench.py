@@ -417,7 +417,7 @@ def run_batched(args, cfg):
     dev = torch.device("cuda", local)
     M, F, K, n_bits, depth = cfg["M"], cfg["F"], cfg["K"], cfg["n_bits"], cfg["depth"]
     L = n_bits // 32
-    data_cfg = dict(cfg, seed=cfg["data_seed"])
+    data_cfg = dict(cfg, seed=cfg.get("data_seed", cfg["seed"]))
     p, q, gh, r, bins = make_inputs(data_cfg)
     levels = synth.gen_tree_levels(M, depth, cfg["seed"])
     key = P.Key.from_primes(n_bits, p, q)
@@ -485,9 +485,11 @@ def run_batched(args, cfg):
                 prof[kname] = tot.value / args.steps
             native.call("paillier_profile", 0)
             hist_levels(False)
-            hist_levels(True)
             t_batched = timed(lambda: hist_levels(False), args.steps)
-            t_per_node = timed(lambda: hist_levels(True), args.steps)
+            t_per_node = None
+            if not args.no_compare:
+                hist_levels(True)
+                t_per_node = timed(lambda: hist_levels(True), args.steps)
         P.sync(stream)
     ct_mults = 0
     strict = 0
@@ -499,14 +501,15 @@ def run_batched(args, cfg):
         "metric": METRIC, "value": ct_mults / t_batched, "unit": "ct-mults/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tree, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "batched: depth-6 tree (63 split nodes, Beta(0.5,0.5) splits) on 250,000 samples x "
-                               "30 features x 256 bins, 2048-bit n; step = encrypt + per-level histograms + CRT "
-                               "decrypt of every level's cells", "M": M, "F": F, "K": K, "n_bits": n_bits,
+        "config": {"workload": f"{args.config}: depth-{depth} tree ({(1 << depth) - 1} nodes, Beta(0.5,0.5) "
+                               f"splits) on {M:,} samples x {F} features x {K} bins, {n_bits}-bit n; step = encrypt "
+                               "+ per-level histograms + CRT decrypt of every level's cells",
+                   "M": M, "F": F, "K": K, "n_bits": n_bits,
                    "depth": depth, "autotuned": bool(args.autotune),
                    "configs": {op: P.get_config(key, i) for i, op in enumerate(("encrypt", "decrypt", "hist"))}},
         "hist_batched_ms_per_tree": 1e3 * t_batched,
-        "hist_per_node_ms_per_tree": 1e3 * t_per_node,
-        "batched_speedup_vs_per_node": t_per_node / t_batched,
+        "hist_per_node_ms_per_tree": 1e3 * t_per_node if t_per_node else None,
+        "batched_speedup_vs_per_node": t_per_node / t_batched if t_per_node else None,
         "ct_mults_per_tree": ct_mults,
         "tree_ms": 1e3 * t_tree,
         "phases_ms_per_tree": {"encrypt": prof["modexp_enc"] + prof["enc_crt"], "prepare": prof["to_mont"],
@@ -520,20 +523,128 @@ def run_batched(args, cfg):
         print(json.dumps(line), flush=True)
 
 
+def run_serving(args, cfg):
+    """Four simulated passive parties send Poisson-arriving histogram + decrypt
+    requests (M log-uniform in [1e3, 1e6], F uniform in [8, 64], K uniform on
+    {64, 96, ..., 256}, 2048- or 3072-bit key with p = 0.5) to one server; the
+    ciphertexts and bins stay resident.  Offered load = --load x the capacity
+    measured with a closed loop first.  Reports p50/p99 latency and throughput."""
+    import random as pyrandom
+    import threading as th
+    import torch
+    from paper_2504_03909_b300 import native, paillier as P
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    MMAX, FMAX, NUNIQ = 1_000_000, 64, 65_536
+    keys, ctms = {}, {}
+    for n_bits, seed in ((2048, 41), (3072, 42)):
+        p, q = synth.gen_primes(n_bits, seed)
+        key = P.Key.from_primes(n_bits, p, q)
+        L = n_bits // 32
+        gh = synth.gen_gh(NUNIQ, seed)
+        r = synth.gen_r(p * q, n_bits, 2 * NUNIQ, seed, p, q)
+        m = P.encode(torch.from_numpy(gh.reshape(-1)).to(dev))
+        ct = P.encrypt(key, m, P.to_limb_tensor(r, dev)).view(2, NUNIQ, 2 * L)
+        # the resident dataset repeats the NUNIQ encrypted samples up to MMAX rows
+        full = ct.repeat(1, (MMAX + NUNIQ - 1) // NUNIQ, 1)[:, :MMAX].contiguous()
+        keys[n_bits] = key
+        ctms[n_bits] = P.ct_prepare(key, full)
+        del ct, full
+    kgrid = list(range(64, 257, 32))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4)
+    bins = [{K: torch.randint(0, K, (FMAX, MMAX), generator=gen, device=dev, dtype=torch.uint8) for K in kgrid}
+            for _ in range(4)]
+    P.sync()
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * 0.5)
+    rng = pyrandom.Random(4)
+
+    def draw():
+        nb = 2048 if rng.random() < 0.5 else 3072
+        M = int(round(10 ** rng.uniform(3, 6)))
+        return dict(nb=nb, party=rng.randrange(4), M=M, F=rng.randint(8, 64), K=rng.choice(kgrid))
+
+    def submit(srv, rq):
+        return srv.submit(keys[rq["nb"]], ctms[rq["nb"]], rq["M"], rq["F"], rq["K"], bins[rq["party"]][rq["K"]],
+                          gh_stride=MMAX, bins_stride=MMAX)
+
+    srv = P.Server(slots=args.slots, hbm_budget=budget)
+    # warm-up and closed-loop capacity (requests/s with every slot busy)
+    warm = [draw() for _ in range(max(2 * args.slots, 8))]
+    for rq in warm[:args.slots]:
+        t, _, _ = submit(srv, rq)
+        srv.wait(t)
+    t0 = time.perf_counter()
+    tick = [submit(srv, rq)[0] for rq in warm]
+    for t in tick:
+        srv.wait(t)
+    capacity = len(warm) / (time.perf_counter() - t0)
+    rate = args.load * capacity
+    reqs = [draw() for _ in range(args.requests)]
+    gaps = [rng.expovariate(rate) for _ in reqs]
+    done_lat = []
+    tickets = []
+    with ClockSampler(0) as clk:
+        t_start = time.perf_counter()
+        t_next = t_start
+        for rq, g in zip(reqs, gaps):
+            t_next += g
+            dt = t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(submit(srv, rq)[0])
+        for t in tickets:
+            st, lat = srv.wait(t)
+            if st == native.REQ_DONE:
+                done_lat.append(lat)
+            srv.release(t)
+        wall = time.perf_counter() - t_start
+    stats = srv.stats()
+    srv.close()
+    lat = np.array(done_lat)
+    work_mults = sum(2 * rq["M"] * rq["F"] for rq in reqs)
+    work_cells = sum(2 * rq["F"] * rq["K"] for rq in reqs)
+    line = {
+        "metric": METRIC, "value": float(np.percentile(lat, 50)), "unit": "ms (p50 request latency)", "n_gpus": 1,
+        "steps": args.requests, "warmup": len(warm), "ms_per_step": 1e3 * wall / args.requests,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "serving: 4 passive parties, Poisson arrivals, histogram + CRT-decrypt requests, "
+                               "M log-uniform [1e3, 1e6], F uniform [8, 64], K uniform {64..256 step 32}, "
+                               "2048/3072-bit keys p = 0.5, resident ciphertexts", "slots": args.slots,
+                   "hbm_budget_bytes": budget, "offered_load": args.load, "requests": args.requests},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()), "throughput_req_per_s": len(lat) / wall,
+        "capacity_req_per_s": capacity, "arrival_rate_req_per_s": rate,
+        "ct_mults_per_s": work_mults / wall, "decrypts_per_s": work_cells / wall,
+        "server": stats, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="level", choices=["level", "toy", "level_small", "batched"])
+    ap.add_argument("--config", default="level", choices=["level", "toy", "level_small", "batched", "serving", "large"])
+    ap.add_argument("--requests", type=int, default=300, help="serving: timed requests")
+    ap.add_argument("--slots", type=int, default=8, help="serving: concurrent request slots")
+    ap.add_argument("--load", type=float, default=0.7, help="serving: offered load / measured capacity")
     ap.add_argument("--autotune", action="store_true", help="autotune the launch configurations first (batched)")
+    ap.add_argument("--no-compare", action="store_true", help="batched/large: skip the per-node comparator")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    cfg = synth.CONFIGS[args.config]
+    cfg = synth.CONFIGS.get(args.config, {})
     if args.impl == "reference":
         run_reference(args, cfg)
     elif args.config == "batched":
+        run_batched(args, cfg)
+    elif args.config == "serving":
+        run_serving(args, cfg)
+    elif args.config == "large":
         run_batched(args, cfg)
     else:
         run_ours(args, cfg)
