@@ -131,6 +131,21 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The slowest rank's value (the timing rule for N > 1); identity on one rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, steps: int, world: int, seconds_max: float) -> float:
+    """Aggregate throughput over all ranks: units every rank processed / the slowest rank's time."""
+    return units_per_rank * steps * world / seconds_max
+
+
 def make_inputs(cfg: dict):
     p, q = synth.gen_primes(cfg["n_bits"], cfg["seed"])
     n = p * q
@@ -305,10 +320,7 @@ def run_ours(args, cfg):
         prof[kname] = (tot.value, cntl.value)
     native.call("paillier_profile", 0)
     P.sync()
-    if dist is not None:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, dist, dev)
 
     # end to end through the public API with pinned host buffers
     h2d = h_v.numel() * 4 + h_r.numel() * 4 + h_bins.numel() + h_node.numel() * 4
@@ -328,14 +340,11 @@ def run_ours(args, cfg):
     e3.record()
     barrier()
     e2e_s = e2.elapsed_time(e3) / 1e3
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
     P.sync()
 
     units = 2 * M  # g and h values through the whole path per step and GPU
-    value = units * args.steps * world / elapsed
+    value = whole_job_rate(units, args.steps, world, elapsed)
     def ms(k):
         return prof[k][0]
 
@@ -387,7 +396,7 @@ def run_ours(args, cfg):
             "launch_ms": enc_launch_ms,
         },
         "clocks": clk.summary(),
-        "e2e": {"value": units * e2e_steps * world / e2e_s, "unit": "enc/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": whole_job_rate(units, e2e_steps, world, e2e_s), "unit": "enc/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
     }

@@ -42,7 +42,7 @@ __all__ = [
     "is_probable_prime", "check_key", "PublicKey", "PrivateKey", "keypair",
     "L", "encode", "decode", "encrypt", "decrypt", "decrypt_crt", "add",
     "plain_histogram", "encrypted_histogram_cell", "encrypted_histogram",
-    "mont_product",
+    "mont_product", "plain_histogram_np",
 ]
 
 SCALE_BITS = 24
@@ -204,6 +204,31 @@ def plain_histogram(m_g, m_h, bins, node, num_nodes: int, K: int):
             cell[0] += int(m_g[i])
             cell[1] += int(m_h[i])
             counts[v][f][b] += 1
+    return sums, counts
+
+
+def plain_histogram_np(m_g, m_h, bins, node, num_nodes: int, K: int):
+    """The same plaintext histogram as ``plain_histogram``, for large inputs:
+    one np.bincount per feature over the key node * K + bin of the samples with
+    node >= 0, in exact int64 arithmetic (sums < 2^63 for M < 2^38 samples of
+    at most 2^25).  Returns (sums int64 [num_nodes][F][K][2], counts int64
+    [num_nodes][F][K])."""
+    import numpy as np
+    node = np.asarray(node).astype(np.int64)
+    sel = node >= 0
+    F = len(bins)
+    sums = np.zeros((num_nodes, F, K, 2), dtype=np.int64)
+    counts = np.zeros((num_nodes, F, K), dtype=np.int64)
+    mg = np.asarray(m_g).astype(np.int64)[sel]
+    mh = np.asarray(m_h).astype(np.int64)[sel]
+    for f in range(F):
+        key = node[sel] * K + np.asarray(bins[f]).astype(np.int64)[sel]
+        counts[:, f, :] = np.bincount(key, minlength=num_nodes * K).reshape(num_nodes, K)
+        for k, mm in enumerate((mg, mh)):
+            # split into 2^20-sized pieces so float64 weights stay exact
+            lo = np.bincount(key, weights=(mm & 0xFFFFF).astype(np.float64), minlength=num_nodes * K)
+            hi = np.bincount(key, weights=(mm >> 20).astype(np.float64), minlength=num_nodes * K)
+            sums[:, f, :, k] = (lo.astype(np.int64) + (hi.astype(np.int64) << 20)).reshape(num_nodes, K)
     return sums, counts
 
 

@@ -155,6 +155,17 @@ def test_plain_histogram_vs_bincount():
         assert [counts[v][f][b] for v in range(nodes) for b in range(K)] == cref.tolist()
 
 
+def test_plain_histogram_np_equals_loop_definition():
+    rng = synth.rng_misc(14)
+    M, F, K, nodes = 2000, 4, 13, 5
+    m = rng.integers(0, 2 ** 25 + 1, size=(2, M))
+    bins = rng.integers(0, K, size=(F, M))
+    node = rng.integers(-1, nodes, size=M)
+    sums, counts = oracle.plain_histogram(m[0], m[1], bins, node, nodes, K)
+    s2, c2 = oracle.plain_histogram_np(m[0], m[1], bins, node, nodes, K)
+    assert s2.tolist() == sums and c2.tolist() == counts
+
+
 def test_paper_operation_count():
     # Sec. III.C: one node, every bin non-empty -> (M - K) x 2 x J modular products
     rng = synth.rng_misc(12)
