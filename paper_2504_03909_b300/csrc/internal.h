@@ -80,7 +80,8 @@ struct pl_key {
   pl::N2Const n2c{};
   // private part
   pl::HalfConst half[2]{};
-  plh::Big e_enc;        // exponent of r: n
+  plh::Big e_enc1[2];    // encryption, mod x: the other prime mod (x - 1)
+  plh::Big e_enc2[2];    // encryption, mod x^2: x itself
   plh::Big e_dec[2];     // p - 1, q - 1
   pl::EncCrtParams enc{};
   pl::DecCrtParams dec{};

@@ -39,11 +39,62 @@ __global__ void k_decode(const uint64_t* __restrict__ s, const int32_t* __restri
   }
 }
 
-// Batched exponentiation in the CRT halves.  Instance (h, i): half h (p^2 or
-// q^2), item i.  A warp takes 32/T consecutive items of one half, so the
+// Fixed-window exponentiation of one instance held by a group of T lanes.
+// acc: the base in Montgomery form on entry, base^e in Montgomery form on exit
+// (e given by nd window digits dg[], least significant first).  tbl: this
+// group's table of 2^w entries of S*T limbs; bs: its shared-memory column.
+template <int S, int T>
+PL_DEV void window_exp(uint32_t (&acc)[S], const uint32_t (&n)[S], uint32_t np, const uint32_t* R1,
+                       const uint8_t* dg, int nd, int w, uint32_t* tbl, uint32_t* bs, int st, int k) {
+  constexpr int NL = S * T;
+  const int nent = 1 << w;
+  uint32_t a[S], t[S];
+  const_slice<S>(a, R1, k);
+  store_slice<S>(tbl, a, k);            // base^0 = Montgomery one
+  store_slice<S>(tbl + NL, acc, k);     // base^1
+  __syncwarp();
+  stage<S>(bs, st, acc, k);
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < S; ++j) a[j] = acc[j];
+  for (int e = 2; e < nent; ++e) {
+    mont_mul<S, T>(t, a, bs, st, n, np, k);
+    store_slice<S>(tbl + e * NL, t, k);
+#pragma unroll
+    for (int j = 0; j < S; ++j) a[j] = t[j];
+  }
+  // left to right: w squarings, then one product with the digit's table entry
+  load_slice_rw<S>(a, tbl + (size_t)dg[nd - 1] * NL, k);
+  for (int di = nd - 2; di >= 0; --di) {
+    const int d = dg[di];
+    for (int s = 0; s <= w; ++s) {
+      __syncwarp();
+      if (s < w) {
+        stage<S>(bs, st, a, k);
+      } else {
+        load_slice_rw<S>(t, tbl + (size_t)d * NL, k);
+        stage<S>(bs, st, t, k);
+      }
+      __syncwarp();
+      mont_mul<S, T>(t, a, bs, st, n, np, k);
+#pragma unroll
+      for (int j = 0; j < S; ++j) a[j] = t[j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < S; ++j) acc[j] = a[j];
+}
+
+// Batched exponentiation in the CRT halves.  Instance (h, i): half h (prime
+// x = p or q), item i.  A warp takes 32/T consecutive items of one half, so the
 // exponent digits are warp-uniform.
-//   ENC: y[h][i] = (1 + m_i n) r_i^n mod N_h      (in = r [count][L])
-//   DEC: y[h][i] = c_i^(x_h - 1) mod N_h          (in = c [count][2L])
+//   ENC: y[h][i] = (1 + m_i n) r_i^n mod x^2          (in = r [count][L])
+//        with r^n mod x^2 = ((r mod x)^(x' mod (x - 1)) mod x)^x mod x^2, x' the
+//        other prime: Fermat gives r^x' = r^(x' mod (x-1)) mod x, and z^x mod x^2
+//        depends only on z mod x (every term of (z + k x)^x after the first has
+//        x^2 as a factor).  One exponent of n_bits/2 bits mod x (L/2 limbs) and
+//        one of n_bits/2 bits mod x^2 replace one of n_bits bits mod x^2.
+//   DEC: y[h][i] = c_i^(x - 1) mod x^2                (in = c [count][2L])
 // Every value is canonical.  tbl: per-group window table, 2^w entries of L
 // limbs for each group of the grid.
 template <int S, int T, bool DEC>
@@ -81,7 +132,7 @@ __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ Modex
     uint32_t* yrow = out + ((size_t)h * count + ii) * NL;
 
     if constexpr (!DEC) {
-      // post-factor (1 + m n) mod N = mont(nR, m) + 1, parked in the output row
+      // post-factor (1 + m n) mod x^2 = mont(nR, m) + 1, parked in the output row
       const uint64_t m = msg[ii];
       __syncwarp();
 #pragma unroll
@@ -94,8 +145,53 @@ __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ Modex
       mont_mul<S, T>(t, a, bs, st, n, np, k);
       normalize<S, T>(t, 0u, 1u, n, k, kFull);
       if (valid) store_slice<S>(yrow, t, k);
-      // base r in Montgomery form: mont(r, R^2) = r R mod N (valid for any r < R)
-      load_slice<S>(a, in + ii * NL, k);
+
+      // stage 1, mod x on L/2 limbs: z = (r mod x)^(x' mod (x - 1)) mod x
+      {
+        constexpr int S2 = S / 2;
+        constexpr int NLh = S2 * T;
+        uint32_t nx[S2], ax[S2], tx[S2];
+        const_slice<S2>(nx, H.Nx, k);
+        const uint32_t npx = H.npx;
+        const uint32_t* rrow = in + ii * NL;
+        // r = r_lo + r_hi Rx: Montgomery form (r mod x) Rx = mont(r_lo, Rx^2) + mont(r_hi, Rx^3)
+        load_slice<S2>(ax, rrow, k);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < S2; ++j) bs[(k * S2 + j) * st] = H.R2x[k * S2 + j];
+        __syncwarp();
+        mont_mul<S2, T>(tx, ax, bs, st, nx, npx, k);
+        store_slice<S2>(mytbl, tx, k);
+        load_slice<S2>(ax, rrow + NLh, k);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < S2; ++j) bs[(k * S2 + j) * st] = H.R3x[k * S2 + j];
+        __syncwarp();
+        mont_mul<S2, T>(tx, ax, bs, st, nx, npx, k);
+        load_slice_rw<S2>(ax, mytbl, k);
+        add_cc(tx[0], ax[0]);
+#pragma unroll
+        for (int j = 1; j < S2; ++j) addc_cc(tx[j], ax[j]);
+        const uint32_t c = carry_out();
+        normalize<S2, T>(tx, c, 0u, nx, k, kFull);
+        window_exp<S2, T>(tx, nx, npx, H.R1x, P.dig1[h], P.ndig1[h], w, mytbl, bs, st, k);
+        // leave Montgomery form mod x
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < S2; ++j) bs[(k * S2 + j) * st] = (k * S2 + j == 0) ? 1u : 0u;
+        __syncwarp();
+        mont_mul<S2, T>(ax, tx, bs, st, nx, npx, k);
+        // z (< x, L/2 limbs) into the L-limb layout of stage 2, zero-extended
+        __syncwarp();
+        stage<S2>(bs, st, ax, k);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          const int idx = k * S + j;
+          a[j] = idx < NLh ? bs[idx * st] : 0u;
+        }
+      }
+      // stage 2 base: z R mod x^2
       __syncwarp();
 #pragma unroll
       for (int j = 0; j < S; ++j) bs[(k * S + j) * st] = H.R2[k * S + j];
@@ -124,42 +220,10 @@ __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ Modex
       normalize<S, T>(t, c, 0u, n, k, kFull);
     }
 
-    // window table: tbl[e] = x^e in Montgomery form, e < 2^w
-    const_slice<S>(a, H.R1, k);
-    store_slice<S>(mytbl, a, k);
-    store_slice<S>(mytbl + NL, t, k);
-    __syncwarp();
-    stage<S>(bs, st, t, k);
-    __syncwarp();
+    // exponentiation mod x^2: exponent x (ENC) or x - 1 (DEC)
+    window_exp<S, T>(t, n, np, H.R1, P.dig[h], P.ndig[h], w, mytbl, bs, st, k);
 #pragma unroll
     for (int j = 0; j < S; ++j) a[j] = t[j];
-    for (int e = 2; e < nent; ++e) {
-      mont_mul<S, T>(t, a, bs, st, n, np, k);
-      store_slice<S>(mytbl + e * NL, t, k);
-#pragma unroll
-      for (int j = 0; j < S; ++j) a[j] = t[j];
-    }
-
-    // left-to-right fixed-window exponentiation
-    const int nd = P.ndig[h];
-    const uint8_t* dg = P.dig[h];
-    load_slice_rw<S>(a, mytbl + (size_t)dg[nd - 1] * NL, k);
-    for (int di = nd - 2; di >= 0; --di) {
-      const int d = dg[di];
-      for (int s = 0; s <= w; ++s) {
-        __syncwarp();
-        if (s < w) {
-          stage<S>(bs, st, a, k);
-        } else {
-          load_slice_rw<S>(t, mytbl + (size_t)d * NL, k);
-          stage<S>(bs, st, t, k);
-        }
-        __syncwarp();
-        mont_mul<S, T>(t, a, bs, st, n, np, k);
-#pragma unroll
-        for (int j = 0; j < S; ++j) a[j] = t[j];
-      }
-    }
 
     // leave Montgomery form: times the post factor (ENC) or times 1 (DEC)
     __syncwarp();

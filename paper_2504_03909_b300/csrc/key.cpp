@@ -41,6 +41,7 @@ void fill_private(pl_key* k) {
   const Big& q = k->q;
   const Big g = plh::add(k->n, Big(1));
   const Big P2[2] = {plh::mul(p, p), plh::mul(q, q)};
+  const Big X[2] = {p, q};
   Big R1s[2];
   for (int h = 0; h < 2; ++h) {
     pl::HalfConst& H = k->half[h];
@@ -54,8 +55,18 @@ void fill_private(pl_key* k) {
     put(H.R3, R3, L);
     put(H.nR, nR, L);
     R1s[h] = R1;
+    // arithmetic mod the prime x itself (L/2 limbs)
+    Big R1x, R2x;
+    mont_consts(X[h], Lh, &H.npx, &R1x, &R2x);
+    const Big R3x = plh::mod(plh::mul(R2x, R1x), X[h]);
+    put(H.Nx, X[h], Lh);
+    put(H.R1x, R1x, Lh);
+    put(H.R2x, R2x, Lh);
+    put(H.R3x, R3x, Lh);
+    // r^n mod x^2 = ((r mod x)^(x' mod (x - 1)) mod x)^x mod x^2, x' the other prime
+    k->e_enc1[h] = plh::mod(X[1 - h], plh::sub(X[h], Big(1)));
+    k->e_enc2[h] = X[h];
   }
-  k->e_enc = k->n;
   k->e_dec[0] = plh::sub(p, Big(1));
   k->e_dec[1] = plh::sub(q, Big(1));
 
@@ -144,17 +155,24 @@ const pl::ModexpParams* pl_key::modexp_params(bool dec, int w) {
   if (it != cache.end()) return it->second.get();
   auto P = std::make_unique<pl::ModexpParams>();
   std::memset(P.get(), 0, sizeof(pl::ModexpParams));
-  for (int h = 0; h < 2; ++h) {
-    P->half[h] = half[h];
-    const Big& e = dec ? e_dec[h] : e_enc;
+  auto digits = [&](const Big& e, uint8_t* dst, int maxd) {
     const int nd = (e.bits() + w - 1) / w;
-    if (nd > pl::kMaxDigits) return nullptr;
+    if (nd > maxd || nd < 1) return -1;
     for (int i = 0; i < nd; ++i) {
       int d = 0;
       for (int b = 0; b < w; ++b) d |= (int)e.bit(i * w + b) << b;
-      P->dig[h][i] = (uint8_t)d;
+      dst[i] = (uint8_t)d;
     }
-    P->ndig[h] = nd;
+    return nd;
+  };
+  for (int h = 0; h < 2; ++h) {
+    P->half[h] = half[h];
+    P->ndig[h] = digits(dec ? e_dec[h] : e_enc2[h], P->dig[h], pl::kMaxDigits);
+    if (P->ndig[h] < 0) return nullptr;
+    if (!dec) {
+      P->ndig1[h] = digits(e_enc1[h], P->dig1[h], pl::kMaxDigitsH);
+      if (P->ndig1[h] < 0) return nullptr;
+    }
   }
   P->w = w;
   const pl::ModexpParams* raw = P.get();

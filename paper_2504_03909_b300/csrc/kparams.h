@@ -10,6 +10,7 @@ namespace pl {
 constexpr int kMaxL = 96;                 // limbs of n for the largest key (3072-bit)
 constexpr int kMaxLh = kMaxL / 2;         // limbs of p, q
 constexpr int kMaxDigits = 3072 / 2 + 1;  // exponent windows at the smallest window (w = 2)
+constexpr int kMaxDigitsH = 1536 / 2 + 1; // the same for exponents of at most 1536 bits
 
 // Device status word bits (OR-ed by kernels, read by paillier_sync)
 constexpr int kStatusBadBin = 1;       // bin >= K
@@ -19,24 +20,36 @@ constexpr int kStatusEncode = 8;       // value outside the encodable range
 constexpr int kStatusTimeout = 16;     // a bounded wait ran out
 constexpr int kStatusCapacity = 32;    // a work list was larger than its buffer
 
-// One half of the key holder's CRT split: arithmetic mod N = p^2 (or q^2),
-// L limbs, R = 2^(32 L).
+// One half of the key holder's CRT split: arithmetic mod N = x^2 for the
+// prime x = p (or q), L limbs, R = 2^(32 L); and mod x itself, L/2 limbs,
+// Rx = 2^(16 L).
 struct HalfConst {
-  uint32_t N[kMaxL];    // p^2
+  uint32_t N[kMaxL];    // x^2
   uint32_t R1[kMaxL];   // R mod N (Montgomery one)
   uint32_t R2[kMaxL];   // R^2 mod N
   uint32_t R3[kMaxL];   // R^3 mod N (reduces a 2L-limb value into Montgomery form)
   uint32_t nR[kMaxL];   // n R mod N (so that mont(m, nR) = m n mod N)
+  uint32_t Nx[kMaxLh];  // x
+  uint32_t R1x[kMaxLh]; // Rx mod x
+  uint32_t R2x[kMaxLh]; // Rx^2 mod x
+  uint32_t R3x[kMaxLh]; // Rx^3 mod x (reduces an L-limb value into Montgomery form mod x)
   uint32_t np;          // -N^-1 mod 2^32
-  uint32_t pad[3];
+  uint32_t npx;         // -x^-1 mod 2^32
+  uint32_t pad[2];
 };
 
 // Batched fixed-window modular exponentiation over both halves.
+//   decryption: c^(x-1) mod x^2, exponent digits in dig;
+//   encryption: r^n mod x^2 = ((r mod x)^(x' mod (x-1)) mod x)^x mod x^2, where x'
+//   is the other prime (y^x mod x^2 depends only on y mod x):
+//   digits of x' mod (x-1) in dig1 (mod x), digits of x in dig (mod x^2).
 struct ModexpParams {
   HalfConst half[2];
-  uint8_t dig[2][kMaxDigits];  // window digits of the exponent, least significant first
+  uint8_t dig[2][kMaxDigits];    // window digits, least significant first
   int ndig[2];
-  int w;                       // window width in bits
+  uint8_t dig1[2][kMaxDigitsH];  // encryption, first exponentiation (mod x)
+  int ndig1[2];
+  int w;                         // window width in bits
   int pad;
 };
 
