@@ -141,6 +141,11 @@ def dist_setup():
     return world, rank, local
 
 
+def sm_count_of(dev) -> int:
+    import torch
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
 def max_over_ranks(x: float, dist=None, device=None) -> float:
     """The slowest rank's value (the timing rule for N > 1); identity on one rank."""
     if dist is None:
@@ -401,6 +406,8 @@ def run_ours(args, cfg):
             "frac": achieved / peak,
             "traffic": None,
             "peak_source": "project microbenchmark paillier_imad_peak, best mix, same run",
+            "peak_derived_TIMAD_s": sm_count_of(dev) * 64 * 2.032e9 / 1e12,
+            "peak_derived_note": "SMs x 64 32-bit IMAD/clk/SM x 2032 MHz max clock",
             "peaks_measured_TIMAD_s": {k: v_ / 1e12 for k, v_ in peaks.items()},
             "imad_per_launch": imad_launch,
             "launch_ms": enc_launch_ms,
