@@ -404,7 +404,10 @@ def run_ours(args, cfg):
             "peak": peak / 1e12,
             "unit": "TIMAD/s",
             "frac": achieved / peak,
-            "traffic": None,
+            # DRAM bytes per encryption of this kernel version from the ncu capture summarised in
+            # profiles/k_modexp_enc_2048bit_small.md (16,384 encryptions, w = 5), scaled to this launch
+            "traffic": units * (23.2e3 + 20.6e3) if (n_bits == 2048 and w == 5) else None,
+            "traffic_note": "ncu dram__bytes_read+write of a 16,384-encryption capture, scaled by encryptions",
             "peak_source": "project microbenchmark paillier_imad_peak, best mix, same run",
             "peak_derived_TIMAD_s": sm_count_of(dev) * 64 * 2.032e9 / 1e12,
             "peak_derived_note": "SMs x 64 32-bit IMAD/clk/SM x 2032 MHz max clock",
