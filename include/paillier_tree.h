@@ -1,0 +1,51 @@
+/*
+ * paillier_tree.h -- tree building on the decrypted histograms (Sec. III.B:
+ * the active party decrypts the cumulative histograms and uses them "for tree
+ * building"; Sec. IV: the secure vertical trees equal the non-secure ones).
+ *
+ * Split finding is XGBoost's exact histogram gain (Chen & Guestrin, KDD 2016):
+ *   score(G, H) = G^2 / (H + lambda)
+ *   gain = 0.5 * (score(G_L, H_L) + score(G_R, H_R) - score(G, H)) - gamma
+ * for the split "bin <= b goes left", over every feature f and bin b < K - 1,
+ * subject to H_L >= min_child_weight and H_R >= min_child_weight.  G, H are the
+ * decoded fixed-point sums: G = (S_g - count * 2^24) / 2^24, exact in float64
+ * (prefix sums are taken on the exact integers first).  The gain is evaluated
+ * in IEEE float64 with one rounding per operation in the order written above
+ * (no fused multiply-add), so the result is reproducible bit for bit.  The
+ * best split of a node is the largest gain > 0; ties go to the lowest feature,
+ * then the lowest bin.  A node without a positive-gain split is a leaf.
+ */
+#ifndef PAILLIER_B300_TREE_H
+#define PAILLIER_B300_TREE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "paillier.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Best split per node from decrypted histogram sums.
+ *   d_sums   : [nodes][F][K][2] uint64 fixed-point sums (g, h) (decrypted cells)
+ *   d_counts : [nodes][F][K] int32 sample counts
+ *   d_best_f, d_best_b : [nodes] out: feature and bin of the best split, -1 for a leaf
+ *   d_best_gain        : [nodes] out (may be NULL): its gain (0 for a leaf) */
+pl_status paillier_split_find(const uint64_t* d_sums, const int32_t* d_counts, int nodes, int F, int K,
+                              double lambda, double gamma, double min_child_weight,
+                              int32_t* d_best_f, int32_t* d_best_b, double* d_best_gain, void* stream);
+
+/* Node membership of the next level: for sample i in node v = d_node[i] >= 0
+ * with split (f, b) = (d_best_f[v], d_best_b[v]), f >= 0:
+ * d_next[i] = 2 v + (d_bins[f * M + i] > b); d_next[i] = -1 if d_node[i] < 0 or
+ * node v is a leaf.  (In the vertical setting the party owning feature f
+ * applies its own split; here the parties are simulated on one device.) */
+pl_status paillier_split_apply(const uint8_t* d_bins, size_t M, const int32_t* d_node, const int32_t* d_best_f,
+                               const int32_t* d_best_b, int32_t* d_next, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAILLIER_B300_TREE_H */

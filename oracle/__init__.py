@@ -11,3 +11,4 @@ or reordering beyond what the definitions state.
 """
 
 from .paillier import *  # noqa: F401,F403
+from . import tree  # noqa: F401

@@ -280,6 +280,30 @@ class Server:
             pass
 
 
+def split_find(sums: torch.Tensor, counts: torch.Tensor, lam: float = 1.0, gamma: float = 0.0,
+               min_child_weight: float = 0.0, stream=None):
+    """Best split per node from decrypted sums [nodes, F, K, 2] (int64 bits of
+    uint64) and counts [nodes, F, K]: (feature, bin, gain) tensors [nodes]."""
+    nodes, F, K, _ = sums.shape
+    assert sums.dtype == torch.int64 and counts.dtype == torch.int32 and counts.shape == (nodes, F, K)
+    bf = torch.empty(nodes, dtype=torch.int32, device=sums.device)
+    bb = torch.empty_like(bf)
+    bg = torch.empty(nodes, dtype=torch.float64, device=sums.device)
+    call("paillier_split_find", _ptr(sums), _ptr(counts), nodes, F, K, lam, gamma, min_child_weight, _ptr(bf),
+         _ptr(bb), _ptr(bg), _stream(stream))
+    return bf, bb, bg
+
+
+def split_apply(bins: torch.Tensor, node: torch.Tensor, best_f: torch.Tensor, best_b: torch.Tensor,
+                out: torch.Tensor | None = None, stream=None):
+    """Next-level node ids of every sample under the chosen splits."""
+    M = node.numel()
+    if out is None:
+        out = torch.empty_like(node)
+    call("paillier_split_apply", _ptr(bins), M, _ptr(node), _ptr(best_f), _ptr(best_b), _ptr(out), _stream(stream))
+    return out
+
+
 def get_config(key: Key, op: int):
     la, pa = C.c_int(), C.c_int()
     call("paillier_get_config", key.handle, op, C.byref(la), C.byref(pa))

@@ -1,0 +1,56 @@
+"""The full secure tree loop on the GPU (encrypt -> per-level encrypted
+histograms -> CRT decrypt -> split finding -> node update) equals the tree the
+oracle builds from the plaintext histograms: the same split (feature, bin,
+float64 gain, bit for bit) at every node and the same node of every sample at
+every level (Sec. IV: secure vertical trees have the same structure as the
+non-secure ones)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import tree as otree
+from paper_2504_03909_b300 import paillier as P, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _secure_vs_plain(n_bits, M, F, K, depth, seed, lam=1.0, gamma=0.0, mcw=1.0):
+    p, q = synth.gen_primes(n_bits, seed)
+    key = P.Key.from_primes(n_bits, p, q)
+    gh = synth.gen_gh(M, seed)
+    r = synth.gen_r(p * q, n_bits, 2 * M, seed, p, q)
+    bins = synth.gen_bins_quantile(F, M, K, seed)
+    m = P.encode(torch.from_numpy(gh.reshape(-1)).cuda())
+    ct = P.encrypt(key, m, P.to_limb_tensor(r))
+    ctm = P.ct_prepare(key, ct.view(2, M, -1))
+    bins_d = torch.from_numpy(bins).cuda()
+    plan = P.LevelPlan(key, M, F, K, 1 << (depth - 1))
+    node = torch.zeros(M, dtype=torch.int32, device="cuda")
+    ms = [oracle.encode(x) for x in gh.reshape(-1)]
+    onode = [0] * M
+    for lvl in range(depth):
+        nn = 1 << lvl
+        hist, cnt = plan.run(ctm, bins_d, node, nn)
+        sums = P.decrypt_u64(key, hist.reshape(-1, 2 * key.L)).view(nn, F, K, 2)
+        bf, bb, bg = P.split_find(sums, cnt, lam, gamma, mcw)
+        nxt = P.split_apply(bins_d, node, bf, bb)
+        P.sync()
+        # oracle: plaintext histogram of the same node assignment, same split rule
+        psums, pcnt = oracle.plain_histogram(ms[:M], ms[M:], bins, onode, nn, K)
+        of, ob, og = otree.split_find(psums, pcnt, lam, gamma, mcw)
+        assert bf.cpu().tolist() == of and bb.cpu().tolist() == ob, lvl
+        assert bg.cpu().tolist() == og, lvl                 # float64 gains bit for bit
+        onode = otree.split_apply(bins, onode, of, ob)
+        assert nxt.cpu().tolist() == onode, lvl
+        node = nxt
+    return sum(1 for f in of if f >= 0)
+
+
+def test_secure_tree_equals_plaintext_tree_1024():
+    assert _secure_vs_plain(1024, 1500, 5, 16, 4, seed=8) > 0
+
+
+def test_secure_tree_equals_plaintext_tree_2048():
+    assert _secure_vs_plain(2048, 6000, 8, 64, 5, seed=9, lam=0.5, gamma=0.01, mcw=2.0) > 0
