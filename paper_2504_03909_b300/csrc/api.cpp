@@ -4,6 +4,7 @@
 #include <mutex>
 
 #include "internal.h"
+#include "../../include/paillier_pack.h"
 
 namespace pl {
 
@@ -294,6 +295,47 @@ pl_status paillier_decrypt(const pl_key* key, const uint32_t* d_ct, size_t count
 
 pl_status paillier_decrypt_u64(const pl_key* key, const uint32_t* d_ct, size_t count, uint64_t* d_m, void* stream) {
   return decrypt_common(key, d_ct, count, d_m, true, stream);
+}
+
+int paillier_pack_slots(const pl_key* key, int slot_bits) {
+  if (!key || slot_bits < 1 || slot_bits > 64) return 0;
+  return (key->n_bits - 2) / slot_bits;
+}
+
+pl_status paillier_pack(const pl_key* key, const uint32_t* d_ct, size_t count, int slot_bits, uint32_t* d_packed,
+                        void* stream) {
+  clear_error();
+  if (!key) return fail(PL_EINVAL, "key is NULL");
+  const int slots = paillier_pack_slots(key, slot_bits);
+  if (slots < 1) return fail(PL_EINVAL, "slot_bits must be 1..64");
+  if (count == 0) return PL_OK;
+  if (!d_ct || !d_packed) return fail(PL_EINVAL, "NULL buffer");
+  if (!aligned16(d_ct) || !aligned16(d_packed)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
+  if (!current_status()) return fail(PL_ECUDA, "no usable CUDA device");
+  return launch_pack(key, d_ct, count, slots, slot_bits, d_packed, static_cast<cudaStream_t>(stream));
+}
+
+pl_status paillier_decrypt_packed_u64(const pl_key* key, const uint32_t* d_packed, size_t count, int slot_bits,
+                                      uint64_t* d_m, void* stream) {
+  clear_error();
+  if (!key) return fail(PL_EINVAL, "key is NULL");
+  if (!key->priv) return fail(PL_EINVAL, "decryption needs the private key");
+  const int slots = paillier_pack_slots(key, slot_bits);
+  if (slots < 1) return fail(PL_EINVAL, "slot_bits must be 1..64");
+  if (count == 0) return PL_OK;
+  if (!d_packed || !d_m) return fail(PL_EINVAL, "NULL buffer");
+  if (!aligned16(d_packed)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
+  int* st = current_status();
+  if (!st) return fail(PL_ECUDA, "no usable CUDA device");
+  pl_key* k = const_cast<pl_key*>(key);
+  const size_t npacked = (count + slots - 1) / slots;
+  Scratch* aux = k->scratch_for_current_device(true);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto* plain = static_cast<uint32_t*>(aux ? aux->get(npacked * key->L * sizeof(uint32_t), s) : nullptr);
+  if (!plain) return fail(PL_ENOMEM, "scratch allocation failed");
+  pl_status rc = launch_decrypt(k, d_packed, npacked, plain, false, st, s);
+  if (rc) return rc;
+  return launch_unpack(plain, key->L, count, slots, slot_bits, d_m, st, s);
 }
 
 }  // extern "C"

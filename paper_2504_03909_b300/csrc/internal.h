@@ -91,11 +91,12 @@ struct pl_key {
   // per-window exponent digit tables (built on demand)
   std::map<int, std::unique_ptr<pl::ModexpParams>> enc_params, dec_params;
   std::mutex mu;
-  // scratch per device
-  std::map<int, std::unique_ptr<pl::Scratch>> scratch;
+  // scratch per device (the second one holds results that outlive a call's
+  // first scratch use, e.g. packed plaintexts between decryption and unpacking)
+  std::map<int, std::unique_ptr<pl::Scratch>> scratch, scratch_aux;
 
   const pl::ModexpParams* modexp_params(bool dec, int w);
-  pl::Scratch* scratch_for_current_device();
+  pl::Scratch* scratch_for_current_device(bool aux = false);
 };
 
 namespace pl {
@@ -112,6 +113,10 @@ pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, size_t ghs, 
                       size_t bstride, int F, int K, const int32_t* d_node, int num_nodes, uint32_t* d_hist,
                       int32_t* d_count, bool per_node, int* st, cudaStream_t s, Scratch* scratch = nullptr);
 int sm_count();
+pl_status launch_pack(const pl_key* key, const uint32_t* ct, size_t count, int slots, int B, uint32_t* packed,
+                      cudaStream_t s);
+pl_status launch_unpack(const uint32_t* plain, int L, size_t count, int slots, int B, uint64_t* out, int* st,
+                        cudaStream_t s);
 
 // ---- histogram pass pieces shared with the level plan ----------------------
 struct HistBufs {

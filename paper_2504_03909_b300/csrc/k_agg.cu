@@ -494,3 +494,143 @@ pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, size_t ghs, 
 }
 
 }  // namespace pl
+
+// ---------------------------------------------------------------------------
+// Packing of histogram cells for fewer decryptions (see paillier_pack.h).
+namespace pl {
+namespace {
+
+// One lane group per packed ciphertext: Horner over `slots` cells mod n^2,
+// cells past `count` taken as the ciphertext 1 (an encryption of 0).
+template <int S, int T>
+__global__ void __launch_bounds__(kBlock) k_pack(const __grid_constant__ N2Const P, const uint32_t* __restrict__ ct,
+                                                 size_t count, int slots, int B, uint32_t* __restrict__ packed,
+                                                 size_t npacked) {
+  constexpr int NL = S * T;
+  constexpr int IPW = 32 / T;
+  extern __shared__ uint32_t smem[];
+  uint32_t* r2 = smem;                 // R^2 mod n^2, one shared copy
+  uint32_t* cols = smem + NL;          // per-group multiplicand columns
+  for (int j = threadIdx.x; j < NL; j += blockDim.x) r2[j] = P.R2[j];
+  __syncthreads();
+  const int ipb = blockDim.x / T;
+  const int lane = threadIdx.x & 31, k = lane % T, gw = lane / T, g = threadIdx.x / T;
+  uint32_t* bs = cols + g;
+  const int st = ipb;
+  uint32_t n[S], a[S], t[S], acc[S];
+  const_slice<S>(n, P.N, k);
+  const uint32_t np = P.np;
+  const size_t nchunk = (npacked + IPW - 1) / IPW;
+  const size_t warp0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t c = warp0; c < nchunk; c += nwarps) {
+    const size_t pi = c * IPW + gw;
+    const bool valid = pi < npacked;
+    const size_t base = (valid ? pi : npacked - 1) * (size_t)slots;
+    // Montgomery form of cell `idx` (or of 1 past the end) into acc-shaped registers
+    auto cell_mont = [&](size_t idx, uint32_t (&dst)[S]) {
+      if (idx < count) {
+        load_slice<S>(a, ct + idx * NL, k);
+      } else {
+#pragma unroll
+        for (int j = 0; j < S; ++j) a[j] = (k * S + j == 0) ? 1u : 0u;
+      }
+      mont_mul<S, T>(dst, a, r2, 1, n, np, k);
+    };
+    cell_mont(base + slots - 1, acc);
+    for (int j = slots - 2; j >= 0; --j) {
+      for (int sq = 0; sq < B; ++sq) {
+        __syncwarp();
+        stage<S>(bs, st, acc, k);
+        __syncwarp();
+        mont_mul<S, T>(t, acc, bs, st, n, np, k);
+#pragma unroll
+        for (int q = 0; q < S; ++q) acc[q] = t[q];
+      }
+      cell_mont(base + j, t);
+      __syncwarp();
+      stage<S>(bs, st, t, k);
+      __syncwarp();
+      mont_mul<S, T>(t, acc, bs, st, n, np, k);
+#pragma unroll
+      for (int q = 0; q < S; ++q) acc[q] = t[q];
+    }
+    // leave Montgomery form
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < S; ++q) bs[(k * S + q) * st] = (k * S + q == 0) ? 1u : 0u;
+    __syncwarp();
+    mont_mul<S, T>(t, acc, bs, st, n, np, k);
+    if (valid) store_slice<S>(packed + pi * NL, t, k);
+  }
+}
+
+template <int S, int T>
+pl_status run_pack(const N2Const& P, const uint32_t* ct, size_t count, int slots, int B, uint32_t* packed,
+                   size_t npacked, cudaStream_t s) {
+  constexpr int NL = S * T;
+  const size_t smem = (size_t)NL * sizeof(uint32_t) * (1 + kBlock / T);
+  static int grid = 0;
+  if (!grid) grid = occupancy_grid<S, T>((const void*)k_pack<S, T>, smem);
+  const size_t ipw = 32 / T;
+  const size_t blocks_needed = ((npacked + ipw - 1) / ipw + (kBlock / 32) - 1) / (kBlock / 32);
+  const int g = (int)std::min<size_t>((size_t)grid, blocks_needed);
+  {
+    ProfScope _ps("pack", s);
+    k_pack<S, T><<<g, kBlock, smem, s>>>(P, ct, count, slots, B, packed, npacked);
+  }
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
+
+// plaintext [np][L] -> count values of B bits; bits past slots * B must be 0
+__global__ void k_unpack(const uint32_t* __restrict__ plain, int L, size_t count, int slots, int B,
+                         uint64_t* __restrict__ out, int* status) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t pi = i / slots;
+    const int j = (int)(i % slots);
+    const uint32_t* x = plain + pi * L;
+    const int bit = j * B;
+    const int w = bit >> 5, sh = bit & 31;
+    uint64_t v = (uint64_t)x[w] >> sh;
+    if (w + 1 < L) v |= (uint64_t)x[w + 1] << (32 - sh);
+    if (sh && w + 2 < L) v |= (uint64_t)x[w + 2] << (64 - sh);
+    if (B < 64) v &= (1ull << B) - 1;
+    out[i] = v;
+    if (j == 0) {  // one check per packed plaintext: nothing above the last slot
+      const int top = slots * B;
+      uint32_t hi = 0;
+      for (int q = top >> 5; q < L; ++q) hi |= (q == (top >> 5)) ? (x[q] >> (top & 31)) : x[q];
+      if ((top & 31) == 0 && (top >> 5) < L) hi |= x[top >> 5];
+      if (hi) atomicOr(status, kStatusRange);
+    }
+  }
+}
+
+}  // namespace
+
+pl_status launch_pack(const pl_key* key, const uint32_t* ct, size_t count, int slots, int B, uint32_t* packed,
+                      cudaStream_t s) {
+  const size_t npacked = (count + slots - 1) / slots;
+  if (!npacked) return PL_OK;
+  const int NL = 2 * key->L, T = key->agg_cfg.T;
+#define PL_CASE(LL, TT) \
+  if (NL == LL && T == TT) return run_pack<LL / TT, TT>(key->n2c, ct, count, slots, B, packed, npacked, s);
+  PL_N2_CASES(PL_CASE)
+#undef PL_CASE
+  return fail(PL_EINVAL, "no mod n^2 kernel for this (limbs, lanes) pair");
+}
+
+pl_status launch_unpack(const uint32_t* plain, int L, size_t count, int slots, int B, uint64_t* out, int* st,
+                        cudaStream_t s) {
+  if (!count) return PL_OK;
+  const int grid = (int)std::min<size_t>((count + 255) / 256, (size_t)sm_count() * 8);
+  {
+    ProfScope _ps("unpack", s);
+    k_unpack<<<grid, 256, 0, s>>>(plain, L, count, slots, B, out, st);
+  }
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
+
+}  // namespace pl

@@ -180,11 +180,11 @@ const pl::ModexpParams* pl_key::modexp_params(bool dec, int w) {
   return raw;
 }
 
-pl::Scratch* pl_key::scratch_for_current_device() {
+pl::Scratch* pl_key::scratch_for_current_device(bool aux) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
   std::lock_guard<std::mutex> lock(mu);
-  auto& s = scratch[dev];
+  auto& s = aux ? scratch_aux[dev] : scratch[dev];
   if (!s) {
     s = std::make_unique<pl::Scratch>();
     s->device = dev;

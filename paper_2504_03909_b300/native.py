@@ -67,6 +67,9 @@ class Request(C.Structure):
 
 
 SIGNATURES.update({
+    "paillier_pack_slots": (_i, [_vp, _i]),
+    "paillier_pack": (_i, [_vp, _vp, _sz, _i, _vp, _vp]),
+    "paillier_decrypt_packed_u64": (_i, [_vp, _vp, _sz, _i, _vp, _vp]),
     "paillier_split_find": (_i, [_vp, _vp, _i, _i, _i, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp, _vp]),
     "paillier_split_apply": (_i, [_vp, _sz, _vp, _vp, _vp, _vp, _vp]),
     "pl_server_create": (_i, [_i, _sz, C.POINTER(C.c_void_p)]),

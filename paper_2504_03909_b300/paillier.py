@@ -280,6 +280,30 @@ class Server:
             pass
 
 
+def pack_slots(key: Key, slot_bits: int) -> int:
+    return lib().paillier_pack_slots(key.handle, slot_bits)
+
+
+def pack(key: Key, ct: torch.Tensor, slot_bits: int, out: torch.Tensor | None = None, stream=None):
+    """Packed ciphertexts [ceil(count / slots), 2L] of cells ct [..., 2L]."""
+    assert ct.dtype == torch.int32 and ct.shape[-1] == 2 * key.L
+    count = ct.numel() // (2 * key.L)
+    slots = pack_slots(key, slot_bits)
+    if out is None:
+        out = torch.empty(((count + slots - 1) // slots, 2 * key.L), dtype=torch.int32, device=ct.device)
+    call("paillier_pack", key.handle, _ptr(ct), count, slot_bits, _ptr(out), _stream(stream))
+    return out
+
+
+def decrypt_packed_u64(key: Key, packed: torch.Tensor, count: int, slot_bits: int,
+                       out: torch.Tensor | None = None, stream=None):
+    """The `count` cell plaintexts (int64 bits of uint64) of packed ciphertexts."""
+    if out is None:
+        out = torch.empty(count, dtype=torch.int64, device=packed.device)
+    call("paillier_decrypt_packed_u64", key.handle, _ptr(packed), count, slot_bits, _ptr(out), _stream(stream))
+    return out
+
+
 def split_find(sums: torch.Tensor, counts: torch.Tensor, lam: float = 1.0, gamma: float = 0.0,
                min_child_weight: float = 0.0, stream=None):
     """Best split per node from decrypted sums [nodes, F, K, 2] (int64 bits of
