@@ -467,16 +467,39 @@ def run_batched(args, cfg):
     plan = P.LevelPlan(key, M, F, K, maxn)
     stream = torch.cuda.Stream()
 
+    pack_bits = args.pack_bits
+    slots = P.pack_slots(key, pack_bits) if pack_bits else 0
+    packed = (torch.empty((-(-(maxn * F * K * 2) // slots), 2 * L), dtype=torch.int32, device=dev)
+              if pack_bits else None)
+    split_nodes = torch.zeros(M, dtype=torch.int32, device=dev)
+
+    def decrypt_level(nn):
+        cells = hist[:nn].reshape(-1, 2 * L)
+        if pack_bits:
+            npk = -(-cells.shape[0] // slots)
+            P.pack(key, cells, pack_bits, out=packed[:npk])
+            P.decrypt_packed_u64(key, packed[:npk], cells.shape[0], pack_bits, out=sums[:cells.shape[0]])
+        else:
+            P.decrypt_u64(key, cells, out=sums[:cells.shape[0]])
+
     def tree_step(with_decrypt=True):
         m = P.encode(v)
         P.encrypt(key, m, r_d, out=ct)
         P.ct_prepare(key, ct, out=ctm)
+        if args.splits == "data":
+            split_nodes.zero_()
         for lvl in range(depth):
             nn = 1 << lvl
-            node_buf.copy_(nodes_d[lvl])
+            if args.splits == "data":
+                node_buf.copy_(split_nodes)
+            else:
+                node_buf.copy_(nodes_d[lvl])
             plan.run(ctm.view(2, M, 2 * L), bins_d, node_buf, nn, hist=hist, count=cnt)
             if with_decrypt:
-                P.decrypt_u64(key, hist[:nn].reshape(-1, 2 * L), out=sums[:nn * F * K * 2])
+                decrypt_level(nn)
+                if args.splits == "data" and lvl + 1 < depth:
+                    bf, bb, _ = P.split_find(sums[:nn * F * K * 2].view(nn, F, K, 2), cnt[:nn], 1.0, 0.0, 1.0)
+                    P.split_apply(bins_d, node_buf, bf, bb, out=split_nodes)
 
     def hist_levels(per_node):
         for lvl in range(depth):
@@ -507,7 +530,7 @@ def run_batched(args, cfg):
             native.call("paillier_profile", 1)
             t_tree = timed(tree_step, args.steps)
             prof = {}
-            for kname in ("modexp_enc", "enc_crt", "modexp_dec", "dec_crt", "to_mont"):
+            for kname in ("modexp_enc", "enc_crt", "modexp_dec", "dec_crt", "to_mont", "pack", "unpack"):
                 tot = native.C.c_double(0)
                 cl = native.C.c_longlong(0)
                 native.call("paillier_profile_read", kname.encode(), native.C.byref(tot), native.C.byref(cl))
@@ -542,9 +565,11 @@ def run_batched(args, cfg):
         "ct_mults_per_tree": ct_mults,
         "tree_ms": 1e3 * t_tree,
         "phases_ms_per_tree": {"encrypt": prof["modexp_enc"] + prof["enc_crt"], "prepare": prof["to_mont"],
-                               "decrypt": prof["modexp_dec"] + prof["dec_crt"]},
+                               "pack": prof["pack"],
+                               "decrypt": prof["modexp_dec"] + prof["dec_crt"] + prof["unpack"]},
         "decrypted_cells_per_tree": cells,
-        "decrypts_per_s": cells / ((prof["modexp_dec"] + prof["dec_crt"]) * 1e-3),
+        "pack_bits": pack_bits, "pack_slots": slots, "splits": args.splits,
+        "cells_decoded_per_s": cells / ((prof["modexp_dec"] + prof["dec_crt"] + prof["unpack"] + prof["pack"]) * 1e-3),
         "graph": plan.stats(),
         "clocks": clk.summary(),
     }
@@ -663,6 +688,9 @@ def main():
     ap.add_argument("--load", type=float, default=0.7, help="serving: offered load / measured capacity")
     ap.add_argument("--autotune", action="store_true", help="autotune the launch configurations first (batched)")
     ap.add_argument("--no-compare", action="store_true", help="batched/large: skip the per-node comparator")
+    ap.add_argument("--pack-bits", type=int, default=0, help="batched/large: pack cells into B-bit slots before decryption")
+    ap.add_argument("--splits", default="beta", choices=["beta", "data"],
+                    help="batched/large: Beta(0.5,0.5) splits or splits found on the decrypted histograms")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
