@@ -44,6 +44,33 @@ pl_status paillier_split_find(const uint64_t* d_sums, const int32_t* d_counts, i
 pl_status paillier_split_apply(const uint8_t* d_bins, size_t M, const int32_t* d_node, const int32_t* d_best_f,
                                const int32_t* d_best_b, int32_t* d_next, void* stream);
 
+/* Histogram subtraction (XGBoost's trick; the paper does not use it): at a
+ * level below the root only the smaller child of every split node needs an
+ * encrypted histogram; the sibling's decrypted sums are the parent's minus the
+ * child's, exact integer arithmetic on the fixed-point sums and counts.
+ *
+ * paillier_child_select: from the children's node ids d_next [M] (2 v and
+ * 2 v + 1, -1 outside) and the parents' decrypted counts, picks the smaller
+ * child of each parent node v (fewer samples; ties -> the left child) and
+ * writes d_small_node [M] = v for the samples of that child, -1 for all
+ * others: a node array of parents.  nodes = number of parents.  d_small_right
+ * [nodes] (out) = 1 if the smaller child is the right one.  The parent's split
+ * (d_best_f, d_best_b) gives the child sizes from d_counts [nodes][F][K]. */
+pl_status paillier_child_select(const int32_t* d_next, size_t M, const int32_t* d_counts, int nodes, int F, int K,
+                                const int32_t* d_best_f, const int32_t* d_best_b, int32_t* d_small_right,
+                                int32_t* d_small_node, void* stream);
+
+/* Full child level from the parents' and the smaller children's decrypted
+ * histograms: for parent v, child (2 v + s) with s = d_small_right[v] gets
+ * d_small_sums[v] and the other child gets d_parent_sums[v] - d_small_sums[v]
+ * (and the same for counts).  Layouts [nodes][F][K][2] (sums, uint64) and
+ * [nodes][F][K] (counts) for parents and small children; [2 nodes][F][K][2]
+ * and [2 nodes][F][K] out. */
+pl_status paillier_child_subtract(const uint64_t* d_parent_sums, const int32_t* d_parent_counts,
+                                  const uint64_t* d_small_sums, const int32_t* d_small_counts,
+                                  const int32_t* d_small_right, int nodes, int F, int K, uint64_t* d_child_sums,
+                                  int32_t* d_child_counts, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

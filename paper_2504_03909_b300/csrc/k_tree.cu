@@ -84,10 +84,93 @@ __global__ void k_split_apply(const uint8_t* __restrict__ bins, size_t M, const 
   }
 }
 
+// per parent: which child is smaller (counts of the split feature's bins)
+__global__ void k_child_sizes(const int32_t* __restrict__ counts, int nodes, int F, int K,
+                              const int32_t* __restrict__ best_f, const int32_t* __restrict__ best_b,
+                              int32_t* __restrict__ small_right) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nodes) return;
+  const int f = best_f[v];
+  if (f < 0) { small_right[v] = 0; return; }
+  const int32_t* c = counts + ((size_t)v * F + f) * K;
+  long long left = 0, right = 0;
+  for (int b = 0; b < K; ++b) (b <= best_b[v] ? left : right) += c[b];
+  small_right[v] = right < left ? 1 : 0;
+}
+
+__global__ void k_child_select(const int32_t* __restrict__ next, size_t M, const int32_t* __restrict__ small_right,
+                               int32_t* __restrict__ small_node) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = next[i];
+    small_node[i] = (c >= 0 && (c & 1) == small_right[c >> 1]) ? (c >> 1) : -1;
+  }
+}
+
+__global__ void k_child_subtract(const uint64_t* __restrict__ ps, const int32_t* __restrict__ pc,
+                                 const uint64_t* __restrict__ ss, const int32_t* __restrict__ sc,
+                                 const int32_t* __restrict__ small_right, int nodes, size_t per_node,
+                                 uint64_t* __restrict__ cs, int32_t* __restrict__ cc) {
+  // per_node = F * K cells; every cell has a g and an h sum and one count
+  const size_t total = (size_t)nodes * per_node;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t v = i / per_node, cell = i % per_node;
+    const int sr = small_right[v];
+    const size_t small_child = 2 * v + sr, big_child = 2 * v + (1 - sr);
+    for (int k = 0; k < 2; ++k) {
+      const uint64_t s = ss[i * 2 + k];
+      cs[(small_child * per_node + cell) * 2 + k] = s;
+      cs[(big_child * per_node + cell) * 2 + k] = ps[i * 2 + k] - s;
+    }
+    cc[small_child * per_node + cell] = sc[i];
+    cc[big_child * per_node + cell] = pc[i] - sc[i];
+  }
+}
+
 }  // namespace
 }  // namespace pl
 
 extern "C" {
+
+pl_status paillier_child_select(const int32_t* d_next, size_t M, const int32_t* d_counts, int nodes, int F, int K,
+                                const int32_t* d_best_f, const int32_t* d_best_b, int32_t* d_small_right,
+                                int32_t* d_small_node, void* stream) {
+  using namespace pl;
+  clear_error();
+  if (nodes < 1 || F < 1 || K < 1 || K > 256) return fail(PL_EINVAL, "bad sizes");
+  if (!d_next || !d_counts || !d_best_f || !d_best_b || !d_small_right || !d_small_node)
+    return fail(PL_EINVAL, "NULL buffer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  k_child_sizes<<<(nodes + 127) / 128, 128, 0, s>>>(d_counts, nodes, F, K, d_best_f, d_best_b, d_small_right);
+  note_launch();
+  PL_CUDA_TRY(cudaGetLastError());
+  if (M) {
+    const int grid = (int)std::min<size_t>((M + 255) / 256, (size_t)sm_count() * 8);
+    k_child_select<<<grid, 256, 0, s>>>(d_next, M, d_small_right, d_small_node);
+    note_launch();
+    PL_CUDA_TRY(cudaGetLastError());
+  }
+  return PL_OK;
+}
+
+pl_status paillier_child_subtract(const uint64_t* d_parent_sums, const int32_t* d_parent_counts,
+                                  const uint64_t* d_small_sums, const int32_t* d_small_counts,
+                                  const int32_t* d_small_right, int nodes, int F, int K, uint64_t* d_child_sums,
+                                  int32_t* d_child_counts, void* stream) {
+  using namespace pl;
+  clear_error();
+  if (nodes < 1 || F < 1 || K < 1) return fail(PL_EINVAL, "bad sizes");
+  if (!d_parent_sums || !d_parent_counts || !d_small_sums || !d_small_counts || !d_small_right || !d_child_sums ||
+      !d_child_counts)
+    return fail(PL_EINVAL, "NULL buffer");
+  const size_t per = (size_t)F * K, total = per * nodes;
+  const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)sm_count() * 8);
+  k_child_subtract<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      d_parent_sums, d_parent_counts, d_small_sums, d_small_counts, d_small_right, nodes, per, d_child_sums,
+      d_child_counts);
+  note_launch();
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
 
 pl_status paillier_split_find(const uint64_t* d_sums, const int32_t* d_counts, int nodes, int F, int K, double lambda,
                               double gamma, double min_child_weight, int32_t* d_best_f, int32_t* d_best_b,

@@ -72,6 +72,8 @@ SIGNATURES.update({
     "paillier_decrypt_packed_u64": (_i, [_vp, _vp, _sz, _i, _vp, _vp]),
     "paillier_split_find": (_i, [_vp, _vp, _i, _i, _i, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp, _vp]),
     "paillier_split_apply": (_i, [_vp, _sz, _vp, _vp, _vp, _vp, _vp]),
+    "paillier_child_select": (_i, [_vp, _sz, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
+    "paillier_child_subtract": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp]),
     "pl_server_create": (_i, [_i, _sz, C.POINTER(C.c_void_p)]),
     "pl_server_submit": (_i, [_vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
     "pl_server_poll": (_i, [_vp, C.c_uint64, C.POINTER(_i), C.POINTER(C.c_double), C.POINTER(_i)]),

@@ -328,6 +328,29 @@ def split_apply(bins: torch.Tensor, node: torch.Tensor, best_f: torch.Tensor, be
     return out
 
 
+def child_select(next_node: torch.Tensor, counts: torch.Tensor, best_f: torch.Tensor, best_b: torch.Tensor,
+                 stream=None):
+    """(small_right [parents], small_node [M]): which child of every parent is
+    smaller, and the node array of parents restricted to those children."""
+    nodes, F, K = counts.shape
+    M = next_node.numel()
+    sr = torch.empty(nodes, dtype=torch.int32, device=counts.device)
+    sn = torch.empty_like(next_node)
+    call("paillier_child_select", _ptr(next_node), M, _ptr(counts), nodes, F, K, _ptr(best_f), _ptr(best_b),
+         _ptr(sr), _ptr(sn), _stream(stream))
+    return sr, sn
+
+
+def child_subtract(parent_sums, parent_counts, small_sums, small_counts, small_right, stream=None):
+    """Child-level sums [2 nodes, F, K, 2] and counts [2 nodes, F, K]."""
+    nodes, F, K, _ = parent_sums.shape
+    cs = torch.empty((2 * nodes, F, K, 2), dtype=torch.int64, device=parent_sums.device)
+    cc = torch.empty((2 * nodes, F, K), dtype=torch.int32, device=parent_sums.device)
+    call("paillier_child_subtract", _ptr(parent_sums), _ptr(parent_counts), _ptr(small_sums), _ptr(small_counts),
+         _ptr(small_right), nodes, F, K, _ptr(cs), _ptr(cc), _stream(stream))
+    return cs, cc
+
+
 def get_config(key: Key, op: int):
     la, pa = C.c_int(), C.c_int()
     call("paillier_get_config", key.handle, op, C.byref(la), C.byref(pa))

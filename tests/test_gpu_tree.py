@@ -16,7 +16,7 @@ from paper_2504_03909_b300 import paillier as P, synth
 pytestmark = pytest.mark.gpu
 
 
-def _secure_vs_plain(n_bits, M, F, K, depth, seed, lam=1.0, gamma=0.0, mcw=1.0):
+def _secure_vs_plain(n_bits, M, F, K, depth, seed, lam=1.0, gamma=0.0, mcw=1.0, subtract=False, pack_bits=0):
     p, q = synth.gen_primes(n_bits, seed)
     key = P.Key.from_primes(n_bits, p, q)
     gh = synth.gen_gh(M, seed)
@@ -30,11 +30,27 @@ def _secure_vs_plain(n_bits, M, F, K, depth, seed, lam=1.0, gamma=0.0, mcw=1.0):
     node = torch.zeros(M, dtype=torch.int32, device="cuda")
     ms = [oracle.encode(x) for x in gh.reshape(-1)]
     onode = [0] * M
+    prev = None  # (sums, counts, best_f, best_b) of the parent level
     for lvl in range(depth):
         nn = 1 << lvl
-        hist, cnt = plan.run(ctm, bins_d, node, nn)
-        sums = P.decrypt_u64(key, hist.reshape(-1, 2 * key.L)).view(nn, F, K, 2)
+
+        def decrypt(h):
+            cells = h.reshape(-1, 2 * key.L)
+            if pack_bits:
+                return P.decrypt_packed_u64(key, P.pack(key, cells, pack_bits), cells.shape[0], pack_bits)
+            return P.decrypt_u64(key, cells)
+
+        if subtract and prev is not None:
+            psums, pcnt, pf, pb = prev
+            small_right, small_node = P.child_select(node, pcnt, pf, pb)
+            hist, scnt = plan.run(ctm, bins_d, small_node, nn // 2)
+            ssums = decrypt(hist).view(nn // 2, F, K, 2)
+            sums, cnt = P.child_subtract(psums, pcnt, ssums, scnt, small_right)
+        else:
+            hist, cnt = plan.run(ctm, bins_d, node, nn)
+            sums = decrypt(hist).view(nn, F, K, 2)
         bf, bb, bg = P.split_find(sums, cnt, lam, gamma, mcw)
+        prev = (sums.clone(), cnt.clone(), bf, bb)
         nxt = P.split_apply(bins_d, node, bf, bb)
         P.sync()
         # oracle: plaintext histogram of the same node assignment, same split rule
@@ -54,3 +70,9 @@ def test_secure_tree_equals_plaintext_tree_1024():
 
 def test_secure_tree_equals_plaintext_tree_2048():
     assert _secure_vs_plain(2048, 6000, 8, 64, 5, seed=9, lam=0.5, gamma=0.01, mcw=2.0) > 0
+
+
+def test_secure_tree_with_subtraction_and_packing_equals_plaintext_tree():
+    assert _secure_vs_plain(2048, 6000, 8, 64, 5, seed=9, lam=0.5, gamma=0.01, mcw=2.0, subtract=True,
+                            pack_bits=40) > 0
+    assert _secure_vs_plain(1024, 1500, 5, 16, 4, seed=8, subtract=True) > 0
