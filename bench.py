@@ -488,18 +488,34 @@ def run_batched(args, cfg):
         P.ct_prepare(key, ct, out=ctm)
         if args.splits == "data":
             split_nodes.zero_()
+        parent = None
         for lvl in range(depth):
             nn = 1 << lvl
             if args.splits == "data":
                 node_buf.copy_(split_nodes)
             else:
                 node_buf.copy_(nodes_d[lvl])
-            plan.run(ctm.view(2, M, 2 * L), bins_d, node_buf, nn, hist=hist, count=cnt)
-            if with_decrypt:
+            if parent is not None:
+                # histogram subtraction: only the smaller child of each parent is aggregated and decrypted
+                psums, pcnt, pf, pb = parent
+                small_right, small_node = P.child_select(node_buf, pcnt, pf, pb)
+                node_buf.copy_(small_node)
+                plan.run(ctm.view(2, M, 2 * L), bins_d, node_buf, nn // 2, hist=hist, count=cnt)
+                decrypt_level(nn // 2)
+                lsums, lcnt = P.child_subtract(psums, pcnt, sums[:nn // 2 * F * K * 2].view(nn // 2, F, K, 2),
+                                               cnt[:nn // 2], small_right)
+                node_buf.copy_(split_nodes)
+            else:
+                plan.run(ctm.view(2, M, 2 * L), bins_d, node_buf, nn, hist=hist, count=cnt)
+                if not with_decrypt:
+                    continue
                 decrypt_level(nn)
-                if args.splits == "data" and lvl + 1 < depth:
-                    bf, bb, _ = P.split_find(sums[:nn * F * K * 2].view(nn, F, K, 2), cnt[:nn], 1.0, 0.0, 1.0)
-                    P.split_apply(bins_d, node_buf, bf, bb, out=split_nodes)
+                lsums, lcnt = sums[:nn * F * K * 2].view(nn, F, K, 2), cnt[:nn]
+            if args.splits == "data" and lvl + 1 < depth:
+                bf, bb, _ = P.split_find(lsums, lcnt, 1.0, 0.0, 1.0)
+                P.split_apply(bins_d, node_buf, bf, bb, out=split_nodes)
+                if args.subtract:
+                    parent = (lsums.clone(), lcnt.clone(), bf, bb)
 
     def hist_levels(per_node):
         for lvl in range(depth):
@@ -568,7 +584,7 @@ def run_batched(args, cfg):
                                "pack": prof["pack"],
                                "decrypt": prof["modexp_dec"] + prof["dec_crt"] + prof["unpack"]},
         "decrypted_cells_per_tree": cells,
-        "pack_bits": pack_bits, "pack_slots": slots, "splits": args.splits,
+        "pack_bits": pack_bits, "pack_slots": slots, "splits": args.splits, "subtract": bool(args.subtract),
         "cells_decoded_per_s": cells / ((prof["modexp_dec"] + prof["dec_crt"] + prof["unpack"] + prof["pack"]) * 1e-3),
         "graph": plan.stats(),
         "clocks": clk.summary(),
@@ -689,6 +705,7 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="autotune the launch configurations first (batched)")
     ap.add_argument("--no-compare", action="store_true", help="batched/large: skip the per-node comparator")
     ap.add_argument("--pack-bits", type=int, default=0, help="batched/large: pack cells into B-bit slots before decryption")
+    ap.add_argument("--subtract", action="store_true", help="tree modes with --splits data: histogram subtraction")
     ap.add_argument("--splits", default="beta", choices=["beta", "data"],
                     help="batched/large: Beta(0.5,0.5) splits or splits found on the decrypted histograms")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
