@@ -41,6 +41,10 @@ from paper_2504_03909_b300 import synth  # noqa: E402
 
 METRIC = "2048-bit Paillier enc/s & encrypted-hist ct-mults/s; p50/p99 request ms"
 
+# DRAM bytes (read + write) per encryption of the current k_modexp ENC kernel, from the ncu
+# capture summarised in profiles/k_modexp_enc_2048bit_small.md, keyed by (n_bits, window)
+TRAFFIC_PER_ENC = {(2048, 5): 23.2e3 + 20.6e3}
+
 
 # ----------------------------------------------------------------------------
 # algorithmic work (integer multiply-add halves; a 32x32->64 limb product = 2)
@@ -406,7 +410,7 @@ def run_ours(args, cfg):
             "frac": achieved / peak,
             # DRAM bytes per encryption of this kernel version from the ncu capture summarised in
             # profiles/k_modexp_enc_2048bit_small.md (16,384 encryptions, w = 5), scaled to this launch
-            "traffic": units * (23.2e3 + 20.6e3) if (n_bits == 2048 and w == 5) else None,
+            "traffic": units * TRAFFIC_PER_ENC.get((n_bits, w)) if (n_bits, w) in TRAFFIC_PER_ENC else None,
             "traffic_note": "ncu dram__bytes_read+write of a 16,384-encryption capture, scaled by encryptions",
             "peak_source": "project microbenchmark paillier_imad_peak, best mix, same run",
             "peak_derived_TIMAD_s": sm_count_of(dev) * 64 * 2.032e9 / 1e12,

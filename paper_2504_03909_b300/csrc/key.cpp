@@ -34,6 +34,9 @@ void fill_public(pl_key* k) {
   put(k->n2c.R2, R2, 2 * L);
 }
 
+// lanes x tile of the histogram products: 8x16 for 1024 and 2048 bits, 16x16 for 3072
+pl::AggCfg default_agg(int L) { return {L == 96 ? 16 : 8, 16}; }
+
 // Everything the key holder's kernels need.
 void fill_private(pl_key* k) {
   const int L = k->L, Lh = k->Lh;
@@ -110,11 +113,13 @@ void fill_private(pl_key* k) {
     k->dec.q_np = plh::neg_inv32(q.d[0]);
     k->dec.Lh = Lh;
   }
-  // default launch configuration by key size
-  const int T_half = (L == 32) ? 2 : 4;  // 16 or 24 limbs per lane
-  k->enc_cfg = {T_half, 5};
-  k->dec_cfg = {T_half, 5};
-  k->agg_cfg = {(L == 32) ? 4 : 8, 64};
+  // default launch configuration by key size: the autotuner's choice on B300
+  // (148 SMs): lanes x window 2x5 / 4x6 / 8x6 for 1024 / 2048 / 3072 bits
+  const int T_half = (L == 32) ? 2 : (L == 64 ? 4 : 8);
+  const int w = (L == 32) ? 5 : 6;
+  k->enc_cfg = {T_half, w};
+  k->dec_cfg = {T_half, w};
+  k->agg_cfg = default_agg(L);
 }
 
 bool check_prime_shape(const Big& x, int half_bits) {
@@ -245,7 +250,7 @@ pl_status paillier_key_import_public(int n_bits, const uint32_t* h_n, pl_key** o
   k->priv = false;
   k->n = n;
   fill_public(k);
-  k->agg_cfg = {(k->L == 32) ? 4 : 8, 64};
+  k->agg_cfg = default_agg(k->L);
   *out = k;
   return PL_OK;
 }
