@@ -113,10 +113,11 @@ void fill_private(pl_key* k) {
     k->dec.q_np = plh::neg_inv32(q.d[0]);
     k->dec.Lh = Lh;
   }
-  // default launch configuration by key size: the autotuner's choice on B300
-  // (148 SMs): lanes x window 2x5 / 4x6 / 8x6 for 1024 / 2048 / 3072 bits
+  // default launch configuration by key size, from measurements on B300 (148
+  // SMs): lanes 2 / 4 / 8 for 1024 / 2048 / 3072 bits, 5-bit windows (6-bit
+  // windows double the window tables, which then miss L2 more at full size)
   const int T_half = (L == 32) ? 2 : (L == 64 ? 4 : 8);
-  const int w = (L == 32) ? 5 : 6;
+  const int w = 5;
   k->enc_cfg = {T_half, w};
   k->dec_cfg = {T_half, w};
   k->agg_cfg = default_agg(L);

@@ -114,8 +114,9 @@ pl_status paillier_autotune(pl_key* key, int op, const char* cache_path, void* s
   int* st = status_word([] { int d = 0; cudaGetDevice(&d); return d; }());
   if (!st) return fail(PL_ECUDA, "status word unavailable");
   const int L = key->L;
-  // synthetic inputs, sized to a few waves of the GPU
-  const size_t count = (size_t)sms * 64;                   // values (encrypt / decrypt)
+  // synthetic inputs, sized to many waves of the GPU so that the window
+  // tables' cache behaviour is that of a full-size launch
+  const size_t count = (size_t)sms * 256;                  // values (encrypt / decrypt)
   const size_t M = (size_t)sms * 256, F = 8, K = 256;      // histogram
   std::vector<void*> bufs;
   auto alloc = [&](size_t bytes) -> void* {
@@ -153,7 +154,7 @@ pl_status paillier_autotune(pl_key* key, int op, const char* cache_path, void* s
       rc = run();  // warm-up (also loads the kernel)
       if (rc) break;
       cudaEventRecord(e0, s);
-      for (int r = 0; r < 2 && !rc; ++r) rc = run();
+      for (int r = 0; r < 1 && !rc; ++r) rc = run();
       cudaEventRecord(e1, s);
       if (rc) break;
       cudaEventSynchronize(e1);
@@ -202,7 +203,7 @@ pl_status paillier_autotune(pl_key* key, int op, const char* cache_path, void* s
   // and every uint8 bin is < K = 256)
   rc = paillier_set_config(key, op, best.lanes, best.param);
   if (rc) return rc;
-  cache_append(cache_path, op, key->n_bits, sms, best, best_ms / 2);
+  cache_append(cache_path, op, key->n_bits, sms, best, op == PL_OP_HIST ? best_ms / 2 : best_ms);
   if (lanes) *lanes = best.lanes;
   if (param) *param = best.param;
   return PL_OK;
