@@ -642,7 +642,7 @@ def run_serving(args, cfg):
 
     def submit(srv, rq):
         return srv.submit(keys[rq["nb"]], ctms[rq["nb"]], rq["M"], rq["F"], rq["K"], bins[rq["party"]][rq["K"]],
-                          gh_stride=MMAX, bins_stride=MMAX)
+                          gh_stride=MMAX, bins_stride=MMAX, pack_bits=args.pack_bits)
 
     srv = P.Server(slots=args.slots, hbm_budget=budget)
     # warm-up and closed-loop capacity (requests/s with every slot busy)
@@ -687,7 +687,8 @@ def run_serving(args, cfg):
         "config": {"workload": "serving: 4 passive parties, Poisson arrivals, histogram + CRT-decrypt requests, "
                                "M log-uniform [1e3, 1e6], F uniform [8, 64], K uniform {64..256 step 32}, "
                                "2048/3072-bit keys p = 0.5, resident ciphertexts", "slots": args.slots,
-                   "hbm_budget_bytes": budget, "offered_load": args.load, "requests": args.requests},
+                   "hbm_budget_bytes": budget, "offered_load": args.load, "requests": args.requests,
+                   "pack_bits": args.pack_bits},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "throughput_req_per_s": len(lat) / wall,
         "capacity_req_per_s": capacity, "arrival_rate_req_per_s": rate,

@@ -49,6 +49,9 @@ typedef struct pl_request {
    * decrypted fixed-point sums [num_nodes][F][K][2] and counts [num_nodes][F][K]. */
   uint64_t* h_sums;
   int32_t* h_counts;
+  /* 0: decrypt every cell; B in [1, 64]: pack the cells into B-bit slots
+   * before decrypting (see paillier_pack.h; every cell sum must be < 2^B). */
+  int pack_bits;
 } pl_request;
 
 #define PL_REQ_QUEUED    0

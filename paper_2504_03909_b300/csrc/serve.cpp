@@ -34,7 +34,7 @@ struct Slot {
   pl::Scratch scratch;
   int* d_status = nullptr;
   int* h_status = nullptr;
-  void* allocs[4] = {};
+  void* allocs[6] = {};
 };
 
 size_t round_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -46,7 +46,13 @@ size_t request_bytes(const pl_request& r) {
   size_t b = round_up(cells * 2 * L * 4) + round_up((size_t)r.num_nodes * r.F * r.K * 4) + round_up(cells * 8);
   if (!r.d_node) b += round_up(r.M * 4);
   const pl::HistLayout h = pl::hist_layout(r.M, r.F, r.num_nodes * r.K, r.key->agg_cfg.tile, (int)(2 * L));
-  b += std::max(h.bytes, pl::decrypt_scratch_bytes(r.key, cells));
+  size_t dec_cells = cells;
+  if (r.pack_bits > 0) {
+    const size_t slots = (size_t)(r.key->n_bits - 2) / (size_t)r.pack_bits;
+    dec_cells = (cells + slots - 1) / slots;
+    b += round_up(dec_cells * 2 * L * 4) + round_up(dec_cells * L * 4);  // packed ciphertexts + plaintexts
+  }
+  b += std::max(h.bytes, pl::decrypt_scratch_bytes(r.key, dec_cells));
   return b;
 }
 
@@ -111,7 +117,17 @@ struct pl_server {
       rc = launch_hist(key, r.d_ctm, r.M, r.gh_stride, r.d_bins, r.bins_stride, r.F, r.K, node, r.num_nodes, hist,
                        counts, false, sl.d_status, s, &sl.scratch);
     }
-    if (rc == PL_OK) rc = launch_decrypt(key, hist, cells, sums, true, sl.d_status, s, &sl.scratch);
+    if (rc == PL_OK && r.pack_bits > 0) {
+      const int slots = (key->n_bits - 2) / r.pack_bits;
+      const size_t npacked = (cells + slots - 1) / slots;
+      auto* packed = static_cast<uint32_t*>(amalloc(4, npacked * 2 * L * 4));
+      auto* plain = static_cast<uint32_t*>(amalloc(5, npacked * L * 4));
+      if (rc == PL_OK) rc = launch_pack(key, hist, cells, slots, r.pack_bits, packed, s);
+      if (rc == PL_OK) rc = launch_decrypt(key, packed, npacked, plain, false, sl.d_status, s, &sl.scratch);
+      if (rc == PL_OK) rc = launch_unpack(plain, (int)L, cells, slots, r.pack_bits, sums, sl.d_status, s);
+    } else if (rc == PL_OK) {
+      rc = launch_decrypt(key, hist, cells, sums, true, sl.d_status, s, &sl.scratch);
+    }
     if (rc == PL_OK) {
       cudaMemcpyAsync(r.h_sums, sums, cells * 8, cudaMemcpyDeviceToHost, s);
       cudaMemcpyAsync(r.h_counts, counts, ncell * 4, cudaMemcpyDeviceToHost, s);
@@ -230,6 +246,7 @@ pl_status pl_server_submit(pl_server* srv, const pl_request* req, uint64_t* tick
   if (!r.d_ctm || !r.d_bins || !r.h_sums || !r.h_counts) return fail(PL_EINVAL, "NULL buffer");
   if (reinterpret_cast<uintptr_t>(r.d_ctm) & 15u) return fail(PL_EINVAL, "d_ctm must be 16-byte aligned");
   if (!agg_supported(2 * r.key->L, r.key->agg_cfg.T)) return fail(PL_EINVAL, "key configuration not supported");
+  if (r.pack_bits < 0 || r.pack_bits > 64) return fail(PL_EINVAL, "pack_bits must be 0..64");
   Req q;
   q.r = r;
   q.bytes = request_bytes(r);

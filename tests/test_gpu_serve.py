@@ -82,6 +82,20 @@ def test_mix_equals_alone_equals_direct(data):
     alone.close()
 
 
+def test_packed_requests_equal_unpacked(data):
+    srv = P.Server(slots=3, hbm_budget=8 << 30)
+    for rq in REQUESTS[:4]:
+        nb, M, F, K, use_node = rq
+        d = data[nb]
+        node = d["node"] if use_node else None
+        kw = dict(node=node, num_nodes=4 if use_node else 1, gh_stride=MFULL, bins_stride=MFULL)
+        t1, s1, c1 = srv.submit(d["key"], d["ctm"], M, F, K, d["bins"][K], **kw)
+        t2, s2, c2 = srv.submit(d["key"], d["ctm"], M, F, K, d["bins"][K], pack_bits=40, **kw)
+        assert srv.wait(t1)[0] == native.REQ_DONE and srv.wait(t2)[0] == native.REQ_DONE
+        assert torch.equal(s1, s2) and torch.equal(c1, c2)
+    srv.close()
+
+
 def test_served_sums_equal_plaintext_histogram(data):
     srv = P.Server(slots=2, hbm_budget=4 << 30)
     rq = (1024, 2500, 5, 16, True)
