@@ -644,9 +644,21 @@ def run_serving(args, cfg):
         return srv.submit(keys[rq["nb"]], ctms[rq["nb"]], rq["M"], rq["F"], rq["K"], bins[rq["party"]][rq["K"]],
                           gh_stride=MMAX, bins_stride=MMAX, pack_bits=args.pack_bits)
 
+    def work(rq):
+        """Modelled multiply-adds of a request: its histogram products mod n^2 plus
+        its decryptions (per packed ciphertext when packing)."""
+        L = rq["nb"] // 32
+        cells = 2 * rq["F"] * rq["K"]
+        if args.pack_bits:
+            slots = (rq["nb"] - 2) // args.pack_bits
+            dec = -(-cells // slots) * dec_imad(rq["nb"], 5) + cells * (args.pack_bits + 2) * mont_imad(2 * L)
+        else:
+            dec = cells * dec_imad(rq["nb"], 5)
+        return 2 * rq["M"] * rq["F"] * mont_imad(2 * L) + dec
+
     srv = P.Server(slots=args.slots, hbm_budget=budget)
-    # warm-up and closed-loop capacity (requests/s with every slot busy)
-    warm = [draw() for _ in range(max(2 * args.slots, 8))]
+    # warm-up, then the closed-loop capacity in work units (every slot busy)
+    warm = [draw() for _ in range(max(4 * args.slots, 32))]
     for rq in warm[:args.slots]:
         t, _, _ = submit(srv, rq)
         srv.wait(t)
@@ -654,7 +666,9 @@ def run_serving(args, cfg):
     tick = [submit(srv, rq)[0] for rq in warm]
     for t in tick:
         srv.wait(t)
-    capacity = len(warm) / (time.perf_counter() - t0)
+    work_rate = sum(work(rq) for rq in warm) / (time.perf_counter() - t0)
+    mean_work = float(np.mean([work(draw()) for _ in range(20000)]))
+    capacity = work_rate / mean_work
     rate = args.load * capacity
     reqs = [draw() for _ in range(args.requests)]
     gaps = [rng.expovariate(rate) for _ in reqs]
