@@ -220,6 +220,64 @@ def oracle_rate(cfg, p, q, gh, r, samples: int, steps: int = 1):
     return done / wall, wall, len(per), ndec
 
 
+def _oracle_op_worker(args):
+    """Times one oracle operation type on a few inputs; returns (ops, seconds)."""
+    import oracle
+    op, p, q, vals = args
+    pub, priv = oracle.keypair(p, q)
+    t0 = time.perf_counter()
+    if op == "encrypt":
+        for m, r in vals:
+            oracle.encrypt(pub, m, r)
+    elif op == "mult":
+        acc = 1
+        for c in vals:
+            acc = oracle.add(pub, acc, c)
+    elif op == "decrypt":
+        for c in vals:
+            oracle.decrypt(priv, c)
+    elif op == "decrypt_crt":
+        for c in vals:
+            oracle.decrypt_crt(priv, c)
+    return len(vals), time.perf_counter() - t0
+
+
+def run_oracle_rates(args):
+    """Oracle rates per operation and key size, one core and all host cores, on
+    bounded seeded samples, with the per-workload extrapolation (context only)."""
+    import multiprocessing as mp
+    import random as pyrandom
+    cores = len(os.sched_getaffinity(0))
+    per_core = {1024: 6, 2048: 3, 3072: 2}
+    out = {"cores": cores, "rates": {}}
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        for nb in (1024, 2048, 3072):
+            p, q = synth.gen_primes(nb, 7)
+            n = p * q
+            rng = pyrandom.Random(nb)
+            import oracle
+            pub = oracle.PublicKey(n)
+            k = per_core[nb]
+            enc_in = [(rng.randrange(1 << 25), rng.randrange(1, n)) for _ in range(k)]
+            cts = [oracle.encrypt(pub, m, r) for m, r in enc_in]
+            mult_in = [rng.randrange(1, n * n) for _ in range(2000)]
+            rates = {}
+            for op, vals in (("encrypt", enc_in), ("mult", mult_in), ("decrypt", cts), ("decrypt_crt", cts)):
+                n1, t1 = _oracle_op_worker((op, p, q, vals))
+                res = pool.map(_oracle_op_worker, [(op, p, q, vals)] * cores)
+                wall = max(t for _, t in res)
+                rates[op] = {"one_core_per_s": n1 / t1, "all_cores_per_s": sum(c for c, _ in res) / wall}
+            out["rates"][nb] = rates
+    r2 = out["rates"][2048]
+    lv = synth.CONFIGS["level"]
+    out["extrapolated_level_step_s_all_cores"] = (2 * lv["M"] / r2["encrypt"]["all_cores_per_s"] +
+                                                  2 * lv["M"] * lv["F"] / r2["mult"]["all_cores_per_s"] +
+                                                  lv["F"] * lv["K"] * 2 / r2["decrypt"]["all_cores_per_s"])
+    out["note"] = "oracle as it stands (lambda-form decrypt is the definition); bounded samples; context only"
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args, cfg):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -717,7 +775,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="level", choices=["level", "toy", "level_small", "batched", "serving", "large"])
+    ap.add_argument("--config", default="level",
+                    choices=["level", "toy", "level_small", "batched", "serving", "large", "oracle"])
     ap.add_argument("--requests", type=int, default=300, help="serving: timed requests")
     ap.add_argument("--slots", type=int, default=8, help="serving: concurrent request slots")
     ap.add_argument("--load", type=float, default=0.7, help="serving: offered load / measured capacity")
@@ -731,7 +790,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     cfg = synth.CONFIGS.get(args.config, {})
-    if args.impl == "reference":
+    if args.config == "oracle":
+        run_oracle_rates(args)
+    elif args.impl == "reference":
         run_reference(args, cfg)
     elif args.config == "batched":
         run_batched(args, cfg)
