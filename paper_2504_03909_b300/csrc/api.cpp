@@ -1,4 +1,6 @@
 // C-ABI entry points: argument checks, then the launchers.
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
 #include <cstring>
 #include <mutex>
@@ -132,6 +134,7 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void adjust_launch_count(long long delta) { g_launches.fetch_add((unsigned long long)delta, std::memory_order_relaxed); }
 
 ProfScope::ProfScope(const char* kernel, cudaStream_t stream) : name(kernel), s(stream) {
+  nvtxRangePushA(kernel);  // a named range around every launch, for timeline tools
   if (!g_prof_on.load(std::memory_order_relaxed)) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
@@ -140,6 +143,7 @@ ProfScope::ProfScope(const char* kernel, cudaStream_t stream) : name(kernel), s(
 }
 
 ProfScope::~ProfScope() {
+  nvtxRangePop();
   note_launch();
   if (!e0) return;
   cudaEvent_t e1;
