@@ -71,6 +71,34 @@ pl_status paillier_child_subtract(const uint64_t* d_parent_sums, const int32_t* 
                                   const int32_t* d_small_right, int nodes, int F, int K, uint64_t* d_child_sums,
                                   int32_t* d_child_counts, void* stream);
 
+/* ------------------------------------------------ inference (Sec. IV.A) --
+ * A partially-saved model: every party keeps the splits of the nodes whose
+ * feature it owns and "nan" for the others.  Inference runs the model jointly:
+ * each party evaluates its own splits on its own features, and the decisions
+ * are combined by walking the tree; the prediction equals the centralized
+ * model's.  Trees here are complete binary trees in level order: node v of
+ * level l is index (2^l - 1) + v, its children 2v and 2v + 1 of level l + 1. */
+
+/* One party's decisions: for every tree node t (level order, `nodes` in all)
+ * whose feature d_tree_f[t] lies in [f_lo, f_lo + F_party), and every sample
+ * i: d_go_right[t * M + i] = (d_bins_party[(f - f_lo) * M + i] > d_tree_b[t]).
+ * Entries of nodes owned by other parties or leaves (d_tree_f[t] < 0) are not
+ * written. */
+pl_status paillier_tree_decide(const uint8_t* d_bins_party, int F_party, int f_lo, size_t M, const int32_t* d_tree_f,
+                               const int32_t* d_tree_b, int nodes, uint8_t* d_go_right, void* stream);
+
+/* Routing with the combined decisions: from the root, follow d_go_right of
+ * each split node until a leaf (d_tree_f < 0) or `depth` levels; d_leaf[i] is
+ * the level-order index of the node reached. */
+pl_status paillier_tree_route(const uint8_t* d_go_right, size_t M, const int32_t* d_tree_f, int depth,
+                              int32_t* d_leaf, void* stream);
+
+/* XGBoost leaf weights w = -G / (H + lambda) of `nodes` nodes from their
+ * decrypted sums [nodes][F][K][2] and counts [nodes][F][K] (feature 0's bins
+ * hold every sample of the node). */
+pl_status paillier_leaf_weights(const uint64_t* d_sums, const int32_t* d_counts, int nodes, int F, int K,
+                                double lambda, double* d_w, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

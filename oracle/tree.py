@@ -70,3 +70,25 @@ def split_apply(bins, node, best_f, best_b):
         else:
             out.append(2 * v + (1 if int(bins[best_f[v]][i]) > best_b[v] else 0))
     return out
+
+
+def predict_leaf(bins, tree_f, tree_b, depth):
+    """Centralized inference (the full model): level-order index of the node each
+    sample reaches, following "bin <= b goes left" until a leaf or the last level."""
+    out = []
+    for i in range(len(bins[0])):
+        v, first = 0, 0
+        for lvl in range(depth):
+            t = first + v
+            if tree_f[t] < 0 or lvl == depth - 1:
+                break
+            v = 2 * v + (1 if int(bins[tree_f[t]][i]) > tree_b[t] else 0)
+            first = 2 * first + 1
+        out.append(first + v)
+    return out
+
+
+def leaf_weight(S_g: int, S_h: int, count: int, lam: float) -> float:
+    """XGBoost's optimal leaf weight -G / (H + lambda) from fixed-point sums."""
+    G, H = _dec(S_g, count), _dec(S_h, count)
+    return -G / (H + lam)

@@ -126,10 +126,91 @@ __global__ void k_child_subtract(const uint64_t* __restrict__ ps, const int32_t*
   }
 }
 
+__global__ void k_tree_decide(const uint8_t* __restrict__ bins, int F_party, int f_lo, size_t M,
+                              const int32_t* __restrict__ tf, const int32_t* __restrict__ tb, int nodes,
+                              uint8_t* __restrict__ go_right) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
+    for (int t = 0; t < nodes; ++t) {
+      const int f = tf[t];
+      if (f < f_lo || f >= f_lo + F_party) continue;
+      go_right[(size_t)t * M + i] = bins[(size_t)(f - f_lo) * M + i] > (uint8_t)tb[t] ? 1 : 0;
+    }
+  }
+}
+
+__global__ void k_tree_route(const uint8_t* __restrict__ go_right, size_t M, const int32_t* __restrict__ tf,
+                             int depth, int32_t* __restrict__ leaf) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
+    int v = 0, first = 0;  // node v of level l has level-order index first + v, first = 2^l - 1
+    for (int l = 0; l < depth; ++l) {
+      const int t = first + v;
+      if (tf[t] < 0 || l == depth - 1) break;
+      v = 2 * v + go_right[(size_t)t * M + i];
+      first = 2 * first + 1;
+    }
+    leaf[i] = first + v;
+  }
+}
+
+__global__ void k_leaf_weights(const uint64_t* __restrict__ sums, const int32_t* __restrict__ counts, int nodes,
+                               int F, int K, double lambda, double* __restrict__ w) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nodes) return;
+  const uint64_t* s = sums + ((size_t)v * F) * K * 2;  // feature 0
+  const int32_t* c = counts + ((size_t)v * F) * K;
+  uint64_t Sg = 0, Sh = 0;
+  long long C = 0;
+  for (int b = 0; b < K; ++b) { Sg += s[2 * b]; Sh += s[2 * b + 1]; C += c[b]; }
+  const double G = fx(Sg, C), H = fx(Sh, C);
+  w[v] = -__ddiv_rn(G, __dadd_rn(H, lambda));
+}
+
 }  // namespace
 }  // namespace pl
 
 extern "C" {
+
+pl_status paillier_tree_decide(const uint8_t* d_bins_party, int F_party, int f_lo, size_t M, const int32_t* d_tree_f,
+                               const int32_t* d_tree_b, int nodes, uint8_t* d_go_right, void* stream) {
+  using namespace pl;
+  clear_error();
+  if (F_party < 1 || f_lo < 0 || nodes < 1) return fail(PL_EINVAL, "bad sizes");
+  if (M == 0) return PL_OK;
+  if (!d_bins_party || !d_tree_f || !d_tree_b || !d_go_right) return fail(PL_EINVAL, "NULL buffer");
+  const int grid = (int)std::min<size_t>((M + 255) / 256, (size_t)sm_count() * 8);
+  k_tree_decide<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_bins_party, F_party, f_lo, M, d_tree_f,
+                                                                      d_tree_b, nodes, d_go_right);
+  note_launch();
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
+
+pl_status paillier_tree_route(const uint8_t* d_go_right, size_t M, const int32_t* d_tree_f, int depth,
+                              int32_t* d_leaf, void* stream) {
+  using namespace pl;
+  clear_error();
+  if (depth < 1 || depth > 30) return fail(PL_EINVAL, "depth must be 1..30");
+  if (M == 0) return PL_OK;
+  if (!d_go_right || !d_tree_f || !d_leaf) return fail(PL_EINVAL, "NULL buffer");
+  const int grid = (int)std::min<size_t>((M + 255) / 256, (size_t)sm_count() * 8);
+  k_tree_route<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_go_right, M, d_tree_f, depth, d_leaf);
+  note_launch();
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
+
+pl_status paillier_leaf_weights(const uint64_t* d_sums, const int32_t* d_counts, int nodes, int F, int K,
+                                double lambda, double* d_w, void* stream) {
+  using namespace pl;
+  clear_error();
+  if (nodes < 1 || F < 1 || K < 1) return fail(PL_EINVAL, "bad sizes");
+  if (!d_sums || !d_counts || !d_w) return fail(PL_EINVAL, "NULL buffer");
+  k_leaf_weights<<<(nodes + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(d_sums, d_counts, nodes, F, K,
+                                                                                     lambda, d_w);
+  note_launch();
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
 
 pl_status paillier_child_select(const int32_t* d_next, size_t M, const int32_t* d_counts, int nodes, int F, int K,
                                 const int32_t* d_best_f, const int32_t* d_best_b, int32_t* d_small_right,

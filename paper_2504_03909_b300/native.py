@@ -73,6 +73,9 @@ SIGNATURES.update({
     "paillier_decrypt_packed_u64": (_i, [_vp, _vp, _sz, _i, _vp, _vp]),
     "paillier_split_find": (_i, [_vp, _vp, _i, _i, _i, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp, _vp]),
     "paillier_split_apply": (_i, [_vp, _sz, _vp, _vp, _vp, _vp, _vp]),
+    "paillier_tree_decide": (_i, [_vp, _i, _i, _sz, _vp, _vp, _i, _vp, _vp]),
+    "paillier_tree_route": (_i, [_vp, _sz, _vp, _i, _vp, _vp]),
+    "paillier_leaf_weights": (_i, [_vp, _vp, _i, _i, _i, C.c_double, _vp, _vp]),
     "paillier_child_select": (_i, [_vp, _sz, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
     "paillier_child_subtract": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp]),
     "pl_server_create": (_i, [_i, _sz, C.POINTER(C.c_void_p)]),

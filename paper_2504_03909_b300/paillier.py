@@ -352,6 +352,30 @@ def child_subtract(parent_sums, parent_counts, small_sums, small_counts, small_r
     return cs, cc
 
 
+def tree_decide(bins_party: torch.Tensor, f_lo: int, tree_f: torch.Tensor, tree_b: torch.Tensor,
+                go_right: torch.Tensor, stream=None):
+    """One party fills go_right [nodes, M] (uint8) for the tree nodes on its features."""
+    F_party, M = bins_party.shape
+    call("paillier_tree_decide", _ptr(bins_party), F_party, f_lo, M, _ptr(tree_f), _ptr(tree_b), tree_f.numel(),
+         _ptr(go_right), _stream(stream))
+    return go_right
+
+
+def tree_route(go_right: torch.Tensor, tree_f: torch.Tensor, depth: int, stream=None):
+    """Level-order index of the node every sample reaches."""
+    M = go_right.shape[1]
+    leaf = torch.empty(M, dtype=torch.int32, device=go_right.device)
+    call("paillier_tree_route", _ptr(go_right), M, _ptr(tree_f), depth, _ptr(leaf), _stream(stream))
+    return leaf
+
+
+def leaf_weights(sums: torch.Tensor, counts: torch.Tensor, lam: float = 1.0, stream=None):
+    nodes, F, K, _ = sums.shape
+    w = torch.empty(nodes, dtype=torch.float64, device=sums.device)
+    call("paillier_leaf_weights", _ptr(sums), _ptr(counts), nodes, F, K, lam, _ptr(w), _stream(stream))
+    return w
+
+
 def get_config(key: Key, op: int):
     la, pa = C.c_int(), C.c_int()
     call("paillier_get_config", key.handle, op, C.byref(la), C.byref(pa))

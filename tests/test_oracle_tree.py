@@ -64,3 +64,17 @@ def test_split_apply_leaves_and_excluded():
     bins = np.array([[0, 5, 9, 3]])
     node = np.array([0, 0, -1, 1])
     assert tree.split_apply(bins, node, [0, -1], [4, -1]) == [0, 1, -1, -1]
+
+
+def test_predict_leaf_and_leaf_weight():
+    # depth-2 tree: root splits on feature 1 at bin 3; left child is a leaf; right child splits feature 0 at bin 0
+    tree_f = [1, -1, 0]
+    tree_b = [3, -1, 0]
+    bins = [[0, 1, 0, 5], [2, 4, 9, 3]]
+    # sample 0: f1=2 <= 3 -> left (node 1, leaf); sample 1: f1=4 > 3 -> node 2, f0=1 > 0 -> right -> level 2 node 3 -> index 6
+    # sample 2: f1=9 -> node 2, f0=0 <= 0 -> index 5; sample 3: f1=3 -> left -> index 1
+    assert tree.predict_leaf(bins, tree_f + [-1] * 4, tree_b + [-1] * 4, 3) == [1, 6, 5, 1]
+    # weight: G = -1.5, H = 0.5, lambda = 1 -> 1.0 ; encoded sums of 3 samples
+    S_g = int((-1.5 + 3) * OFF)
+    S_h = int((0.5 + 3) * OFF)
+    assert tree.leaf_weight(S_g, S_h, 3, 1.0) == 1.0
