@@ -244,3 +244,80 @@ def make_bins(cfg: dict) -> np.ndarray:
     if cfg["bins"] == "uniform":
         return gen_bins_uniform(cfg["F"], cfg["M"], cfg["K"], seed)
     return gen_bins_quantile(cfg["F"], cfg["M"], cfg["K"], seed, dist=cfg["bins"])
+
+
+# ----------------------------------------------------------------------------
+# secure horizontal pattern (Sec. III.A, III.C): CKKS inputs
+
+_TAG_CKKS = 71
+
+
+def ckks_prime(log_n: int, bits: int = 60) -> int:
+    """The largest prime q < 2^bits with q = 1 mod 2N (N = 2^log_n): an
+    NTT-friendly modulus.  Deterministic (Miller-Rabin with fixed bases that
+    decide primality below 3.3e24)."""
+    two_n = 1 << (log_n + 1)
+    q = ((1 << bits) - 1) // two_n * two_n + 1
+    bases = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41)
+    while True:
+        d, s = q - 1, 0
+        while d % 2 == 0:
+            d //= 2
+            s += 1
+        ok = True
+        for a in bases:
+            x = pow(a, d, q)
+            if x in (1, q - 1):
+                continue
+            for _ in range(s - 1):
+                x = x * x % q
+                if x == q - 1:
+                    break
+            else:
+                ok = False
+                break
+        if ok:
+            return q
+        q -= two_n
+
+
+def ckks_secret(N: int, seed: int) -> np.ndarray:
+    """Ternary secret key: coefficients uniform in {-1, 0, 1} (int8 [N])."""
+    return _rng(seed, _TAG_CKKS).integers(-1, 2, size=N, dtype=np.int8)
+
+
+def ckks_uniform(N: int, q: int, seed: int, tag: int = 0) -> np.ndarray:
+    """Uniform polynomial mod q (uint64 [N]), by rejection from 64-bit draws."""
+    rng = _rng(seed, _TAG_CKKS * 100 + tag)
+    out = np.empty(0, dtype=np.uint64)
+    limit = (1 << 64) - ((1 << 64) % q)
+    while out.size < N:
+        x = np.asarray(rng.bit_generator.random_raw(N), dtype=np.uint64)
+        x = x[x < np.uint64(limit)] % np.uint64(q)
+        out = np.concatenate([out, x])
+    return out[:N]
+
+
+def ckks_gaussian(shape, seed: int, tag: int, sigma: float = 3.2) -> np.ndarray:
+    """Rounded Gaussian errors (int32), sigma 3.2, clipped at 6 sigma."""
+    e = np.rint(_rng(seed, _TAG_CKKS * 100 + tag).normal(0.0, sigma, size=shape))
+    return np.clip(e, -19, 19).astype(np.int32)
+
+
+def ckks_ternary(shape, seed: int, tag: int) -> np.ndarray:
+    return _rng(seed, _TAG_CKKS * 100 + tag).integers(-1, 2, size=shape, dtype=np.int8)
+
+
+def horizontal_histograms(M: int, F: int, K: int, clients: int, seed: int):
+    """Local G/H histograms of `clients` row partitions of one synthetic data
+    set (Table III's even split): float64 [clients][F][K][2]."""
+    gh = gen_gh(M, seed).astype(np.float64)
+    bins = gen_bins_quantile(F, M, K, seed)
+    bounds = np.linspace(0, M, clients + 1).astype(int)
+    out = np.zeros((clients, F, K, 2))
+    for c in range(clients):
+        lo, hi = bounds[c], bounds[c + 1]
+        for f in range(F):
+            for k in range(2):
+                out[c, f, :, k] = np.bincount(bins[f, lo:hi], weights=gh[k, lo:hi], minlength=K)
+    return out
