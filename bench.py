@@ -299,6 +299,221 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# secure horizontal pattern (CKKS)
+
+METRIC_H = "CKKS secure-horizontal rounds/s (clients encrypt local G/H histograms, server adds, client decrypts)"
+
+
+def horizontal_inputs(cfg):
+    """Local histograms packed into complex slots (G real, H imaginary), the key
+    material and every client's encryption randomness (all seeded)."""
+    log_n, clients, F, K = cfg["log_n"], cfg["clients"], cfg["F"], cfg["K"]
+    N = 1 << log_n
+    slots = N // 2
+    cells = F * K
+    msgs = -(-cells // slots)
+    hist = synth.horizontal_histograms(cfg["M"], F, K, clients, cfg["seed"])
+    flat = np.zeros((clients, msgs * slots, 2))
+    flat[:, :cells] = hist.reshape(clients, cells, 2)
+    flat = flat.reshape(clients * msgs, slots, 2)
+    q = synth.ckks_prime(log_n)
+    seed = cfg["seed"]
+    key = (synth.ckks_secret(N, seed), synth.ckks_uniform(N, q, seed), synth.ckks_gaussian(N, seed, 1))
+    rnd = (synth.ckks_ternary((clients * msgs, N), seed, 2), synth.ckks_gaussian((clients * msgs, N), seed, 3),
+           synth.ckks_gaussian((clients * msgs, N), seed, 4))
+    return N, q, msgs, cells, hist, flat, key, rnd
+
+
+def horizontal_config(cfg, msgs):
+    return {"workload": f"secure horizontal round: {cfg['clients']} clients, {cfg['M']:,} samples split evenly, "
+                        f"J x K = {cfg['F']} x {cfg['K']} G/H histograms packed into {msgs} plaintexts per client "
+                        f"(N = {1 << cfg['log_n']}, one 60-bit prime, scale 2^{cfg['scale_bits']}); step = "
+                        "encode + encrypt every client's plaintexts, server sum, decrypt + decode",
+            "clients": cfg["clients"], "M": cfg["M"], "F": cfg["F"], "K": cfg["K"], "N": 1 << cfg["log_n"],
+            "l2": "L2 flushed (256 MB write) before every timed step; steps timed one by one",
+            "parallelism": "replica per GPU"}
+
+
+def _horizontal_oracle_sample(cfg):
+    """The oracle on one client plaintext (encode + encrypt) and one aggregate
+    (sum of the clients' ciphertexts, decrypt + decode); returns seconds per
+    round scaled to the whole round and the seconds spent."""
+    from oracle import ckks as ock
+    N, q, msgs, cells, hist, flat, (s, a, e), (v, e0, e1) = horizontal_inputs(cfg)
+    scale = 2.0 ** cfg["scale_bits"]
+    clients = cfg["clients"]
+    b = ock.keygen(s, a, e, q)
+    t0 = time.perf_counter()
+    m = ock.encode(flat[0, :, 0] + 1j * flat[0, :, 1], N, scale)
+    c = ock.encrypt(b, a, m, v[0], e0[0], e1[0], q)
+    t1 = time.perf_counter()
+    tot = c
+    for _ in range(clients - 1):
+        tot = ock.add(tot, c, q)
+    t2 = time.perf_counter()
+    ock.decode(ock.centre(ock.decrypt(tot, s, q), q), N, scale)
+    t3 = time.perf_counter()
+    per_round = clients * msgs * (t1 - t0) + msgs * (t2 - t1) + msgs * (t3 - t2)
+    return per_round, t3 - t0
+
+
+def run_horizontal(args, cfg):
+    import torch
+    from paper_2504_03909_b300 import ckks as G, native
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    clients = cfg["clients"]
+    N, q, msgs, cells, hist, flat, (s, a, e), (v, e0, e1) = horizontal_inputs(cfg)
+    scale = 2.0 ** cfg["scale_bits"]
+    ctx = G.Context(cfg["log_n"], q, scale)
+    B = clients * msgs
+    pin = lambda x, dt=None: (torch.from_numpy(np.ascontiguousarray(x)).view(dt) if dt else
+                              torch.from_numpy(np.ascontiguousarray(x))).pin_memory()
+    h_re, h_im = pin(flat[..., 0]), pin(flat[..., 1])
+    h_v, h_e0, h_e1 = pin(v), pin(e0), pin(e1)
+    re_d, im_d, v_d, e0_d, e1_d = (t.to(dev) for t in (h_re, h_im, h_v, h_e0, h_e1))
+    s_d = torch.from_numpy(s).to(dev)
+    a_d = torch.from_numpy(a.view(np.int64)).to(dev)
+    b_d = ctx.keygen(s_d, a_d, torch.from_numpy(e).to(dev))
+    c_all = torch.empty(B, 2, N, dtype=torch.int64, device=dev)
+    tot = torch.empty(msgs, 2, N, dtype=torch.int64, device=dev)
+    h_out = torch.empty(2, msgs, N // 2, dtype=torch.float64).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    outs = {}
+
+    def step(mark=False):
+        if mark:
+            ev[0].record()
+        m = ctx.encode(re_d, im_d)
+        if mark:
+            ev[1].record()
+        ctx.encrypt(b_d, a_d, m, v_d, e0_d, e1_d, out=c_all)
+        if mark:
+            ev[2].record()
+        ctx.sum([c_all[k * msgs:(k + 1) * msgs] for k in range(clients)], out=tot)
+        if mark:
+            ev[3].record()
+        d = ctx.decrypt(tot, s_d)
+        if mark:
+            ev[4].record()
+        outs["re"], outs["im"] = ctx.decode(d)
+        if mark:
+            ev[5].record()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    # correctness of the timed configuration against the plain sums (CKKS error bound)
+    got = np.stack([outs["re"].cpu().numpy(), outs["im"].cpu().numpy()], -1).reshape(-1, 2)[:cells]
+    err = float(np.abs(got - hist.sum(0).reshape(-1, 2)).max())
+    bound = clients * N * (0.5 + 19 * (2 * N + 1)) / scale
+    if not err <= bound + 1e-9 * np.abs(hist).sum(0).max():
+        raise RuntimeError(f"horizontal round error {err} above the bound {bound}")
+
+    t0e = torch.cuda.Event(enable_timing=True)
+    t1e = torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    phases = np.zeros(5)
+    n0 = native.lib().paillier_launch_count()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            t0e.record()
+            step(mark=True)
+            t1e.record()
+            torch.cuda.synchronize()
+            total += t0e.elapsed_time(t1e) / 1e3
+            phases += [ev[i].elapsed_time(ev[i + 1]) for i in range(5)]
+    launches = native.lib().paillier_launch_count() - n0
+    barrier()
+    total = max_over_ranks(total, dist, dev)
+
+    # end to end: host -> device copies of every client's slots and randomness,
+    # the round, the decoded global histogram back to the host
+    h2d = sum(t.numel() * t.element_size() for t in (h_re, h_im, h_v, h_e0, h_e1))
+    d2h = h_out.numel() * 8
+    e2e = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        t0e.record()
+        for dst, src in ((re_d, h_re), (im_d, h_im), (v_d, h_v), (e0_d, h_e0), (e1_d, h_e1)):
+            dst.copy_(src, non_blocking=True)
+        step()
+        h_out[0].copy_(outs["re"], non_blocking=True)
+        h_out[1].copy_(outs["im"], non_blocking=True)
+        t1e.record()
+        torch.cuda.synchronize()
+        e2e += t0e.elapsed_time(t1e) / 1e3
+    e2e = max_over_ranks(e2e, dist, dev)
+
+    ph = phases / args.steps  # ms
+    names = ["encode", "encrypt", "sum", "decrypt", "decode"]
+    # dominant kernel: the encoder's direct canonical-embedding sum, float64 FMA bound
+    enc_flops = B * N * (N // 2) * 4  # per coefficient and slot: two multiplies, two adds
+    line = {
+        "metric": METRIC_H, "value": whole_job_rate(1, args.steps, world, total), "unit": "rounds/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64",
+        "data": "synthetic (seeded local histograms of logistic g/h over N(0,1) features, quantile-binned)",
+        "config": horizontal_config(cfg, msgs),
+        "phases_ms_per_step": dict(zip(names, ph.tolist())),
+        "ciphertexts_per_s": B / (ph[1] * 1e-3),
+        "max_abs_error": err, "error_bound": bound,
+        "roofline": {"bound": "alu", "kernel": "k_encode (float64)", "achieved": enc_flops / (ph[0] * 1e-3) / 1e12,
+                     "peak": 1.25, "unit": "TFLOP/s", "frac": enc_flops / (ph[0] * 1e-3) / 1e12 / 1.25,
+                     "traffic": None, "peak_source": "nominal B300 FP64 rate (no measured FP64 peak)"},
+        "clocks": clk.summary(),
+        "e2e": {"value": whole_job_rate(1, args.steps, world, e2e), "unit": "rounds/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per_round, wall = _horizontal_oracle_sample(cfg)
+        line["cpu_baseline"] = {"value": 1.0 / per_round, "unit": "rounds/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one client plaintext (encode + encrypt) and one aggregate (sum of "
+                                          f"{clients}, decrypt + decode), scaled to the round's {B} and {msgs}; "
+                                          f"{wall:.1f} s wall"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference_horizontal(args, cfg):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    N, q, msgs, *_ = horizontal_inputs(cfg)
+    t = [_horizontal_oracle_sample(cfg) for _ in range(args.steps)]
+    per_round = sum(x[0] for x in t) / len(t)
+    rate = 1.0 / per_round
+    sample = (f"per step one client plaintext (encode + encrypt) and one aggregate (sum, decrypt + decode) of the "
+              f"horizontal round, scaled to its {cfg['clients'] * msgs} plaintexts and {msgs} aggregates")
+    line = {
+        "impl": "reference", "metric": METRIC_H, "value": rate, "unit": "rounds/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_round, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "python-int+f64", "data": "synthetic",
+        "config": horizontal_config(cfg, msgs),
+        "cpu_baseline": {"value": rate, "unit": "rounds/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": "rounds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def workload_config(name, cfg):
     desc = {
         "level": "one tree level: 250,000 samples x 30 features (N(0,1), quantile-binned) x 256 bins, 2048-bit n, "
@@ -776,7 +991,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", default="level",
-                    choices=["level", "toy", "level_small", "batched", "serving", "large", "oracle"])
+                    choices=["level", "toy", "level_small", "batched", "serving", "large", "horizontal", "oracle"])
     ap.add_argument("--requests", type=int, default=300, help="serving: timed requests")
     ap.add_argument("--slots", type=int, default=8, help="serving: concurrent request slots")
     ap.add_argument("--load", type=float, default=0.7, help="serving: offered load / measured capacity")
@@ -792,8 +1007,12 @@ def main():
     cfg = synth.CONFIGS.get(args.config, {})
     if args.config == "oracle":
         run_oracle_rates(args)
+    elif args.impl == "reference" and args.config == "horizontal":
+        run_reference_horizontal(args, cfg)
     elif args.impl == "reference":
         run_reference(args, cfg)
+    elif args.config == "horizontal":
+        run_horizontal(args, cfg)
     elif args.config == "batched":
         run_batched(args, cfg)
     elif args.config == "serving":

@@ -87,6 +87,15 @@ SIGNATURES.update({
     "pl_server_stats": (_i, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                              C.POINTER(C.c_longlong), C.POINTER(_i), C.POINTER(_sz)]),
     "pl_server_destroy": (None, [_vp]),
+    "ckks_create": (_i, [_i, C.c_uint64, C.c_double, C.POINTER(C.c_void_p)]),
+    "ckks_free": (None, [_vp]),
+    "ckks_slots": (_i, [_vp]),
+    "ckks_encode": (_i, [_vp, _vp, _vp, _sz, _vp, _vp]),
+    "ckks_decode": (_i, [_vp, _vp, _sz, _vp, _vp, _vp]),
+    "ckks_keygen": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "ckks_encrypt": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "ckks_sum": (_i, [_vp, C.POINTER(C.c_void_p), _i, _sz, _vp, _vp]),
+    "ckks_decrypt": (_i, [_vp, _vp, _vp, _sz, _vp, _vp]),
 })
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
 

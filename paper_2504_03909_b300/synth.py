@@ -236,6 +236,9 @@ CONFIGS = {
     "batched": dict(M=250_000, F=30, K=256, n_bits=2048, seed=3, data_seed=2, bins="normal", depth=6),
     # large: 1M samples x 64 log-normal features x 256 bins, 3072-bit n, depth 8
     "large": dict(M=1_000_000, F=64, K=256, n_bits=3072, seed=5, bins="lognormal", depth=8),
+    # secure horizontal (CKKS): 5 clients, 200k samples split evenly, 30 features x 256 bins,
+    # N = 8192 (4096 complex slots, G real / H imaginary), one 60-bit prime, scale 2^40
+    "horizontal": dict(M=200_000, F=30, K=256, clients=5, log_n=13, scale_bits=40, seed=7),
 }
 
 
