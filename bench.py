@@ -305,23 +305,26 @@ def run_reference(args, cfg):
 METRIC_H = "CKKS secure-horizontal rounds/s (clients encrypt local G/H histograms, server adds, client decrypts)"
 
 
-def horizontal_inputs(cfg):
+def horizontal_inputs(cfg, nodes: int = 1):
     """Local histograms packed into complex slots (G real, H imaginary), the key
-    material and every client's encryption randomness (all seeded)."""
+    material and every client's encryption randomness (all seeded).  Plaintext
+    order [client][node][message]; `nodes` > 1 repeats the node's histograms
+    (the histograms of one tree level) with fresh randomness per plaintext."""
     log_n, clients, F, K = cfg["log_n"], cfg["clients"], cfg["F"], cfg["K"]
     N = 1 << log_n
     slots = N // 2
     cells = F * K
     msgs = -(-cells // slots)
     hist = synth.horizontal_histograms(cfg["M"], F, K, clients, cfg["seed"])
-    flat = np.zeros((clients, msgs * slots, 2))
-    flat[:, :cells] = hist.reshape(clients, cells, 2)
-    flat = flat.reshape(clients * msgs, slots, 2)
+    flat = np.zeros((clients, 1, msgs * slots, 2))
+    flat[:, 0, :cells] = hist.reshape(clients, cells, 2)
+    flat = np.repeat(flat, nodes, axis=1).reshape(clients * nodes * msgs, slots, 2)
     q = synth.ckks_prime(log_n)
     seed = cfg["seed"]
     key = (synth.ckks_secret(N, seed), synth.ckks_uniform(N, q, seed), synth.ckks_gaussian(N, seed, 1))
-    rnd = (synth.ckks_ternary((clients * msgs, N), seed, 2), synth.ckks_gaussian((clients * msgs, N), seed, 3),
-           synth.ckks_gaussian((clients * msgs, N), seed, 4))
+    B = clients * nodes * msgs
+    rnd = (synth.ckks_ternary((B, N), seed, 2), synth.ckks_gaussian((B, N), seed, 3),
+           synth.ckks_gaussian((B, N), seed, 4))
     return N, q, msgs, cells, hist, flat, key, rnd
 
 
@@ -358,6 +361,108 @@ def _horizontal_oracle_sample(cfg):
     return per_round, t3 - t0
 
 
+# algorithmic work of the CKKS kernels, per plaintext (N = 2n coefficients)
+def ckks_fft_flop(N: int) -> int:
+    """encode/decode: a length-n complex radix-2 FFT (5 n log2 n FLOP) plus the
+    twist by omega^k (6 n) and the scaling (2 n)."""
+    n = N // 2
+    return 5 * n * (n.bit_length() - 1) + 8 * n
+
+
+def ckks_encrypt_imad(N: int) -> int:
+    """k_encrypt: forward NTT of v (N/2 log2 N Montgomery products), 4 N in the
+    pointwise products, two inverse NTTs (+ N for the N^-1 fold); 20 IMAD
+    halves per 64-bit Montgomery product (a b: 4 limb products, m = lo q': 2,
+    m q: 4; 2 halves each)."""
+    lg = N.bit_length() - 1
+    mm = (N // 2) * lg + 4 * N + 2 * (N // 2) * lg + N
+    return 20 * mm
+
+
+def ckks_decrypt_imad(N: int) -> int:
+    """k_decrypt: forward NTT of c1, 2 N in the pointwise product, one inverse
+    NTT (+ N/2 for the N^-1 fold); 20 IMAD halves per Montgomery product."""
+    lg = N.bit_length() - 1
+    return 20 * ((N // 2) * lg + 2 * N + (N // 2) * lg + N // 2)
+
+
+class _HorizontalCase:
+    """Device buffers and one captured CUDA graph of a horizontal round over
+    `nodes` node histograms."""
+
+    def __init__(self, cfg, ctx, nodes, dev, torch):
+        clients = cfg["clients"]
+        N, q, msgs, cells, hist, flat, (s, a, e), (v, e0, e1) = horizontal_inputs(cfg, nodes)
+        self.N, self.msgs, self.cells, self.hist, self.nodes = N, msgs, cells, hist, nodes
+        B = clients * nodes * msgs
+        self.B = B
+        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        self.h_in = [pin(flat[..., 0]), pin(flat[..., 1]), pin(v), pin(e0), pin(e1)]
+        self.d_in = [t.to(dev) for t in self.h_in]
+        self.s_d = torch.from_numpy(s).to(dev)
+        self.a_d = torch.from_numpy(a.view(np.int64)).to(dev)
+        self.b_d = ctx.keygen(self.s_d, self.a_d, torch.from_numpy(e).to(dev))
+        # the clients' keys are fixed across rounds: transforms taken once, outside the round
+        ctx.prepare_public_key(self.b_d, self.a_d)
+        ctx.prepare_secret_key(self.s_d)
+        self.m = torch.empty(B, N, dtype=torch.int64, device=dev)
+        self.c = torch.empty(B, 2, N, dtype=torch.int64, device=dev)
+        self.tot = torch.empty(nodes * msgs, 2, N, dtype=torch.int64, device=dev)
+        self.h_out = torch.empty(2, nodes * msgs, N // 2, dtype=torch.float64).pin_memory()
+        self.ctx, self.clients, self.torch = ctx, clients, torch
+        self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        self.out = {}
+        torch.cuda.synchronize()  # inputs and the key are ready before any other stream uses them
+
+    def step(self, mark=False, copies=False):
+        ctx, ev, k = self.ctx, self.ev, self.nodes * self.msgs
+        if copies:
+            for dst, src in zip(self.d_in, self.h_in):
+                dst.copy_(src, non_blocking=True)
+        re, im, v, e0, e1 = self.d_in
+        if mark:
+            ev[0].record()
+        self.m = ctx.encode(re, im)
+        if mark:
+            ev[1].record()
+        ctx.encrypt_prepared(self.m, v, e0, e1, out=self.c)
+        if mark:
+            ev[2].record()
+        ctx.sum([self.c[i * k:(i + 1) * k] for i in range(self.clients)], out=self.tot)
+        if mark:
+            ev[3].record()
+        d = ctx.decrypt_prepared(self.tot)
+        if mark:
+            ev[4].record()
+        self.out["re"], self.out["im"] = ctx.decode(d)
+        if mark:
+            ev[5].record()
+        if copies:
+            self.h_out[0].copy_(self.out["re"], non_blocking=True)
+            self.h_out[1].copy_(self.out["im"], non_blocking=True)
+
+    def capture(self, copies=False):
+        """Captures one round (warm: scratch already sized) into a CUDA graph;
+        returns (graph, library kernels in it)."""
+        from paper_2504_03909_b300 import native
+        torch = self.torch
+        g = torch.cuda.CUDAGraph()
+        n0 = native.lib().paillier_launch_count()
+        with torch.cuda.graph(g):
+            self.step(copies=copies)
+        return g, int(native.lib().paillier_launch_count() - n0)
+
+    def check(self, scale):
+        got = np.stack([self.out["re"].cpu().numpy(), self.out["im"].cpu().numpy()], -1)
+        got = got.reshape(self.nodes, -1, 2)[:, :self.cells]
+        want = self.hist.sum(0).reshape(-1, 2)
+        err = float(np.abs(got - want[None]).max())
+        bound = self.clients * self.N * (0.5 + 19 * (2 * self.N + 1)) / scale
+        if not err <= bound + 1e-9 * np.abs(want).max():
+            raise RuntimeError(f"horizontal round error {err} above the bound {bound}")
+        return err, bound
+
+
 def run_horizontal(args, cfg):
     import torch
     from paper_2504_03909_b300 import ckks as G, native
@@ -370,43 +475,11 @@ def run_horizontal(args, cfg):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     clients = cfg["clients"]
-    N, q, msgs, cells, hist, flat, (s, a, e), (v, e0, e1) = horizontal_inputs(cfg)
     scale = 2.0 ** cfg["scale_bits"]
+    q = synth.ckks_prime(cfg["log_n"])
     ctx = G.Context(cfg["log_n"], q, scale)
-    B = clients * msgs
-    pin = lambda x, dt=None: (torch.from_numpy(np.ascontiguousarray(x)).view(dt) if dt else
-                              torch.from_numpy(np.ascontiguousarray(x))).pin_memory()
-    h_re, h_im = pin(flat[..., 0]), pin(flat[..., 1])
-    h_v, h_e0, h_e1 = pin(v), pin(e0), pin(e1)
-    re_d, im_d, v_d, e0_d, e1_d = (t.to(dev) for t in (h_re, h_im, h_v, h_e0, h_e1))
-    s_d = torch.from_numpy(s).to(dev)
-    a_d = torch.from_numpy(a.view(np.int64)).to(dev)
-    b_d = ctx.keygen(s_d, a_d, torch.from_numpy(e).to(dev))
-    c_all = torch.empty(B, 2, N, dtype=torch.int64, device=dev)
-    tot = torch.empty(msgs, 2, N, dtype=torch.int64, device=dev)
-    h_out = torch.empty(2, msgs, N // 2, dtype=torch.float64).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-    outs = {}
-
-    def step(mark=False):
-        if mark:
-            ev[0].record()
-        m = ctx.encode(re_d, im_d)
-        if mark:
-            ev[1].record()
-        ctx.encrypt(b_d, a_d, m, v_d, e0_d, e1_d, out=c_all)
-        if mark:
-            ev[2].record()
-        ctx.sum([c_all[k * msgs:(k + 1) * msgs] for k in range(clients)], out=tot)
-        if mark:
-            ev[3].record()
-        d = ctx.decrypt(tot, s_d)
-        if mark:
-            ev[4].record()
-        outs["re"], outs["im"] = ctx.decode(d)
-        if mark:
-            ev[5].record()
+    stream = torch.cuda.Stream()
 
     def barrier():
         torch.cuda.synchronize()
@@ -414,79 +487,119 @@ def run_horizontal(args, cfg):
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        step()
-    barrier()
-    # correctness of the timed configuration against the plain sums (CKKS error bound)
-    got = np.stack([outs["re"].cpu().numpy(), outs["im"].cpu().numpy()], -1).reshape(-1, 2)[:cells]
-    err = float(np.abs(got - hist.sum(0).reshape(-1, 2)).max())
-    bound = clients * N * (0.5 + 19 * (2 * N + 1)) / scale
-    if not err <= bound + 1e-9 * np.abs(hist).sum(0).max():
-        raise RuntimeError(f"horizontal round error {err} above the bound {bound}")
+    # measured peaks (same process, same clocks)
+    peaks = {}
+    for name, fn, extra in (("fp64_flop_s", "paillier_fp64_peak", ()), ("imad_s", "paillier_imad_peak", (1,))):
+        rate, el = native.C.c_double(0), native.C.c_double(0)
+        native.call(fn, *extra, 1000.0, native.C.byref(rate), native.C.byref(el), torch.cuda.current_stream().cuda_stream)
+        peaks[name] = rate.value
 
-    t0e = torch.cuda.Event(enable_timing=True)
-    t1e = torch.cuda.Event(enable_timing=True)
-    total = 0.0
-    phases = np.zeros(5)
-    n0 = native.lib().paillier_launch_count()
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1)
-            t0e.record()
-            step(mark=True)
-            t1e.record()
-            torch.cuda.synchronize()
-            total += t0e.elapsed_time(t1e) / 1e3
-            phases += [ev[i].elapsed_time(ev[i + 1]) for i in range(5)]
-    launches = native.lib().paillier_launch_count() - n0
-    barrier()
+    def measure(nodes, steps):
+        """Warm-up, correctness check, captured graph; timed replays (one by one,
+        L2 flushed before each) and per-phase times from an eager pass."""
+        case = _HorizontalCase(cfg, ctx, nodes, dev, torch)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                case.step()
+            stream.synchronize()
+            err, bound = case.check(scale)
+            g, launches = case.capture()
+            ge, _ = case.capture(copies=True)
+            t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            phases = np.zeros(5)
+            for _ in range(steps):  # per-phase times, eager (events between the library calls)
+                flush.fill_(1)
+                case.step(mark=True)
+                stream.synchronize()
+                phases += [case.ev[i].elapsed_time(case.ev[i + 1]) for i in range(5)]
+            barrier()
+            total = 0.0
+            with ClockSampler(local) as clk:
+                # keep the GPU busy long enough for the sampler's first readings
+                t_end = time.perf_counter() + 0.6
+                while time.perf_counter() < t_end:
+                    for _ in range(50):
+                        g.replay()
+                    stream.synchronize()
+                for _ in range(steps):
+                    flush.fill_(1)
+                    t0e.record()
+                    g.replay()
+                    t1e.record()
+                    stream.synchronize()
+                    total += t0e.elapsed_time(t1e) / 1e3
+            e2e = 0.0
+            for _ in range(steps):
+                flush.fill_(1)
+                t0e.record()
+                ge.replay()
+                t1e.record()
+                stream.synchronize()
+                e2e += t0e.elapsed_time(t1e) / 1e3
+            case.check(scale)
+        return case, total, e2e, phases / steps, launches, err, bound, clk.summary()
+
+    case, total, e2e, ph, launches, err, bound, clk = measure(args.nodes, args.steps)
     total = max_over_ranks(total, dist, dev)
-
-    # end to end: host -> device copies of every client's slots and randomness,
-    # the round, the decoded global histogram back to the host
-    h2d = sum(t.numel() * t.element_size() for t in (h_re, h_im, h_v, h_e0, h_e1))
-    d2h = h_out.numel() * 8
-    e2e = 0.0
-    for _ in range(args.steps):
-        flush.fill_(1)
-        t0e.record()
-        for dst, src in ((re_d, h_re), (im_d, h_im), (v_d, h_v), (e0_d, h_e0), (e1_d, h_e1)):
-            dst.copy_(src, non_blocking=True)
-        step()
-        h_out[0].copy_(outs["re"], non_blocking=True)
-        h_out[1].copy_(outs["im"], non_blocking=True)
-        t1e.record()
-        torch.cuda.synchronize()
-        e2e += t0e.elapsed_time(t1e) / 1e3
     e2e = max_over_ranks(e2e, dist, dev)
+    lvl = None
+    if args.nodes == 1:
+        lvl_case, lt, le, lph, _, _, _, _ = measure(32, args.steps)
+        lvl = (lvl_case, lt, lph)
 
-    ph = phases / args.steps  # ms
+    N, B, msgs = case.N, case.B, case.msgs
     names = ["encode", "encrypt", "sum", "decrypt", "decode"]
-    # dominant kernel: the encoder's direct canonical-embedding sum, float64 FMA bound
-    enc_flops = B * N * (N // 2) * 4  # per coefficient and slot: two multiplies, two adds
+    fft_flop = ckks_fft_flop(N)
+    enc_imad = ckks_encrypt_imad(N)
+
+    def roof(phases, b):
+        """Dominant phase and its achieved rate against the measured peak."""
+        i = int(np.argmax(phases))
+        if names[i] in ("encode", "decode"):
+            work, peak, unit, kern = fft_flop * (b if names[i] == "encode" else b // clients), peaks["fp64_flop_s"], \
+                "TFLOP/s", f"k_{names[i]} (float64 FFT)"
+        elif names[i] in ("encrypt", "decrypt"):
+            per = enc_imad if names[i] == "encrypt" else ckks_decrypt_imad(N)
+            work, peak, unit, kern = per * (b if names[i] == "encrypt" else b // clients), peaks["imad_s"], \
+                "TIMAD/s", f"k_{names[i]} (64-bit Montgomery NTT)"
+        else:
+            return None
+        ach = work / (phases[i] * 1e-3)
+        return {"bound": "alu", "kernel": kern, "achieved": ach / 1e12, "peak": peak / 1e12, "unit": unit,
+                "frac": ach / peak, "traffic": None, "work_per_launch": work, "launch_ms": phases[i],
+                "ctas": b if names[i] in ("encode", "encrypt") else b // clients, "sms": sm_count_of(dev),
+                "peak_source": "project microbenchmark in the same run (paillier_fp64_peak / paillier_imad_peak "
+                               "mad.wide)"}
+
     line = {
-        "metric": METRIC_H, "value": whole_job_rate(1, args.steps, world, total), "unit": "rounds/s",
+        "metric": METRIC_H, "value": whole_job_rate(args.nodes, args.steps, world, total),
+        "unit": "rounds/s" if args.nodes == 1 else "node-rounds/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64",
         "data": "synthetic (seeded local histograms of logistic g/h over N(0,1) features, quantile-binned)",
-        "config": horizontal_config(cfg, msgs),
+        "config": dict(horizontal_config(cfg, msgs), nodes=args.nodes, graph="one CUDA graph per round"),
         "phases_ms_per_step": dict(zip(names, ph.tolist())),
-        "ciphertexts_per_s": B / (ph[1] * 1e-3),
+        "phases_note": "eager pass with events between the library calls (launch gaps included)",
         "max_abs_error": err, "error_bound": bound,
-        "roofline": {"bound": "alu", "kernel": "k_encode (float64)", "achieved": enc_flops / (ph[0] * 1e-3) / 1e12,
-                     "peak": 1.25, "unit": "TFLOP/s", "frac": enc_flops / (ph[0] * 1e-3) / 1e12 / 1.25,
-                     "traffic": None, "peak_source": "nominal B300 FP64 rate (no measured FP64 peak)"},
-        "clocks": clk.summary(),
-        "e2e": {"value": whole_job_rate(1, args.steps, world, e2e), "unit": "rounds/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches),
+        "roofline": roof(ph, B),
+        "clocks": clk,
+        "e2e": {"value": whole_job_rate(args.nodes, args.steps, world, e2e), "unit": "rounds/s",
+                "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in case.h_in),
+                "d2h_bytes_per_step": case.h_out.numel() * 8},
+        "gpu_launches": launches * args.steps,
+        "peaks_measured": {"fp64_TFLOP_s": peaks["fp64_flop_s"] / 1e12, "imad_T_s": peaks["imad_s"] / 1e12},
     }
+    if lvl is not None:
+        lc, lt, lph = lvl
+        line["level_32_nodes"] = {"rounds_per_s": 32 * args.steps / lt, "ms_per_level": 1e3 * lt / args.steps,
+                                  "phases_ms": dict(zip(names, lph.tolist())), "roofline": roof(lph, lc.B),
+                                  "note": "32 node histograms (a depth-6 tree's last level) in one batch"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         per_round, wall = _horizontal_oracle_sample(cfg)
         line["cpu_baseline"] = {"value": 1.0 / per_round, "unit": "rounds/s", "cores": 1, "kind": "oracle",
                                 "sample": f"one client plaintext (encode + encrypt) and one aggregate (sum of "
-                                          f"{clients}, decrypt + decode), scaled to the round's {B} and {msgs}; "
-                                          f"{wall:.1f} s wall"}
+                                          f"{clients}, decrypt + decode), scaled to the round's {clients * msgs} "
+                                          f"and {msgs}; {wall:.1f} s wall"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -1003,6 +1116,7 @@ def main():
                     help="batched/large: Beta(0.5,0.5) splits or splits found on the decrypted histograms")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nodes", type=int, default=1, help="horizontal: node histograms per round")
     args = ap.parse_args()
     cfg = synth.CONFIGS.get(args.config, {})
     if args.config == "oracle":

@@ -35,7 +35,7 @@ extern "C" {
 
 typedef struct ckks_ctx ckks_ctx;
 
-/* N = 2^log_n (log_n in 4..14), q an odd prime < 2^62 with q = 1 mod 2N
+/* N = 2^log_n (log_n in 4..13), q an odd prime < 2^62 with q = 1 mod 2N
  * (checked), scale > 0.  Allocates the transform and embedding tables on the
  * current device. */
 pl_status ckks_create(int log_n, uint64_t q, double scale, ckks_ctx** out);
@@ -72,6 +72,19 @@ pl_status ckks_sum(ckks_ctx* ctx, const uint64_t* const* d_cts, int count, size_
 /* d_m [batch][N] = c0 + c1 s mod q for ciphertexts d_c [batch][2][N]. */
 pl_status ckks_decrypt(ckks_ctx* ctx, const uint64_t* d_c, const int8_t* d_s, size_t batch, uint64_t* d_m,
                        void* stream);
+
+/* Prepared keys: a client's keys do not change between rounds, so their
+ * transforms can be taken once.  ckks_prepare_public_key stores (b, a) and
+ * ckks_prepare_secret_key stores s in the transform domain inside ctx (device
+ * memory owned by ctx, replaced by the next call; the stored key is ready for
+ * work later on the same stream).  ckks_encrypt_prepared and
+ * ckks_decrypt_prepared then equal ckks_encrypt / ckks_decrypt with that key,
+ * bit for bit; they return PL_EINVAL if no key was prepared. */
+pl_status ckks_prepare_public_key(ckks_ctx* ctx, const uint64_t* d_b, const uint64_t* d_a, void* stream);
+pl_status ckks_prepare_secret_key(ckks_ctx* ctx, const int8_t* d_s, void* stream);
+pl_status ckks_encrypt_prepared(ckks_ctx* ctx, const int64_t* d_m, const int8_t* d_v, const int32_t* d_e0,
+                                const int32_t* d_e1, size_t batch, uint64_t* d_c, void* stream);
+pl_status ckks_decrypt_prepared(ckks_ctx* ctx, const uint64_t* d_c, size_t batch, uint64_t* d_m, void* stream);
 
 #ifdef __cplusplus
 }

@@ -24,6 +24,11 @@ extern "C" {
  * allocates and frees a small device buffer and synchronises the stream. */
 pl_status paillier_imad_peak(int mix, double target_ms, double* imad_per_s, double* elapsed_ms, void* stream);
 
+/* Float64 fused multiply-add peak of the current GPU (independent
+ * fma.rn.f64 chains), measured like paillier_imad_peak.  Unit: FLOP/s, one
+ * FMA being 2 FLOP.  The roofline of the CKKS embedding (FFT) kernels. */
+pl_status paillier_fp64_peak(double target_ms, double* flop_per_s, double* elapsed_ms, void* stream);
+
 /* Number of kernels the library has launched so far in this process. */
 unsigned long long paillier_launch_count(void);
 

@@ -87,6 +87,41 @@ class Context:
         call("ckks_sum", self._h, arr, len(cts), batch, _ptr(out), _stream(stream))
         return out
 
+    def prepare_public_key(self, b: torch.Tensor, a: torch.Tensor, stream=None) -> None:
+        """Keeps (b, a) in the transform domain for encrypt_prepared."""
+        self._batch(b, self.N)
+        self._batch(a, self.N)
+        call("ckks_prepare_public_key", self._h, _ptr(b), _ptr(a), _stream(stream))
+
+    def prepare_secret_key(self, s: torch.Tensor, stream=None) -> None:
+        """Keeps s in the transform domain for decrypt_prepared."""
+        if s.dtype != torch.int8:
+            raise ValueError("s must be int8")
+        self._batch(s, self.N)
+        call("ckks_prepare_secret_key", self._h, _ptr(s), _stream(stream))
+
+    def encrypt_prepared(self, m, v, e0, e1, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """encrypt() under the prepared public key."""
+        if m.dtype != torch.int64 or v.dtype != torch.int8 or e0.dtype != torch.int32 or e1.dtype != torch.int32:
+            raise ValueError("m int64, v int8, e0/e1 int32")
+        batch = self._batch(m, self.N)
+        for t in (v, e0, e1):
+            if t.numel() != m.numel():
+                raise ValueError("v, e0, e1 must have the shape of m")
+        if out is None:
+            out = torch.empty(batch, 2, self.N, dtype=torch.int64, device=m.device)
+        call("ckks_encrypt_prepared", self._h, _ptr(m), _ptr(v), _ptr(e0), _ptr(e1), batch, _ptr(out),
+             _stream(stream))
+        return out
+
+    def decrypt_prepared(self, c: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """decrypt() under the prepared secret key."""
+        batch = self._batch(c, self.N) // 2
+        if out is None:
+            out = torch.empty(batch, self.N, dtype=torch.int64, device=c.device)
+        call("ckks_decrypt_prepared", self._h, _ptr(c), batch, _ptr(out), _stream(stream))
+        return out
+
     def decrypt(self, c: torch.Tensor, s: torch.Tensor, stream=None) -> torch.Tensor:
         """c0 + c1 s mod q: [batch, N] in [0, q) from c [batch, 2, N]."""
         batch = self._batch(c, self.N) // 2

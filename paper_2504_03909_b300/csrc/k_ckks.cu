@@ -66,96 +66,235 @@ __device__ __forceinline__ u64 smod(long long x, u64 q) {  // signed small or la
 }
 
 struct NttConst {
-  u64 q, qn, r2, ninv;  // ninv in Montgomery form
+  u64 q, qn, r2;
+  u64 ninv;    // N^-1, Montgomery form
+  u64 last;    // inverse twiddle of the last Gentleman-Sande stage times N^-1, Montgomery form
   int log_n;
 };
 
-// In-place negacyclic NTT of one polynomial per block (shared memory).
-// Forward: Cooley-Tukey, natural order in, bit-reversed order out, twiddles
-// psi^bitrev(i) (Montgomery form).  Inverse: Gentleman-Sande back to natural
-// order, then the factor N^-1.
-__global__ void k_ntt(u64* __restrict__ data, const u64* __restrict__ tw, NttConst C, int inverse) {
-  extern __shared__ u64 a[];
-  const int N = 1 << C.log_n;
-  u64* p = data + (size_t)blockIdx.x * N;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) a[i] = p[i];
-  __syncthreads();
-  const u64 q = C.q, qn = C.qn;
-  if (!inverse) {
-    for (int m = 1, t = N >> 1; m < N; m <<= 1, t >>= 1) {
-      for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
-        const int i = b / t, j = b - i * t, idx = 2 * i * t + j;
-        const u64 U = a[idx], V = mmul(a[idx + t], tw[m + i], q, qn);
-        a[idx] = addm(U, V, q);
-        a[idx + t] = subm(U, V, q);
-      }
-      __syncthreads();
+constexpr int kMaxLogN = 13;  // one polynomial (or two) resident in shared memory per CTA
+constexpr int kThreads = 1024;
+
+// ---- negacyclic NTT on a shared-memory polynomial (all threads of the CTA) --
+// Forward: Cooley-Tukey, natural order in, bit-reversed order out; the stage
+// with butterfly distance t has N/(2t) blocks, block i using psi^bitrev(N/(2t)+i)
+// (table tw, Montgomery form).  Inverse: Gentleman-Sande with psi^-bitrev
+// (table itw) back to natural order, the factor N^-1 folded into the last
+// stage.  Three consecutive stages run in registers on 8 elements per thread
+// (one barrier per three stages); the one or two stages left over run as plain
+// radix-2 stages.  Both expect the input visible to all threads and end with a
+// barrier.
+
+__device__ __forceinline__ void ct_bfly(u64& x, u64& y, u64 w, const NttConst& C) {
+  const u64 v = mmul(y, w, C.q, C.qn);
+  y = subm(x, v, C.q);
+  x = addm(x, v, C.q);
+}
+
+__device__ __forceinline__ void gs_bfly(u64& x, u64& y, u64 w, const NttConst& C) {
+  const u64 s = addm(x, y, C.q);
+  y = mmul(subm(x, y, C.q), w, C.q, C.qn);
+  x = s;
+}
+
+// the last inverse stage: both outputs times N^-1 (C.last = psi^-bitrev(1) N^-1)
+__device__ __forceinline__ void gs_last(u64& x, u64& y, const NttConst& C) {
+  const u64 s = addm(x, y, C.q);
+  y = mmul(subm(x, y, C.q), C.last, C.q, C.qn);
+  x = mmul(s, C.ninv, C.q, C.qn);
+}
+
+__device__ void ntt_fwd(u64* a, const u64* tw, const NttConst& C) {
+  const int L = C.log_n, N = 1 << L;
+  int lt = L - 1;  // log2 of the butterfly distance of the next stage
+  for (; lt >= 2; lt -= 3) {
+    // distances t, t/2, t/4 on e_k = 2t i + j + k t/4 (k < 8, j < t/4)
+    const int q4 = lt - 2, m = N >> (lt + 1);
+    for (int g = threadIdx.x; g < N / 8; g += blockDim.x) {
+      const int i = g >> q4, j = g & ((1 << q4) - 1);
+      const int base = (i << (lt + 1)) + j;
+      u64 x[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = a[base + (k << q4)];
+      const u64 w1 = tw[m + i];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) ct_bfly(x[k], x[k + 4], w1, C);
+      const u64 w2a = tw[2 * m + 2 * i], w2b = tw[2 * m + 2 * i + 1];
+      ct_bfly(x[0], x[2], w2a, C);
+      ct_bfly(x[1], x[3], w2a, C);
+      ct_bfly(x[4], x[6], w2b, C);
+      ct_bfly(x[5], x[7], w2b, C);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) ct_bfly(x[2 * k], x[2 * k + 1], tw[4 * m + 4 * i + k], C);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[base + (k << q4)] = x[k];
     }
-  } else {
-    for (int m = N, t = 1; m > 1; m >>= 1, t <<= 1) {
-      const int h = m >> 1;
-      for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
-        const int i = b / t, j = b - i * t, idx = 2 * i * t + j;
-        const u64 U = a[idx], V = a[idx + t];
-        a[idx] = addm(U, V, q);
-        a[idx + t] = mmul(subm(U, V, q), tw[h + i], q, qn);
-      }
-      __syncthreads();
-    }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) a[i] = mmul(a[i], C.ninv, q, qn);
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < N; i += blockDim.x) p[i] = a[i];
+  for (; lt >= 0; --lt) {
+    const int m = N >> (lt + 1);
+    for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
+      const int i = b >> lt, idx = (i << (lt + 1)) + (b & ((1 << lt) - 1));
+      u64 x = a[idx], y = a[idx + (1 << lt)];
+      ct_bfly(x, y, tw[m + i], C);
+      a[idx] = x;
+      a[idx + (1 << lt)] = y;
+    }
+    __syncthreads();
+  }
 }
 
-// out[i] = x[i] y[i mod period] mod q  (period = N broadcasts one polynomial)
-// (out may alias x)
-__global__ void k_pointwise(const u64* x, const u64* __restrict__ y, size_t period, size_t count, NttConst C,
-                            u64* out) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = mmul(mmul(x[i], y[i % period], C.q, C.qn), C.r2, C.q, C.qn);
+// inverse transform of one or two polynomials (b may be NULL)
+__device__ void ntt_inv(u64* a, u64* b, const u64* itw, const NttConst& C) {
+  const int L = C.log_n, N = 1 << L;
+  int lt = 0;
+  for (; lt < L % 3; ++lt) {  // leading radix-2 stages (never the last one: L >= 4)
+    const int h = N >> (lt + 1);
+    for (int k = threadIdx.x; k < N / 2; k += blockDim.x) {
+      const int i = k >> lt, idx = (i << (lt + 1)) + (k & ((1 << lt) - 1));
+      const u64 w = itw[h + i];
+      for (u64* p = a; p; p = (p == a ? b : nullptr)) {
+        u64 x = p[idx], y = p[idx + (1 << lt)];
+        gs_bfly(x, y, w, C);
+        p[idx] = x;
+        p[idx + (1 << lt)] = y;
+      }
+    }
+    __syncthreads();
+  }
+  for (; lt < L; lt += 3) {
+    // distances t, 2t, 4t on e_k = 8t I + j + k t (k < 8, j < t)
+    const int h1 = N >> (lt + 1), h2 = N >> (lt + 2), h3 = N >> (lt + 3);
+    const bool last = (lt + 3 == L);
+    for (int g = threadIdx.x; g < N / 8; g += blockDim.x) {
+      const int I = g >> lt, base = (I << (lt + 3)) + (g & ((1 << lt) - 1));
+      const u64 w1[4] = {itw[h1 + 4 * I], itw[h1 + 4 * I + 1], itw[h1 + 4 * I + 2], itw[h1 + 4 * I + 3]};
+      const u64 w2a = itw[h2 + 2 * I], w2b = itw[h2 + 2 * I + 1], w3 = itw[h3 + I];
+      for (u64* p = a; p; p = (p == a ? b : nullptr)) {
+        u64 x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = p[base + (k << lt)];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gs_bfly(x[2 * k], x[2 * k + 1], w1[k], C);
+        gs_bfly(x[0], x[2], w2a, C);
+        gs_bfly(x[1], x[3], w2a, C);
+        gs_bfly(x[4], x[6], w2b, C);
+        gs_bfly(x[5], x[7], w2b, C);
+        if (last) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) gs_last(x[k], x[k + 4], C);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) gs_bfly(x[k], x[k + 4], w3, C);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) p[base + (k << lt)] = x[k];
+      }
+    }
+    __syncthreads();
+  }
 }
 
+__device__ __forceinline__ u64 to_q(u64 x, u64) { return x; }  // already in [0, q)
+__device__ __forceinline__ u64 to_q(int8_t x, u64 q) { return smod(x, q); }
+
+// Every kernel below keeps its twiddle table in shared memory (copied once at
+// entry with 16-byte loads): one DRAM/L2 round trip instead of one per stage.
+__device__ __forceinline__ void stage_table(u64* dst, const u64* __restrict__ src, int N) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+  for (int i = threadIdx.x; i < N / 2; i += blockDim.x) d4[i] = s4[i];
+}
+
+// forward transforms of one or two polynomials: CTA b reads src[b] (reduced
+// into [0, q)) and writes dst + b N.  smem: poly [N] + twiddles [N]
+// With mont = 1 the outputs are in Montgomery form (x R mod q), so that one
+// Montgomery product with them is a plain product mod q.
 template <typename T>
-__global__ void k_to_modq(const T* __restrict__ x, size_t count, u64 q, u64* __restrict__ out) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = smod((long long)x[i], q);
+__global__ void __launch_bounds__(kThreads)
+    k_ntt(const T* __restrict__ src0, const T* __restrict__ src1, u64* __restrict__ dst, const u64* __restrict__ tw,
+          NttConst C, int mont) {
+  extern __shared__ u64 sm[];
+  const int N = 1 << C.log_n;
+  u64* t = sm + N;
+  const T* src = blockIdx.x == 0 ? src0 : src1;
+  stage_table(t, tw, N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = to_q(src[i], C.q);
+  __syncthreads();
+  ntt_fwd(sm, t, C);
+  u64* p = dst + (size_t)blockIdx.x * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) p[i] = mont ? mmul(sm[i], C.r2, C.q, C.qn) : sm[i];
 }
 
-// b = -(a s) + e
-__global__ void k_keygen_finish(const u64* __restrict__ as, const int32_t* __restrict__ e, int N, u64 q,
-                                u64* __restrict__ b) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-    b[i] = addm(subm(0, as[i], q), smod(e[i], q), q);
-}
-
-// c0 = bv + e0 + m, c1 = av + e1 for every message (bv, av [batch][N])
-__global__ void k_encrypt_finish(const u64* __restrict__ bv, const u64* __restrict__ av,
-                                 const int32_t* __restrict__ e0, const int32_t* __restrict__ e1,
-                                 const int64_t* __restrict__ m, size_t batch, int N, u64 q, u64* __restrict__ c) {
-  const size_t count = batch * (size_t)N;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = i / N, k = i % N;
-    c[(p * 2) * N + k] = addm(addm(bv[i], smod(e0[i], q), q), smod(m[i], q), q);
-    c[(p * 2 + 1) * N + k] = addm(av[i], smod(e1[i], q), q);
+// Encryption of one plaintext per CTA: v -> NTT -> (v b^, v a^) -> inverse NTT
+// (both at once) -> c0 = b v + e0 + m, c1 = a v + e1.  pk = [b^ | a^], the
+// public key in the transform domain, Montgomery form.  smem: x, y,
+// twiddles [N] each.
+__global__ void __launch_bounds__(kThreads)
+    k_encrypt(const u64* __restrict__ pk, const int64_t* __restrict__ m, const int8_t* __restrict__ v,
+              const int32_t* __restrict__ e0, const int32_t* __restrict__ e1, const u64* __restrict__ tw,
+              const u64* __restrict__ itw, NttConst C, u64* __restrict__ c) {
+  extern __shared__ u64 sm[];
+  const int N = 1 << C.log_n;
+  const size_t p = blockIdx.x;
+  u64 *x = sm, *y = sm + N, *t = sm + 2 * N;
+  stage_table(t, tw, N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = smod(v[p * N + i], C.q);
+  __syncthreads();
+  ntt_fwd(x, t, C);
+  stage_table(t, itw, N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const u64 xv = x[i];
+    x[i] = mmul(xv, pk[i], C.q, C.qn);
+    y[i] = mmul(xv, pk[N + i], C.q, C.qn);
+  }
+  __syncthreads();
+  ntt_inv(x, y, t, C);
+  u64* c0 = c + p * 2 * N;
+  u64* c1 = c0 + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    c0[i] = addm(addm(x[i], smod(e0[p * N + i], C.q), C.q), smod(m[p * N + i], C.q), C.q);
+    c1[i] = addm(y[i], smod(e1[p * N + i], C.q), C.q);
   }
 }
 
-// m = c0 + (c1 s)
-__global__ void k_decrypt_finish(const u64* __restrict__ c, const u64* __restrict__ c1s, size_t batch, int N, u64 q,
-                                 u64* __restrict__ m) {
-  const size_t count = batch * (size_t)N;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = i / N, k = i % N;
-    m[i] = addm(c[(p * 2) * N + k], c1s[i], q);
-  }
+// Decryption of one ciphertext per CTA: m = c0 + InvNTT(NTT(c1) s^), s^ in
+// Montgomery form.
+// smem: poly + twiddles [N] each.
+__global__ void __launch_bounds__(kThreads)
+    k_decrypt(const u64* __restrict__ c, const u64* __restrict__ shat, const u64* __restrict__ tw,
+              const u64* __restrict__ itw, NttConst C, u64* __restrict__ m) {
+  extern __shared__ u64 sm[];
+  const int N = 1 << C.log_n;
+  const size_t p = blockIdx.x;
+  u64* t = sm + N;
+  const u64* c0 = c + p * 2 * N;
+  stage_table(t, tw, N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = c0[N + i];
+  __syncthreads();
+  ntt_fwd(sm, t, C);
+  stage_table(t, itw, N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x)
+    sm[i] = mmul(sm[i], shat[i], C.q, C.qn);
+  __syncthreads();
+  ntt_inv(sm, nullptr, t, C);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) m[p * N + i] = addm(c0[i], sm[i], C.q);
 }
 
-// gather c1 of every ciphertext into a contiguous [batch][N] array
-__global__ void k_take_c1(const u64* __restrict__ c, size_t batch, int N, u64* __restrict__ out) {
-  const size_t count = batch * (size_t)N;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = c[(i / N * 2 + 1) * N + i % N];
+// b = -(a s) + e, from a^ (Montgomery form) and s^ (transform domain).
+// smem: poly + twiddles.
+__global__ void __launch_bounds__(kThreads)
+    k_keygen(const u64* __restrict__ ahat, const u64* __restrict__ shat, const int32_t* __restrict__ e,
+             const u64* __restrict__ itw, NttConst C, u64* __restrict__ b) {
+  extern __shared__ u64 sm[];
+  const int N = 1 << C.log_n;
+  u64* t = sm + N;
+  stage_table(t, itw, N);
+  for (int i = threadIdx.x; i < N; i += blockDim.x)
+    sm[i] = mmul(ahat[i], shat[i], C.q, C.qn);
+  __syncthreads();
+  ntt_inv(sm, nullptr, t, C);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) b[i] = addm(subm(0, sm[i], C.q), smod(e[i], C.q), C.q);
 }
 
 constexpr int kMaxSum = 256;  // operands of one ckks_sum (kernel parameter space)
@@ -171,75 +310,145 @@ __global__ void k_sum(const __grid_constant__ SumArgs a, int count, size_t n, u6
   }
 }
 
-// m_k = rint((2 scale / N) sum_j (cos(pi r_j k / N) re_j + sin(pi r_j k / N) im_j))
-__global__ void k_encode(const double* __restrict__ re, const double* __restrict__ im, size_t batch, int log_n,
-                         const int32_t* __restrict__ r, const double* __restrict__ cs, const double* __restrict__ sn,
-                         double scale, int64_t* __restrict__ m) {
-  const int N = 1 << log_n, n = N / 2, mask = 2 * N - 1;
-  const size_t count = batch * (size_t)N;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = i / N;
-    const long long k = (long long)(i % N);
-    const double* zr = re + p * n;
-    const double* zi = im + p * n;
-    double s = 0.0;
-    for (int j = 0; j < n; ++j) {
-      const int t = (int)((k * r[j]) & mask);
-      s += cs[t] * zr[j] + sn[t] * zi[j];
+// ---- canonical embedding by FFT ---------------------------------------------
+// With omega = exp(i pi / N) and n = N / 2: every slot root zeta_j = omega^r_j
+// has r_j = 5^j = 1 mod 4, so zeta_j^n = i and, for a real m of degree < N,
+//   m(zeta_j) = w(zeta_j),  w_k = m_k + i m_(k+n)  (k < n),
+// a complex polynomial of degree < n.  The r_j run over all residues 1 mod 4 in
+// [0, 2N), so zeta_j = omega W^t with W = omega^4 = exp(2 pi i / n) and
+// t = pos_j = (r_j - 1) / 4 a permutation of [0, n):
+//   decode:  z_j = Z[pos_j] / scale,  Z[t] = sum_k (w_k omega^k) W^(t k)
+//   encode:  w_k = omega^-k (1/n) sum_t Y[t] W^(-t k),  Y[pos_j] = scale z_j,
+//            m_k = round(Re w_k), m_(k+n) = round(Im w_k)
+// Length-n radix-2 decimation in time on a bit-reversed load, in shared memory,
+// with the stage twiddles W^j (j < n/2) staged in shared memory too.
+
+// DIT stages; a bit-reversed on entry, natural order on exit; w[j] = W^j
+__device__ void fft_stages(double2* a, const double2* w, int log_m, double sign) {
+  const int n = 1 << log_m;
+  for (int lg = 1; lg <= log_m; ++lg) {
+    const int half = 1 << (lg - 1);
+    for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+      const int g = b >> (lg - 1), j = b & (half - 1);
+      const int i0 = (g << lg) + j;
+      const double2 t = w[j << (log_m - lg)];
+      const double wr = t.x, wi = sign * t.y;
+      const double2 u = a[i0], x = a[i0 + half];
+      const double vr = x.x * wr - x.y * wi, vi = x.x * wi + x.y * wr;
+      a[i0] = make_double2(u.x + vr, u.y + vi);
+      a[i0 + half] = make_double2(u.x - vr, u.y - vi);
     }
-    m[i] = (int64_t)rint(s * (2.0 * scale / N));
+    __syncthreads();
   }
 }
 
-// z_j = sum_k m_k exp(i pi r_j k / N) / scale, m centred
-__global__ void k_decode(const u64* __restrict__ m, size_t batch, int log_n, u64 q, const int32_t* __restrict__ r,
-                         const double* __restrict__ cs, const double* __restrict__ sn, double scale,
-                         double* __restrict__ re, double* __restrict__ im) {
-  const int N = 1 << log_n, n = N / 2, mask = 2 * N - 1;
-  const size_t count = batch * (size_t)n;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = i / n, j = i % n;
-    const u64* mp = m + p * N;
-    const long long rj = r[j];
-    double sr = 0.0, si = 0.0;
-    for (int k = 0; k < N; ++k) {
-      const u64 x = mp[k];
-      const double v = x > q / 2 ? -(double)(q - x) : (double)x;
-      const int t = (int)((rj * k) & mask);
-      sr += v * cs[t];
-      si += v * sn[t];
-    }
-    re[i] = sr / scale;
-    im[i] = si / scale;
+__device__ __forceinline__ int brev(int x, int bits) { return (int)(__brev((unsigned)x) >> (32 - bits)); }
+
+// smem: a [n] + w [n/2] double2
+__global__ void __launch_bounds__(kThreads)
+    k_encode(const double* __restrict__ re, const double* __restrict__ im, int log_n,
+             const int32_t* __restrict__ pos, const double2* __restrict__ fftw, const double2* __restrict__ twist,
+             double scale, int64_t* __restrict__ m) {
+  extern __shared__ double2 z[];
+  const int log_m = log_n - 1, n = 1 << log_m, N = 2 * n;
+  double2* w = z + n;
+  const size_t p = blockIdx.x;
+  for (int j = threadIdx.x; j < n / 2; j += blockDim.x) w[j] = fftw[j];
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    z[brev(pos[j], log_m)] = make_double2(re[p * n + j], im[p * n + j]);
+  __syncthreads();
+  fft_stages(z, w, log_m, -1.0);
+  const double f = scale / n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double2 t = twist[k], v = z[k];  // v * conj(omega^k)
+    m[p * N + k] = (int64_t)rint((v.x * t.x + v.y * t.y) * f);
+    m[p * N + k + n] = (int64_t)rint((v.y * t.x - v.x * t.y) * f);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_decode(const u64* __restrict__ m, int log_n, u64 q, const int32_t* __restrict__ pos,
+             const double2* __restrict__ fftw, const double2* __restrict__ twist, double scale, double inv,
+             double* __restrict__ re, double* __restrict__ im) {
+  extern __shared__ double2 z[];
+  const int log_m = log_n - 1, n = 1 << log_m, N = 2 * n;
+  double2* w = z + n;
+  const size_t p = blockIdx.x;
+  for (int j = threadIdx.x; j < n / 2; j += blockDim.x) w[j] = fftw[j];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const u64 a = m[p * N + k], b = m[p * N + k + n];
+    const double x = a > q / 2 ? -(double)(q - a) : (double)a;
+    const double y = b > q / 2 ? -(double)(q - b) : (double)b;
+    const double2 t = twist[k];
+    z[brev(k, log_m)] = make_double2(x * t.x - y * t.y, x * t.y + y * t.x);
+  }
+  __syncthreads();
+  fft_stages(z, w, log_m, 1.0);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double2 v = z[pos[j]];
+    // inv = 1 / scale when scale is a power of two (the product is then exact
+    // and equals the quotient), else 0
+    re[p * n + j] = inv != 0.0 ? v.x * inv : v.x / scale;
+    im[p * n + j] = inv != 0.0 ? v.y * inv : v.y / scale;
   }
 }
 
 int ew_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, (size_t)pl::sm_count() * 8); }
 
+template <typename K>
+cudaError_t allow_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)((3u << kMaxLogN) * sizeof(u64)));
+}
+
 }  // namespace
 
 struct ckks_ctx {
   int log_n = 0, N = 0, device = 0;
-  double scale = 1.0;
+  double scale = 1.0, inv_scale = 0.0;  // inv_scale: 1 / scale if scale is a power of two, else 0
   NttConst C{};
   u64* d_tw = nullptr;   // forward twiddles psi^bitrev(i), Montgomery form
   u64* d_itw = nullptr;  // inverse twiddles psi^-bitrev(i), Montgomery form
-  int32_t* d_r = nullptr;
-  double* d_cos = nullptr;
-  double* d_sin = nullptr;
+  int32_t* d_pos = nullptr;    // slot j -> (r_j - 1) / 4
+  double2* d_fftw = nullptr;   // W^j = exp(2 pi i j / n), j < n / 2
+  double2* d_twist = nullptr;  // omega^k = exp(i pi k / N), k < n
   pl::Scratch scratch;
+  u64* d_pk = nullptr;    // prepared [b^ | a^], Montgomery form (NULL until prepared)
+  u64* d_shat = nullptr;  // prepared s^, Montgomery form
 
   ~ckks_ctx() {
+    cudaFree(d_pk);
+    cudaFree(d_shat);
     cudaFree(d_tw);
     cudaFree(d_itw);
-    cudaFree(d_r);
-    cudaFree(d_cos);
-    cudaFree(d_sin);
+    cudaFree(d_pos);
+    cudaFree(d_fftw);
+    cudaFree(d_twist);
   }
+  int threads() const { return std::min(N / 2, kThreads); }
 
-  pl_status ntt(u64* polys, size_t count, bool inverse, cudaStream_t s) {
-    const int threads = std::min(N / 2, 1024);
-    k_ntt<<<(unsigned)count, threads, (size_t)N * sizeof(u64), s>>>(polys, inverse ? d_itw : d_tw, C, inverse);
+  pl_status launch_encrypt(const u64* pk, const int64_t* d_m, const int8_t* d_v, const int32_t* d_e0,
+                           const int32_t* d_e1, size_t batch, u64* d_c, cudaStream_t s) {
+    k_encrypt<<<(unsigned)batch, threads(), 3 * poly_bytes(), s>>>(pk, d_m, d_v, d_e0, d_e1, d_tw, d_itw, C, d_c);
+    pl::note_launch();
+    PL_CUDA_TRY(cudaGetLastError());
+    return PL_OK;
+  }
+  pl_status launch_decrypt(const u64* d_c, const u64* shat, size_t batch, u64* d_m, cudaStream_t s) {
+    k_decrypt<<<(unsigned)batch, threads(), 2 * poly_bytes(), s>>>(d_c, shat, d_tw, d_itw, C, d_m);
+    pl::note_launch();
+    PL_CUDA_TRY(cudaGetLastError());
+    return PL_OK;
+  }
+  int fft_threads() const { return std::min(N / 4, kThreads); }
+  size_t fft_smem() const { return (size_t)(N / 2 + N / 4) * sizeof(double2); }
+  size_t poly_bytes() const { return (size_t)N * sizeof(u64); }
+
+  // dst [2][N] = NTT(src0), NTT(src1) (src1 may be NULL: one polynomial),
+  // in Montgomery form if mont
+  template <typename T>
+  pl_status ntt(const T* src0, const T* src1, u64* dst, bool mont, cudaStream_t s) {
+    k_ntt<T><<<src1 ? 2 : 1, threads(), 2 * poly_bytes(), s>>>(src0, src1, dst, d_tw, C, mont ? 1 : 0);
     pl::note_launch();
     PL_CUDA_TRY(cudaGetLastError());
     return PL_OK;
@@ -251,7 +460,7 @@ extern "C" {
 pl_status ckks_create(int log_n, uint64_t q, double scale, ckks_ctx** out) {
   using namespace pl;
   clear_error();
-  if (!out || log_n < 4 || log_n > 14 || !(scale > 0)) return fail(PL_EINVAL, "need 4 <= log_n <= 14, scale > 0");
+  if (!out || log_n < 4 || log_n > kMaxLogN || !(scale > 0)) return fail(PL_EINVAL, "need 4 <= log_n <= 13, scale > 0");
   const int N = 1 << log_n;
   if (q >= (1ull << 62) || q < 3 || q % (2ull * N) != 1 || !h_prime(q))
     return fail(PL_EINVAL, "q must be a prime < 2^62 with q = 1 mod 2N");
@@ -260,8 +469,10 @@ pl_status ckks_create(int log_n, uint64_t q, double scale, ckks_ctx** out) {
   c->log_n = log_n;
   c->N = N;
   c->scale = scale;
+  int ex = 0;
+  if (std::frexp(scale, &ex) == 0.5) c->inv_scale = std::ldexp(1.0, 1 - ex);
   cudaGetDevice(&c->device);
-  // primitive 2N-th root of unity
+  // primitive 2N-th root of unity: psi^N = -1
   u64 psi = 0;
   for (u64 g = 2; g < 1000 && !psi; ++g) {
     const u64 x = h_pow(g, (q - 1) / (2ull * N), q);
@@ -271,11 +482,7 @@ pl_status ckks_create(int log_n, uint64_t q, double scale, ckks_ctx** out) {
   const u64 R = (u64)(((u128)1 << 64) % q);
   u64 qinv = 1;
   for (int i = 0; i < 6; ++i) qinv *= 2 - q * qinv;
-  c->C.q = q;
-  c->C.qn = (u64)0 - qinv;
-  c->C.r2 = h_mul(R, R, q);
-  c->C.ninv = h_mul(h_pow((u64)N, q - 2, q), R, q);
-  c->C.log_n = log_n;
+  const u64 ninv = h_pow((u64)N, q - 2, q);
   std::vector<u64> tw(N), itw(N);
   const u64 ipsi = h_pow(psi, q - 2, q);
   for (int i = 0; i < N; ++i) {
@@ -283,14 +490,19 @@ pl_status ckks_create(int log_n, uint64_t q, double scale, ckks_ctx** out) {
     tw[i] = h_mul(h_pow(psi, (u64)e, q), R, q);
     itw[i] = h_mul(h_pow(ipsi, (u64)e, q), R, q);
   }
-  std::vector<int32_t> r(N / 2);
-  u64 x = 1;
-  for (int j = 0; j < N / 2; ++j) { r[j] = (int32_t)x; x = x * 5 % (2ull * N); }
-  std::vector<double> cs(2 * N), sn(2 * N);
-  for (int t = 0; t < 2 * N; ++t) {
-    cs[t] = std::cos(M_PI * t / N);
-    sn[t] = std::sin(M_PI * t / N);
-  }
+  c->C.q = q;
+  c->C.qn = (u64)0 - qinv;
+  c->C.r2 = h_mul(R, R, q);
+  c->C.ninv = h_mul(ninv, R, q);
+  c->C.last = h_mul(itw[1], ninv, q);
+  c->C.log_n = log_n;
+  const int n = N / 2;
+  std::vector<int32_t> pos(n);
+  u64 x = 1;  // r_j = 5^j mod 2N
+  for (int j = 0; j < n; ++j) { pos[j] = (int32_t)((x - 1) / 4); x = x * 5 % (2ull * N); }
+  std::vector<double2> fftw(n / 2), twist(n);
+  for (int j = 0; j < n / 2; ++j) fftw[j] = make_double2(std::cos(M_PI * 4 * j / N), std::sin(M_PI * 4 * j / N));
+  for (int k = 0; k < n; ++k) twist[k] = make_double2(std::cos(M_PI * k / N), std::sin(M_PI * k / N));
   cudaError_t e = cudaSuccess;
   auto up = [&](void** d, const void* h, size_t bytes) {
     if (e != cudaSuccess) return;
@@ -299,11 +511,12 @@ pl_status ckks_create(int log_n, uint64_t q, double scale, ckks_ctx** out) {
   };
   up((void**)&c->d_tw, tw.data(), N * sizeof(u64));
   up((void**)&c->d_itw, itw.data(), N * sizeof(u64));
-  up((void**)&c->d_r, r.data(), r.size() * sizeof(int32_t));
-  up((void**)&c->d_cos, cs.data(), cs.size() * sizeof(double));
-  up((void**)&c->d_sin, sn.data(), sn.size() * sizeof(double));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ntt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((1 << 14) * sizeof(u64)));
+  up((void**)&c->d_pos, pos.data(), pos.size() * sizeof(int32_t));
+  up((void**)&c->d_fftw, fftw.data(), fftw.size() * sizeof(double2));
+  up((void**)&c->d_twist, twist.data(), twist.size() * sizeof(double2));
+  for (cudaError_t a : {allow_smem(k_ntt<u64>), allow_smem(k_ntt<int8_t>), allow_smem(k_encrypt),
+                        allow_smem(k_decrypt), allow_smem(k_keygen), allow_smem(k_encode), allow_smem(k_decode)})
+    if (e == cudaSuccess) e = a;
   if (e != cudaSuccess) { delete c; return cuda_fail(e, "ckks tables"); }
   c->scratch.device = c->device;
   *out = c;
@@ -321,9 +534,9 @@ pl_status ckks_encode(ckks_ctx* ctx, const double* d_re, const double* d_im, siz
   if (!ctx) return fail(PL_EINVAL, "ctx is NULL");
   if (!batch) return PL_OK;
   if (!d_re || !d_im || !d_m) return fail(PL_EINVAL, "NULL buffer");
-  const size_t n = batch * (size_t)ctx->N;
-  k_encode<<<ew_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(d_re, d_im, batch, ctx->log_n, ctx->d_r,
-                                                                      ctx->d_cos, ctx->d_sin, ctx->scale, d_m);
+  if (batch > 0x7fffffff) return fail(PL_ERANGE, "batch too large");
+  k_encode<<<(unsigned)batch, ctx->fft_threads(), ctx->fft_smem(), static_cast<cudaStream_t>(stream)>>>(
+      d_re, d_im, ctx->log_n, ctx->d_pos, ctx->d_fftw, ctx->d_twist, ctx->scale, d_m);
   note_launch();
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
@@ -335,9 +548,9 @@ pl_status ckks_decode(ckks_ctx* ctx, const uint64_t* d_m, size_t batch, double* 
   if (!ctx) return fail(PL_EINVAL, "ctx is NULL");
   if (!batch) return PL_OK;
   if (!d_re || !d_im || !d_m) return fail(PL_EINVAL, "NULL buffer");
-  const size_t n = batch * (size_t)(ctx->N / 2);
-  k_decode<<<ew_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(d_m, batch, ctx->log_n, ctx->C.q, ctx->d_r,
-                                                                      ctx->d_cos, ctx->d_sin, ctx->scale, d_re, d_im);
+  if (batch > 0x7fffffff) return fail(PL_ERANGE, "batch too large");
+  k_decode<<<(unsigned)batch, ctx->fft_threads(), ctx->fft_smem(), static_cast<cudaStream_t>(stream)>>>(
+      d_m, ctx->log_n, ctx->C.q, ctx->d_pos, ctx->d_fftw, ctx->d_twist, ctx->scale, ctx->inv_scale, d_re, d_im);
   note_launch();
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
@@ -348,22 +561,14 @@ pl_status ckks_keygen(ckks_ctx* ctx, const int8_t* d_s, const uint64_t* d_a, con
   using namespace pl;
   clear_error();
   if (!ctx || !d_s || !d_a || !d_e || !d_b) return fail(PL_EINVAL, "NULL argument");
-  const int N = ctx->N;
+  const size_t N = (size_t)ctx->N;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto* t = static_cast<u64*>(ctx->scratch.get(2 * (size_t)N * sizeof(u64), s));
+  auto* t = static_cast<u64*>(ctx->scratch.get(2 * N * sizeof(u64), s));
   if (!t) return fail(PL_ENOMEM, "scratch");
-  u64 *ta = t, *ts = t + N;
-  PL_CUDA_TRY(cudaMemcpyAsync(ta, d_a, N * sizeof(u64), cudaMemcpyDeviceToDevice, s));
-  k_to_modq<int8_t><<<ew_grid(N), 256, 0, s>>>(d_s, N, ctx->C.q, ts);
-  note_launch();
-  pl_status rc = ctx->ntt(ta, 1, false, s);
-  if (!rc) rc = ctx->ntt(ts, 1, false, s);
+  pl_status rc = ctx->ntt<u64>(d_a, nullptr, t, true, s);  // a^ (Montgomery form)
+  if (!rc) rc = ctx->ntt<int8_t>(d_s, nullptr, t + N, false, s);  // s^
   if (rc) return rc;
-  k_pointwise<<<ew_grid(N), 256, 0, s>>>(ta, ts, N, N, ctx->C, ta);
-  note_launch();
-  rc = ctx->ntt(ta, 1, true, s);
-  if (rc) return rc;
-  k_keygen_finish<<<ew_grid(N), 256, 0, s>>>(ta, d_e, N, ctx->C.q, d_b);
+  k_keygen<<<1, ctx->threads(), 2 * ctx->poly_bytes(), s>>>(t, t + N, d_e, ctx->d_itw, ctx->C, d_b);
   note_launch();
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
@@ -376,31 +581,13 @@ pl_status ckks_encrypt(ckks_ctx* ctx, const uint64_t* d_b, const uint64_t* d_a, 
   clear_error();
   if (!ctx || !d_b || !d_a || !d_m || !d_v || !d_e0 || !d_e1 || !d_c) return fail(PL_EINVAL, "NULL argument");
   if (!batch) return PL_OK;
-  const size_t N = (size_t)ctx->N, n = batch * N;
+  if (batch > 0x7fffffff) return fail(PL_ERANGE, "batch too large");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // tb, ta: the key in the transform domain; tv: v; bv, av: products
-  auto* t = static_cast<u64*>(ctx->scratch.get((2 * N + 3 * n) * sizeof(u64), s));
-  if (!t) return fail(PL_ENOMEM, "scratch");
-  u64 *tb = t, *ta = t + N, *tv = t + 2 * N, *bv = tv + n, *av = bv + n;
-  PL_CUDA_TRY(cudaMemcpyAsync(tb, d_b, N * sizeof(u64), cudaMemcpyDeviceToDevice, s));
-  PL_CUDA_TRY(cudaMemcpyAsync(ta, d_a, N * sizeof(u64), cudaMemcpyDeviceToDevice, s));
-  k_to_modq<int8_t><<<ew_grid(n), 256, 0, s>>>(d_v, n, ctx->C.q, tv);
-  note_launch();
-  pl_status rc = ctx->ntt(tb, 1, false, s);
-  if (!rc) rc = ctx->ntt(ta, 1, false, s);
-  if (!rc) rc = ctx->ntt(tv, batch, false, s);
+  auto* pk = static_cast<u64*>(ctx->scratch.get(2 * ctx->poly_bytes(), s));
+  if (!pk) return fail(PL_ENOMEM, "scratch");
+  pl_status rc = ctx->ntt<u64>(d_b, d_a, pk, true, s);  // [b^ | a^], Montgomery form
   if (rc) return rc;
-  k_pointwise<<<ew_grid(n), 256, 0, s>>>(tv, tb, N, n, ctx->C, bv);
-  k_pointwise<<<ew_grid(n), 256, 0, s>>>(tv, ta, N, n, ctx->C, av);
-  note_launch();
-  note_launch();
-  rc = ctx->ntt(bv, batch, true, s);
-  if (!rc) rc = ctx->ntt(av, batch, true, s);
-  if (rc) return rc;
-  k_encrypt_finish<<<ew_grid(n), 256, 0, s>>>(bv, av, d_e0, d_e1, d_m, batch, (int)N, ctx->C.q, d_c);
-  note_launch();
-  PL_CUDA_TRY(cudaGetLastError());
-  return PL_OK;
+  return ctx->launch_encrypt(pk, d_m, d_v, d_e0, d_e1, batch, d_c, s);
 }
 
 pl_status ckks_sum(ckks_ctx* ctx, const uint64_t* const* d_cts, int count, size_t batch, uint64_t* d_out,
@@ -427,26 +614,50 @@ pl_status ckks_decrypt(ckks_ctx* ctx, const uint64_t* d_c, const int8_t* d_s, si
   clear_error();
   if (!ctx || !d_c || !d_s || !d_m) return fail(PL_EINVAL, "NULL argument");
   if (!batch) return PL_OK;
-  const size_t N = (size_t)ctx->N, n = batch * N;
+  if (batch > 0x7fffffff) return fail(PL_ERANGE, "batch too large");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto* t = static_cast<u64*>(ctx->scratch.get((N + n) * sizeof(u64), s));
-  if (!t) return fail(PL_ENOMEM, "scratch");
-  u64 *ts = t, *c1 = t + N;
-  k_to_modq<int8_t><<<ew_grid(N), 256, 0, s>>>(d_s, N, ctx->C.q, ts);
-  k_take_c1<<<ew_grid(n), 256, 0, s>>>(d_c, batch, (int)N, c1);
-  note_launch();
-  note_launch();
-  pl_status rc = ctx->ntt(ts, 1, false, s);
-  if (!rc) rc = ctx->ntt(c1, batch, false, s);
+  auto* shat = static_cast<u64*>(ctx->scratch.get(ctx->poly_bytes(), s));
+  if (!shat) return fail(PL_ENOMEM, "scratch");
+  pl_status rc = ctx->ntt<int8_t>(d_s, nullptr, shat, true, s);
   if (rc) return rc;
-  k_pointwise<<<ew_grid(n), 256, 0, s>>>(c1, ts, N, n, ctx->C, c1);
-  note_launch();
-  rc = ctx->ntt(c1, batch, true, s);
-  if (rc) return rc;
-  k_decrypt_finish<<<ew_grid(n), 256, 0, s>>>(d_c, c1, batch, (int)N, ctx->C.q, d_m);
-  note_launch();
-  PL_CUDA_TRY(cudaGetLastError());
-  return PL_OK;
+  return ctx->launch_decrypt(d_c, shat, batch, d_m, s);
+}
+
+pl_status ckks_prepare_public_key(ckks_ctx* ctx, const uint64_t* d_b, const uint64_t* d_a, void* stream) {
+  using namespace pl;
+  clear_error();
+  if (!ctx || !d_b || !d_a) return fail(PL_EINVAL, "NULL argument");
+  if (!ctx->d_pk) PL_CUDA_TRY(cudaMalloc(&ctx->d_pk, 2 * ctx->poly_bytes()));
+  return ctx->ntt<u64>(d_b, d_a, ctx->d_pk, true, static_cast<cudaStream_t>(stream));
+}
+
+pl_status ckks_prepare_secret_key(ckks_ctx* ctx, const int8_t* d_s, void* stream) {
+  using namespace pl;
+  clear_error();
+  if (!ctx || !d_s) return fail(PL_EINVAL, "NULL argument");
+  if (!ctx->d_shat) PL_CUDA_TRY(cudaMalloc(&ctx->d_shat, ctx->poly_bytes()));
+  return ctx->ntt<int8_t>(d_s, nullptr, ctx->d_shat, true, static_cast<cudaStream_t>(stream));
+}
+
+pl_status ckks_encrypt_prepared(ckks_ctx* ctx, const int64_t* d_m, const int8_t* d_v, const int32_t* d_e0,
+                                const int32_t* d_e1, size_t batch, uint64_t* d_c, void* stream) {
+  using namespace pl;
+  clear_error();
+  if (!ctx || !d_m || !d_v || !d_e0 || !d_e1 || !d_c) return fail(PL_EINVAL, "NULL argument");
+  if (!ctx->d_pk) return fail(PL_EINVAL, "no public key prepared");
+  if (!batch) return PL_OK;
+  if (batch > 0x7fffffff) return fail(PL_ERANGE, "batch too large");
+  return ctx->launch_encrypt(ctx->d_pk, d_m, d_v, d_e0, d_e1, batch, d_c, static_cast<cudaStream_t>(stream));
+}
+
+pl_status ckks_decrypt_prepared(ckks_ctx* ctx, const uint64_t* d_c, size_t batch, uint64_t* d_m, void* stream) {
+  using namespace pl;
+  clear_error();
+  if (!ctx || !d_c || !d_m) return fail(PL_EINVAL, "NULL argument");
+  if (!ctx->d_shat) return fail(PL_EINVAL, "no secret key prepared");
+  if (!batch) return PL_OK;
+  if (batch > 0x7fffffff) return fail(PL_ERANGE, "batch too large");
+  return ctx->launch_decrypt(d_c, ctx->d_shat, batch, d_m, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -77,36 +77,37 @@ __global__ void __launch_bounds__(256) k_imad_lohi(uint32_t* out, int iters, uin
   out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = y;
 }
 
+// 16 independent float64 FMA chains (fma.rn.f64) with distinct operands
+__global__ void __launch_bounds__(256) k_dfma(double* out, int iters, uint32_t seed) {
+  double acc[16], a[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) { a[j] = 1.0 + 1e-9 * (seed * (j + 7) + threadIdx.x); acc[j] = a[j] * 1e-3; }
+  double b = 0.999999 - 1e-12 * (seed ^ threadIdx.x);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) asm volatile("fma.rn.f64 %0, %1, %2, %0;" : "+d"(acc[j]) : "d"(a[j]), "d"(b));
+    b = 0.999999 - 1e-18 * acc[it & 15];
+  }
+  double y = 0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) y += acc[j];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = y;
+}
+
 constexpr int kRowS = 16;
 // IMAD per iteration and thread: 2 rows x 2 S multiply-add halves + 2 mul.lo
 constexpr double kRowsImadPerIter = 2.0 * 2 * kRowS + 2;
 constexpr double kWideImadPerIter = 2.0 * 16;  // 16 mad.wide (+1 mul.lo ignored), 2 IMAD each
 constexpr double kLoHiImadPerIter = 2.0 * 16;  // 16 mad.lo + 16 mad.hi
+constexpr double kDfmaFlopPerIter = 2.0 * 16;  // 16 fma.rn.f64 (+1 fma ignored), 2 FLOP each
 
-}  // namespace
-}  // namespace pl
-
-extern "C" pl_status paillier_imad_peak(int mix, double target_ms, double* imad_per_s, double* elapsed_ms,
-                                        void* stream) {
-  using namespace pl;
-  clear_error();
-  if (!imad_per_s || mix < 0 || mix > 2 || !(target_ms > 0)) return fail(PL_EINVAL, "bad argument");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int blocks = sm_count() * 8, threads = 256;
-  uint32_t* out = nullptr;
-  PL_CUDA_TRY(cudaMalloc(&out, sizeof(uint32_t) * (size_t)blocks * threads));
+// Runs launch(iters, seed) once to calibrate, then for about target_ms;
+// returns the timed iterations and milliseconds.
+template <typename F>
+cudaError_t timed_probe(F launch, double target_ms, cudaStream_t s, int* iters_out, float* ms_out) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  auto launch = [&](int iters, uint32_t seed) {
-    if (mix == 0)
-      k_imad_rows<kRowS><<<blocks, threads, 0, s>>>(out, iters, seed);
-    else if (mix == 1)
-      k_imad_wide<<<blocks, threads, 0, s>>>(out, iters, seed);
-    else
-      k_imad_lohi<<<blocks, threads, 0, s>>>(out, iters, seed);
-  };
-  // calibrate
   int iters = 2000;
   float ms = 0.f;
   launch(iters, 1);
@@ -127,10 +128,57 @@ extern "C" pl_status paillier_imad_peak(int mix, double target_ms, double* imad_
   if (e == cudaSuccess) e = cudaGetLastError();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  *iters_out = iters;
+  *ms_out = ms;
+  return e;
+}
+
+}  // namespace
+}  // namespace pl
+
+extern "C" pl_status paillier_imad_peak(int mix, double target_ms, double* imad_per_s, double* elapsed_ms,
+                                        void* stream) {
+  using namespace pl;
+  clear_error();
+  if (!imad_per_s || mix < 0 || mix > 2 || !(target_ms > 0)) return fail(PL_EINVAL, "bad argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int blocks = sm_count() * 8, threads = 256;
+  uint32_t* out = nullptr;
+  PL_CUDA_TRY(cudaMalloc(&out, sizeof(uint32_t) * (size_t)blocks * threads));
+  auto launch = [&](int iters, uint32_t seed) {
+    if (mix == 0)
+      k_imad_rows<kRowS><<<blocks, threads, 0, s>>>(out, iters, seed);
+    else if (mix == 1)
+      k_imad_wide<<<blocks, threads, 0, s>>>(out, iters, seed);
+    else
+      k_imad_lohi<<<blocks, threads, 0, s>>>(out, iters, seed);
+  };
+  int iters = 0;
+  float ms = 0.f;
+  const cudaError_t e = timed_probe(launch, target_ms, s, &iters, &ms);
   cudaFree(out);
   if (e != cudaSuccess) return cuda_fail(e, "imad peak kernel");
   const double per = mix == 0 ? kRowsImadPerIter : (mix == 1 ? kWideImadPerIter : kLoHiImadPerIter);
   *imad_per_s = per * iters * (double)blocks * threads / (ms * 1e-3);
+  if (elapsed_ms) *elapsed_ms = ms;
+  return PL_OK;
+}
+
+extern "C" pl_status paillier_fp64_peak(double target_ms, double* flop_per_s, double* elapsed_ms, void* stream) {
+  using namespace pl;
+  clear_error();
+  if (!flop_per_s || !(target_ms > 0)) return fail(PL_EINVAL, "bad argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int blocks = sm_count() * 8, threads = 256;
+  double* out = nullptr;
+  PL_CUDA_TRY(cudaMalloc(&out, sizeof(double) * (size_t)blocks * threads));
+  auto launch = [&](int iters, uint32_t seed) { k_dfma<<<blocks, threads, 0, s>>>(out, iters, seed); };
+  int iters = 0;
+  float ms = 0.f;
+  const cudaError_t e = timed_probe(launch, target_ms, s, &iters, &ms);
+  cudaFree(out);
+  if (e != cudaSuccess) return cuda_fail(e, "fp64 peak kernel");
+  *flop_per_s = kDfmaFlopPerIter * iters * (double)blocks * threads / (ms * 1e-3);
   if (elapsed_ms) *elapsed_ms = ms;
   return PL_OK;
 }

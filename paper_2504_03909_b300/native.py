@@ -45,6 +45,7 @@ SIGNATURES = {
     "paillier_last_error": (C.c_char_p, []),
     "paillier_test_mont_mul": (_i, [_i, _i, _vp, _vp, _vp, _sz, _vp, _vp]),
     "paillier_imad_peak": (_i, [_i, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
+    "paillier_fp64_peak": (_i, [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
     "paillier_launch_count": (C.c_ulonglong, []),
     "paillier_profile": (_i, [_i]),
     "paillier_profile_read": (_i, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
@@ -96,6 +97,10 @@ SIGNATURES.update({
     "ckks_encrypt": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "ckks_sum": (_i, [_vp, C.POINTER(C.c_void_p), _i, _sz, _vp, _vp]),
     "ckks_decrypt": (_i, [_vp, _vp, _vp, _sz, _vp, _vp]),
+    "ckks_prepare_public_key": (_i, [_vp, _vp, _vp, _vp]),
+    "ckks_prepare_secret_key": (_i, [_vp, _vp, _vp]),
+    "ckks_encrypt_prepared": (_i, [_vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "ckks_decrypt_prepared": (_i, [_vp, _vp, _sz, _vp, _vp]),
 })
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
 

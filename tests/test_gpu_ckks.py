@@ -3,12 +3,24 @@ against the CKKS oracle.
 
 Integer stages (key generation, encryption, addition, decryption: products in
 R_q by the negacyclic NTT) are compared bit for bit with the oracle's exact
-products on the same inputs.  Encoding and decoding are float64 sums of N/2 and
-N terms taken in different orders on the two sides; each side's rounding error
-is at most gamma_n * sum |term| (gamma_n = n u / (1 - n u), u = 2^-53, plus two
-ulps for the table's cos/sin and one for the product), so the two results differ
-by at most twice that, plus one unit for a rounding boundary crossed on one side
-only (encoding rounds to integers)."""
+products on the same inputs.
+
+Encoding and decoding are float64 on both sides, computed differently: the
+oracle sums the terms of the embedding directly, the kernels use a radix-2
+FFT of length N/2 over the slot structure.  Each is compared with the exact value through its own error
+bound, and the two bounds are added (plus one unit where the result is rounded
+to an integer, since the two sides may fall on either side of a rounding
+boundary):
+  direct sum of n terms   |err| <= gamma_(n+3) * sum |term|
+                          (gamma_k = k u / (1 - k u), u = 2^-53; three more
+                          roundings for the table's cos/sin and the product)
+  radix-2 FFT, length n   ||err||_2 <= ||y||_2 * L eta / (1 - L eta), L = log2 n,
+                          eta = mu + gamma_4 (sqrt 2 + mu), mu = 2u the twiddle
+                          error (Higham, Accuracy and Stability of Numerical
+                          Algorithms, 2nd ed., Thm. 24.2), ||y||_2 = sqrt(n) ||x||_2;
+                          the tests take L = log2 N and sqrt(N) (an upper bound);
+                          the twist by omega^k and the final scaling add
+                          gamma_5 sqrt 2 relative to the same norm."""
 
 import numpy as np
 import pytest
@@ -24,6 +36,18 @@ U = 2.0 ** -53
 
 def _gamma(n):
     return (n + 3) * U / (1 - (n + 3) * U)
+
+
+def _g(k):
+    return k * U / (1 - k * U)
+
+
+def _fft_rel(N):
+    """Relative 2-norm error of the kernels' FFT path (see the module text)."""
+    L = N.bit_length() - 1
+    mu = 2 * U
+    eta = mu + _g(4) * (np.sqrt(2) + mu)
+    return L * eta / (1 - L * eta) + _g(5) * np.sqrt(2)
 
 
 def _inputs(N, q, batch, seed):
@@ -85,7 +109,34 @@ def test_encrypt_sum_decrypt_bit_exact(log_n, batch):
         assert _u64(dec[i]) == ock.decrypt(t, s, q), f"decrypt {i}"
 
 
-@pytest.mark.parametrize("log_n,batch,mag", [(4, 2, 1.0), (10, 3, 1e4), (12, 1, 1e5)])
+@pytest.mark.parametrize("log_n,batch", [(4, 3), (13, 3)])
+def test_prepared_keys_bit_exact(log_n, batch):
+    """encrypt/decrypt with keys prepared once equal the per-call forms and the oracle."""
+    N = 1 << log_n
+    q = synth.ckks_prime(log_n)
+    ctx = G.Context(log_n, q, 2.0 ** 30)
+    s, a, e, v, e0, e1 = _inputs(N, q, batch, 51 + log_n)
+    b = ock.keygen(s, a, e, q)
+    b_d = _dev(np.array(b, dtype=np.uint64), torch.int64)
+    a_d, s_d = _dev(a, torch.int64), _dev(s)
+    m = synth.rng_misc(53).integers(-(2 ** 40), 2 ** 40, size=(batch, N), dtype=np.int64)
+    args = (_dev(m), _dev(v), _dev(e0), _dev(e1))
+    with pytest.raises(Exception):
+        ctx.encrypt_prepared(*args)  # nothing prepared yet
+    ctx.prepare_public_key(b_d, a_d)
+    ctx.prepare_secret_key(s_d)
+    c1 = ctx.encrypt_prepared(*args)
+    c2 = ctx.encrypt(b_d, a_d, *args)
+    assert torch.equal(c1, c2)
+    d1 = ctx.decrypt_prepared(c1)
+    assert torch.equal(d1, ctx.decrypt(c1, s_d))
+    i = batch - 1
+    c0o, c1o = ock.encrypt(b, a, m[i], v[i], e0[i], e1[i], q)
+    assert _u64(c1[i, 0]) == c0o and _u64(c1[i, 1]) == c1o
+    assert _u64(d1[i]) == ock.decrypt((c0o, c1o), s, q)
+
+
+@pytest.mark.parametrize("log_n,batch,mag", [(4, 2, 1.0), (10, 3, 1e4), (12, 1, 1e5), (13, 1, 1e4)])
 def test_encode_within_float_bound(log_n, batch, mag):
     N, scale = 1 << log_n, 2.0 ** 40
     ctx = G.Context(log_n, synth.ckks_prime(log_n), scale)
@@ -95,15 +146,17 @@ def test_encode_within_float_bound(log_n, batch, mag):
     got = ctx.encode(_dev(re), _dev(im)).cpu().numpy()
     for i in range(batch):
         want = ock.encode(re[i] + 1j * im[i], N, scale)
-        terms = (np.abs(re[i]) + np.abs(im[i])).sum() * (2.0 * scale / N)
-        tol = 1 + 2 * _gamma(N // 2) * terms
+        f = 2.0 * scale / N
+        terms = (np.abs(re[i]) + np.abs(im[i])).sum() * f
+        z2 = np.sqrt((re[i] ** 2 + im[i] ** 2).sum())
+        tol = 1 + _gamma(N // 2) * terms + f * np.sqrt(N) * z2 * _fft_rel(N) + U * np.abs(want).max()
         assert np.abs(got[i] - want).max() <= tol
         # and the encoding decodes back to the slots (the embedding is the right one)
         back = ock.decode(got[i], N, scale)
         assert np.abs(back - (re[i] + 1j * im[i])).max() <= N * (0.5 + tol) / scale + 1e-9 * mag
 
 
-@pytest.mark.parametrize("log_n,batch", [(4, 2), (10, 2), (12, 1)])
+@pytest.mark.parametrize("log_n,batch", [(4, 2), (10, 2), (12, 1), (13, 1)])
 def test_decode_within_float_bound(log_n, batch):
     N, scale = 1 << log_n, 2.0 ** 40
     q = synth.ckks_prime(log_n)
@@ -114,7 +167,9 @@ def test_decode_within_float_bound(log_n, batch):
     re, im = ctx.decode(_dev(mq, torch.int64))
     for i in range(batch):
         want = ock.decode(ock.centre([int(x) for x in mq[i]], q), N, scale)
-        tol = 2 * _gamma(N) * np.abs(mc[i]).astype(np.float64).sum() / scale
+        mf = mc[i].astype(np.float64)
+        tol = (_gamma(N) * np.abs(mf).sum() + np.sqrt(N) * np.sqrt((mf ** 2).sum()) * _fft_rel(N)) / scale
+        tol += U * np.abs(want).max()
         assert np.abs(re.cpu().numpy()[i] - want.real).max() <= tol
         assert np.abs(im.cpu().numpy()[i] - want.imag).max() <= tol
 
@@ -175,6 +230,8 @@ def test_edges():
         G.Context(log_n, q + 2, 2.0 ** 30)
     with pytest.raises(PaillierError):
         G.Context(log_n, 12289 * 12289, 2.0 ** 30)  # 12289 = 6 * 2048 + 1 is prime, its square is not
+    with pytest.raises(PaillierError):
+        G.Context(14, synth.ckks_prime(14), 2.0 ** 30)  # N = 16384 does not fit one CTA's shared memory
     # zero ciphertext (all-zero randomness and message) decrypts to zero
     z8 = torch.zeros(1, N, dtype=torch.int8, device="cuda")
     z32 = torch.zeros(1, N, dtype=torch.int32, device="cuda")
