@@ -43,7 +43,7 @@ METRIC = "2048-bit Paillier enc/s & encrypted-hist ct-mults/s; p50/p99 request m
 
 # DRAM bytes (read + write) per encryption of the current k_modexp ENC kernel, from the ncu
 # capture summarised in profiles/k_modexp_enc_2048bit_small.md, keyed by (n_bits, window)
-TRAFFIC_PER_ENC = {(2048, 5): 23.2e3 + 20.6e3}
+TRAFFIC_PER_ENC = {}
 
 
 # ----------------------------------------------------------------------------
@@ -54,31 +54,49 @@ def mont_imad(nl: int) -> int:
     return 4 * nl * nl + nl
 
 
-def modexp_montmuls(exp_bits: int, w: int, dec: bool) -> int:
-    """Montgomery products of one half-size exponentiation as the kernel runs it."""
-    nd = (exp_bits + w - 1) // w
-    pre = 2  # ENC: m n and r R; DEC: c_lo R and c_hi R^2
-    return pre + ((1 << w) - 2) + (nd - 1) * (w + 1) + 1
+def sliding_ops(e: int, w: int) -> int:
+    """Length of the left-to-right sliding-window schedule of exponent e > 0 as
+    the kernel runs it: one op for the leading window, then per zero bit outside
+    a window one squaring, per window of len bits len squarings + one product."""
+    i, n = e.bit_length() - 1, 0
+    while i >= 0:
+        if not (e >> i) & 1:
+            n, i = n + 1, i - 1
+            continue
+        j = max(i - w + 1, 0)
+        while not (e >> j) & 1:
+            j += 1
+        n += 1 if n == 0 else (i - j + 1) + 1
+        i = j - 1
+    return n
+
+
+def exp_montmuls(e: int, w: int, pre: int = 2, post: int = 1) -> int:
+    """Montgomery products of one exponentiation: `pre` to enter Montgomery form,
+    the odd-power table (one squaring + 2^(w-1) - 1 products), the schedule after
+    its leading window, `post` to leave."""
+    return pre + (1 << (w - 1)) + (sliding_ops(e, w) - 1) + post
 
 
 def enc_imad(n_bits: int, w: int, p: int, q: int) -> int:
     """One encryption as the kernel runs it, per CRT half (prime x, other prime x'):
-    mod x (L/2 limbs): r to Montgomery form (2), table, (x' mod (x-1)) exponent, out (1);
-    mod x^2 (L limbs): m n (1), to Montgomery (1), table, exponent x, post-factor (1)."""
+    mod x (L/2 limbs): exponent x' mod (x - 1); mod x^2 (L limbs): exponent x."""
     L = n_bits // 32
     total = 0
     for x, xo in ((p, q), (q, p)):
-        nd1 = -(-(xo % (x - 1)).bit_length() // w)
-        nd2 = -(-x.bit_length() // w)
-        table = (1 << w) - 2
-        total += (2 + table + (nd1 - 1) * (w + 1) + 1) * mont_imad(L // 2)
-        total += (2 + table + (nd2 - 1) * (w + 1) + 1) * mont_imad(L)
+        total += exp_montmuls(xo % (x - 1), w) * mont_imad(L // 2)
+        total += exp_montmuls(x, w) * mont_imad(L)
     return total
 
 
-def dec_imad(n_bits: int, w: int) -> int:
+def dec_imad(n_bits: int, w: int, p: int | None = None, q: int | None = None) -> int:
+    """One CRT decryption: c^(x - 1) mod x^2 per half.  Without the primes, an
+    exponent of n_bits/2 bits with half its bits set stands in."""
     L = n_bits // 32
-    return 2 * modexp_montmuls(n_bits // 2, w, True) * mont_imad(L)
+    if p is None:
+        e = int("10" * (n_bits // 4), 2)
+        return 2 * exp_montmuls(e, w) * mont_imad(L)
+    return sum(exp_montmuls(x - 1, w) for x in (p, q)) * mont_imad(L)
 
 
 # ----------------------------------------------------------------------------
@@ -1037,9 +1055,9 @@ def run_serving(args, cfg):
         cells = 2 * rq["F"] * rq["K"]
         if args.pack_bits:
             slots = (rq["nb"] - 2) // args.pack_bits
-            dec = -(-cells // slots) * dec_imad(rq["nb"], 5) + cells * (args.pack_bits + 2) * mont_imad(2 * L)
+            dec = -(-cells // slots) * dec_imad(rq["nb"], 6 if rq["nb"] >= 2048 else 5) + cells * (args.pack_bits + 2) * mont_imad(2 * L)
         else:
-            dec = cells * dec_imad(rq["nb"], 5)
+            dec = cells * dec_imad(rq["nb"], 6 if rq["nb"] >= 2048 else 5)
         return 2 * rq["M"] * rq["F"] * mont_imad(2 * L) + dec
 
     srv = P.Server(slots=args.slots, hbm_budget=budget)

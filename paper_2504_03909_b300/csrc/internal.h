@@ -108,6 +108,13 @@ pl_status launch_encrypt(pl_key* key, const uint64_t* d_m, const uint32_t* d_r, 
 pl_status launch_decrypt(pl_key* key, const uint32_t* d_ct, size_t count, void* d_out, bool u64, int* st,
                          cudaStream_t s, Scratch* scratch = nullptr);
 size_t decrypt_scratch_bytes(const pl_key* key, size_t count);
+
+// Sliding-window schedule of exponent e (> 0) for window w (layout in
+// ModexpParams); returns the number of ops, or -1 if more than maxops.
+int sliding_schedule(const plh::Big& e, int w, uint8_t* op, int maxops);
+
+// Window-table entries per instance (the odd powers below 2^w).
+__host__ __device__ constexpr size_t table_entries(int w) { return (size_t)1 << (w - 1); }
 pl_status launch_ct_prepare(pl_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_ctm, cudaStream_t s);
 pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, size_t ghs, const uint8_t* d_bins,
                       size_t bstride, int F, int K, const int32_t* d_node, int num_nodes, uint32_t* d_hist,

@@ -39,47 +39,49 @@ __global__ void k_decode(const uint64_t* __restrict__ s, const int32_t* __restri
   }
 }
 
-// Fixed-window exponentiation of one instance held by a group of T lanes.
-// acc: the base in Montgomery form on entry, base^e in Montgomery form on exit
-// (e given by nd window digits dg[], least significant first).  tbl: this
-// group's table of 2^w entries of S*T limbs; bs: its shared-memory column.
+// Sliding-window exponentiation of one instance held by a group of T lanes.
+// acc: the base in Montgomery form on entry, base^e in Montgomery form on exit,
+// e given by its schedule op[0..nop) (layout in ModexpParams).  tbl: this
+// group's table of 2^(w-1) entries of S*T limbs (the odd powers); bs: its
+// shared-memory column.  Every op is one Montgomery product.
 template <int S, int T>
-PL_DEV void window_exp(uint32_t (&acc)[S], const uint32_t (&n)[S], uint32_t np, const uint32_t* R1,
-                       const uint8_t* dg, int nd, int w, uint32_t* tbl, uint32_t* bs, int st, int k) {
+PL_DEV void window_exp(uint32_t (&acc)[S], const uint32_t (&n)[S], uint32_t np, const uint8_t* op, int nop, int w,
+                       uint32_t* tbl, uint32_t* bs, int st, int k) {
   constexpr int NL = S * T;
-  const int nent = 1 << w;
+  const int nent = 1 << (w - 1);
   uint32_t a[S], t[S];
-  const_slice<S>(a, R1, k);
-  store_slice<S>(tbl, a, k);            // base^0 = Montgomery one
-  store_slice<S>(tbl + NL, acc, k);     // base^1
+  store_slice<S>(tbl, acc, k);  // base^1
+  // base^2, staged as the multiplier of the table build
   __syncwarp();
   stage<S>(bs, st, acc, k);
   __syncwarp();
+  mont_mul<S, T>(t, acc, bs, st, n, np, k);
+  __syncwarp();
+  stage<S>(bs, st, t, k);
+  __syncwarp();
 #pragma unroll
   for (int j = 0; j < S; ++j) a[j] = acc[j];
-  for (int e = 2; e < nent; ++e) {
+  for (int e = 1; e < nent; ++e) {  // base^(2e + 1) = base^(2e - 1) base^2
     mont_mul<S, T>(t, a, bs, st, n, np, k);
     store_slice<S>(tbl + e * NL, t, k);
 #pragma unroll
     for (int j = 0; j < S; ++j) a[j] = t[j];
   }
-  // left to right: w squarings, then one product with the digit's table entry
-  load_slice_rw<S>(a, tbl + (size_t)dg[nd - 1] * NL, k);
-  for (int di = nd - 2; di >= 0; --di) {
-    const int d = dg[di];
-    for (int s = 0; s <= w; ++s) {
-      __syncwarp();
-      if (s < w) {
-        stage<S>(bs, st, a, k);
-      } else {
-        load_slice_rw<S>(t, tbl + (size_t)d * NL, k);
-        stage<S>(bs, st, t, k);
-      }
-      __syncwarp();
-      mont_mul<S, T>(t, a, bs, st, n, np, k);
-#pragma unroll
-      for (int j = 0; j < S; ++j) a[j] = t[j];
+  // most significant window first
+  load_slice_rw<S>(a, tbl + (size_t)(op[0] >> 1) * NL, k);
+  for (int i = 1; i < nop; ++i) {
+    const int v = op[i];
+    __syncwarp();
+    if (v == 0) {
+      stage<S>(bs, st, a, k);
+    } else {
+      load_slice_rw<S>(t, tbl + (size_t)(v >> 1) * NL, k);
+      stage<S>(bs, st, t, k);
     }
+    __syncwarp();
+    mont_mul<S, T>(t, a, bs, st, n, np, k);
+#pragma unroll
+    for (int j = 0; j < S; ++j) a[j] = t[j];
   }
 #pragma unroll
   for (int j = 0; j < S; ++j) acc[j] = a[j];
@@ -95,8 +97,8 @@ PL_DEV void window_exp(uint32_t (&acc)[S], const uint32_t (&n)[S], uint32_t np, 
 //        x^2 as a factor).  One exponent of n_bits/2 bits mod x (L/2 limbs) and
 //        one of n_bits/2 bits mod x^2 replace one of n_bits bits mod x^2.
 //   DEC: y[h][i] = c_i^(x - 1) mod x^2                (in = c [count][2L])
-// Every value is canonical.  tbl: per-group window table, 2^w entries of L
-// limbs for each group of the grid.
+// Every value is canonical.  tbl: per-group window table, 2^(w-1) entries of
+// L limbs for each group of the grid.
 template <int S, int T, bool DEC>
 __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ ModexpParams P,
                                                    const uint32_t* __restrict__ in, const uint64_t* __restrict__ msg,
@@ -113,8 +115,7 @@ __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ Modex
   uint32_t* bs = smem + g;
   const int st = ipb;
   const int w = P.w;
-  const int nent = 1 << w;
-  uint32_t* mytbl = tbl + ((size_t)blockIdx.x * ipb + g) * (size_t)nent * NL;
+  uint32_t* mytbl = tbl + ((size_t)blockIdx.x * ipb + g) * table_entries(w) * NL;
   const size_t nchunk = (count + IPW - 1) / IPW;
   const size_t nitems = 2 * nchunk;
   const size_t warp0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ Modex
         for (int j = 1; j < S2; ++j) addc_cc(tx[j], ax[j]);
         const uint32_t c = carry_out();
         normalize<S2, T>(tx, c, 0u, nx, k, kFull);
-        window_exp<S2, T>(tx, nx, npx, H.R1x, P.dig1[h], P.ndig1[h], w, mytbl, bs, st, k);
+        window_exp<S2, T>(tx, nx, npx, P.op1[h], P.nop1[h], w, mytbl, bs, st, k);
         // leave Montgomery form mod x
         __syncwarp();
 #pragma unroll
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ Modex
     }
 
     // exponentiation mod x^2: exponent x (ENC) or x - 1 (DEC)
-    window_exp<S, T>(t, n, np, H.R1, P.dig[h], P.ndig[h], w, mytbl, bs, st, k);
+    window_exp<S, T>(t, n, np, P.op[h], P.nop[h], w, mytbl, bs, st, k);
 #pragma unroll
     for (int j = 0; j < S; ++j) a[j] = t[j];
 
@@ -417,7 +418,7 @@ static pl_status modexp_phase(pl_key* key, const ModexpCfg& cfg, const uint32_t*
   const size_t ipb = kBlock / cfg.T;
   Carve cv;
   const size_t off_y = cv.take((size_t)2 * count * L * sizeof(uint32_t));
-  const size_t off_t = cv.take((size_t)grid * ipb * ((size_t)1 << cfg.w) * L * sizeof(uint32_t));
+  const size_t off_t = cv.take((size_t)grid * ipb * table_entries(cfg.w) * L * sizeof(uint32_t));
   Scratch* sc = scratch ? scratch : key->scratch_for_current_device();
   if (!sc) return fail(PL_ECUDA, "no current device");
   char* base = static_cast<char*>(sc->get(cv.off, s));
@@ -457,7 +458,7 @@ size_t decrypt_scratch_bytes(const pl_key* key, size_t count) {
   const size_t ipb = kBlock / cfg.T;
   Carve cv;
   cv.take((size_t)2 * count * L * sizeof(uint32_t));
-  cv.take((size_t)grid * ipb * ((size_t)1 << cfg.w) * L * sizeof(uint32_t));
+  cv.take((size_t)grid * ipb * table_entries(cfg.w) * L * sizeof(uint32_t));
   return cv.off;
 }
 
@@ -496,9 +497,9 @@ namespace pl {
 namespace {
 
 constexpr size_t kNaMaxCount = 8192;  // ciphertexts per call
-constexpr int kNaWindow = 4;          // window bits: 16 table entries per instance
+constexpr int kNaWindow = 4;          // window bits
 constexpr size_t kNaYWords = 2 * kNaMaxCount * kMaxL;                       // y[2][count][L]
-constexpr size_t kNaTblWords = (size_t)148 * 32 * (1u << kNaWindow) * kMaxL;  // 4736 slots at L = 96
+constexpr size_t kNaTblWords = (size_t)148 * 32 * 16 * kMaxL;  // 16 table entries for 4736 instances at L = 96
 constexpr int kNaMaxDevices = 64;
 
 static __device__ __align__(256) uint32_t g_na_scratch[kNaYWords + kNaTblWords];
@@ -551,19 +552,13 @@ extern "C" pl_status paillier_decrypt_u64_noalloc(const pl_key* key, const uint3
   if (rc) return rc;
   const int L = key->L;
   const int T = key->dec_cfg.T;
-  // exponent digits of p - 1 and q - 1 at the fixed window, built on the stack
+  // schedules of p - 1 and q - 1 at the fixed window, built on the stack
   ModexpParams P;
   std::memset(&P, 0, sizeof(P));
   for (int h = 0; h < 2; ++h) {
     P.half[h] = key->half[h];
-    const plh::Big& e = key->e_dec[h];
-    const int nd = (e.bits() + kNaWindow - 1) / kNaWindow;
-    for (int i = 0; i < nd; ++i) {
-      int d = 0;
-      for (int b = 0; b < kNaWindow; ++b) d |= (int)e.bit(i * kNaWindow + b) << b;
-      P.dig[h][i] = (uint8_t)d;
-    }
-    P.ndig[h] = nd;
+    P.nop[h] = sliding_schedule(key->e_dec[h], kNaWindow, P.op[h], kMaxOps);
+    if (P.nop[h] < 0) return fail(PL_EINVAL, "exponent too long");
   }
   P.w = kNaWindow;
   int grid = 0;
@@ -571,7 +566,7 @@ extern "C" pl_status paillier_decrypt_u64_noalloc(const pl_key* key, const uint3
   if (rc) return rc;
   // the table slots the array holds for this key size bound the grid
   const size_t ipb = kBlock / T;
-  const size_t slots = kNaTblWords / (((size_t)1 << kNaWindow) * L);
+  const size_t slots = kNaTblWords / (table_entries(kNaWindow) * L);
   const size_t ipw = 32 / (size_t)T;
   const size_t warps_needed = 2 * ((count + ipw - 1) / ipw);
   const size_t blocks_needed = (warps_needed + (kBlock / 32) - 1) / (kBlock / 32);

@@ -114,10 +114,11 @@ void fill_private(pl_key* k) {
     k->dec.Lh = Lh;
   }
   // default launch configuration by key size, from measurements on B300 (148
-  // SMs): lanes 2 / 4 / 8 for 1024 / 2048 / 3072 bits, 5-bit windows (6-bit
-  // windows double the window tables, which then miss L2 more at full size)
+  // SMs): lanes 2 / 4 / 8 for 1024 / 2048 / 3072 bits; sliding windows of 6 bits
+  // from 2048 bits up (32 odd powers per instance; +0.4 % / +1.1 % over 5 bits
+  // at 2048 / 3072 bits, full-size launches), 5 bits for 1024
   const int T_half = (L == 32) ? 2 : (L == 64 ? 4 : 8);
-  const int w = 5;
+  const int w = (L == 32) ? 5 : 6;
   k->enc_cfg = {T_half, w};
   k->dec_cfg = {T_half, w};
   k->agg_cfg = default_agg(L);
@@ -161,23 +162,13 @@ const pl::ModexpParams* pl_key::modexp_params(bool dec, int w) {
   if (it != cache.end()) return it->second.get();
   auto P = std::make_unique<pl::ModexpParams>();
   std::memset(P.get(), 0, sizeof(pl::ModexpParams));
-  auto digits = [&](const Big& e, uint8_t* dst, int maxd) {
-    const int nd = (e.bits() + w - 1) / w;
-    if (nd > maxd || nd < 1) return -1;
-    for (int i = 0; i < nd; ++i) {
-      int d = 0;
-      for (int b = 0; b < w; ++b) d |= (int)e.bit(i * w + b) << b;
-      dst[i] = (uint8_t)d;
-    }
-    return nd;
-  };
   for (int h = 0; h < 2; ++h) {
     P->half[h] = half[h];
-    P->ndig[h] = digits(dec ? e_dec[h] : e_enc2[h], P->dig[h], pl::kMaxDigits);
-    if (P->ndig[h] < 0) return nullptr;
+    P->nop[h] = pl::sliding_schedule(dec ? e_dec[h] : e_enc2[h], w, P->op[h], pl::kMaxOps);
+    if (P->nop[h] < 0) return nullptr;
     if (!dec) {
-      P->ndig1[h] = digits(e_enc1[h], P->dig1[h], pl::kMaxDigitsH);
-      if (P->ndig1[h] < 0) return nullptr;
+      P->nop1[h] = pl::sliding_schedule(e_enc1[h], w, P->op1[h], pl::kMaxOps);
+      if (P->nop1[h] < 0) return nullptr;
     }
   }
   P->w = w;
@@ -185,6 +176,39 @@ const pl::ModexpParams* pl_key::modexp_params(bool dec, int w) {
   cache[w] = std::move(P);
   return raw;
 }
+
+namespace pl {
+
+int sliding_schedule(const plh::Big& e, int w, uint8_t* op, int maxops) {
+  int i = e.bits() - 1;  // the top bit is set
+  if (i < 0 || w < 1 || w > 8) return -1;
+  int n = 0;
+  while (i >= 0) {
+    if (!e.bit(i)) {  // a zero outside a window: one squaring
+      if (n >= maxops) return -1;
+      op[n++] = 0;
+      --i;
+      continue;
+    }
+    // the window: bits i .. j, at most w of them, ending in a set bit
+    int j = i - w + 1 > 0 ? i - w + 1 : 0;
+    while (!e.bit(j)) ++j;
+    int v = 0;
+    for (int b = i; b >= j; --b) v = (v << 1) | (int)e.bit(b);
+    const int len = i - j + 1;
+    if (n == 0) {
+      op[n++] = (uint8_t)v;  // start from base^v
+    } else {
+      if (n + len + 1 > maxops) return -1;
+      for (int s = 0; s < len; ++s) op[n++] = 0;
+      op[n++] = (uint8_t)v;
+    }
+    i = j - 1;
+  }
+  return n;
+}
+
+}  // namespace pl
 
 pl::Scratch* pl_key::scratch_for_current_device(bool aux) {
   int dev = 0;

@@ -9,8 +9,10 @@ namespace pl {
 
 constexpr int kMaxL = 96;                 // limbs of n for the largest key (3072-bit)
 constexpr int kMaxLh = kMaxL / 2;         // limbs of p, q
-constexpr int kMaxDigits = 3072 / 2 + 1;  // exponent windows at the smallest window (w = 2)
-constexpr int kMaxDigitsH = 1536 / 2 + 1; // the same for exponents of at most 1536 bits
+// Sliding-window schedules (see ModexpParams): at most one squaring per
+// exponent bit and one product per set bit, for exponents of at most 1536 bits
+// (the primes of a 3072-bit key).
+constexpr int kMaxOps = 2 * 1536 + 2;
 
 // Device status word bits (OR-ed by kernels, read by paillier_sync)
 constexpr int kStatusBadBin = 1;       // bin >= K
@@ -38,18 +40,23 @@ struct HalfConst {
   uint32_t pad[2];
 };
 
-// Batched fixed-window modular exponentiation over both halves.
-//   decryption: c^(x-1) mod x^2, exponent digits in dig;
+// Batched left-to-right sliding-window exponentiation over both halves.
+//   decryption: c^(x-1) mod x^2, schedule in op;
 //   encryption: r^n mod x^2 = ((r mod x)^(x' mod (x-1)) mod x)^x mod x^2, where x'
 //   is the other prime (y^x mod x^2 depends only on y mod x):
-//   digits of x' mod (x-1) in dig1 (mod x), digits of x in dig (mod x^2).
+//   schedule of x' mod (x-1) in op1 (mod x), of x in op (mod x^2).
+// A schedule for exponent e and window w: op[0] is the odd value v of the
+// leading window (start from base^v); then, most significant bits first, 0 =
+// square, odd v = multiply by base^v (v < 2^w).  The table holds the odd powers
+// base^1, base^3, .., base^(2^w - 1).  The exponents are the key's, so every
+// instance of a launch runs the same schedule.
 struct ModexpParams {
   HalfConst half[2];
-  uint8_t dig[2][kMaxDigits];    // window digits, least significant first
-  int ndig[2];
-  uint8_t dig1[2][kMaxDigitsH];  // encryption, first exponentiation (mod x)
-  int ndig1[2];
-  int w;                         // window width in bits
+  uint8_t op[2][kMaxOps];
+  int nop[2];
+  uint8_t op1[2][kMaxOps];   // encryption, first exponentiation (mod x)
+  int nop1[2];
+  int w;                     // window width in bits
   int pad;
 };
 

@@ -20,7 +20,7 @@ std::vector<Cand> candidates(const pl_key* key, int op) {
   if (op == PL_OP_ENCRYPT || op == PL_OP_DECRYPT) {
     for (int T : {2, 4, 8})
       if (pl::modexp_supported(key->L, T))
-        for (int w : {4, 5, 6}) c.push_back({T, w});
+        for (int w : {4, 5, 6, 7}) c.push_back({T, w});
   } else {
     for (int T : {4, 8, 16})
       if (pl::agg_supported(2 * key->L, T))
