@@ -43,7 +43,7 @@ METRIC = "2048-bit Paillier enc/s & encrypted-hist ct-mults/s; p50/p99 request m
 
 # DRAM bytes (read + write) per encryption of the current k_modexp ENC kernel, from the ncu
 # capture summarised in profiles/k_modexp_enc_2048bit_small.md, keyed by (n_bits, window)
-TRAFFIC_PER_ENC = {}
+TRAFFIC_PER_ENC = {(2048, 6): 329.54e6 / 16384 + 330.36e6 / 16384}
 
 
 # ----------------------------------------------------------------------------
@@ -815,7 +815,8 @@ def run_ours(args, cfg):
             # DRAM bytes per encryption of this kernel version from the ncu capture summarised in
             # profiles/k_modexp_enc_2048bit_small.md (16,384 encryptions, w = 5), scaled to this launch
             "traffic": units * TRAFFIC_PER_ENC.get((n_bits, w)) if (n_bits, w) in TRAFFIC_PER_ENC else None,
-            "traffic_note": "ncu dram__bytes_read+write of a 16,384-encryption capture, scaled by encryptions",
+            "traffic_note": "ncu dram__bytes_read+write of a 16,384-encryption capture of this kernel version "
+                            "(profiles/k_modexp_enc_2048bit_small.md), scaled by encryptions",
             "peak_source": "project microbenchmark paillier_imad_peak, best mix, same run",
             "peak_derived_TIMAD_s": sm_count_of(dev) * 64 * 2.032e9 / 1e12,
             "peak_derived_note": "SMs x 64 32-bit IMAD/clk/SM x 2032 MHz max clock",
