@@ -570,6 +570,11 @@ def run_horizontal(args, cfg):
     fft_flop = ckks_fft_flop(N)
     enc_imad = ckks_encrypt_imad(N)
 
+    def ctas(polys):
+        """CTAs of a launch over `polys` polynomials: a cluster of 8 per polynomial
+        up to 64 polynomials (N >= 1024), else one each."""
+        return polys * 8 if cfg["log_n"] >= 10 and polys <= 64 else polys
+
     def roof(phases, b):
         """Dominant phase and its achieved rate against the measured peak."""
         i = int(np.argmax(phases))
@@ -585,7 +590,7 @@ def run_horizontal(args, cfg):
         ach = work / (phases[i] * 1e-3)
         return {"bound": "alu", "kernel": kern, "achieved": ach / 1e12, "peak": peak / 1e12, "unit": unit,
                 "frac": ach / peak, "traffic": None, "work_per_launch": work, "launch_ms": phases[i],
-                "ctas": b if names[i] in ("encode", "encrypt") else b // clients, "sms": sm_count_of(dev),
+                "ctas": ctas(b if names[i] in ("encode", "encrypt") else b // clients), "sms": sm_count_of(dev),
                 "peak_source": "project microbenchmark in the same run (paillier_fp64_peak / paillier_imad_peak "
                                "mad.wide)"}
 

@@ -1,6 +1,7 @@
 // CKKS for the secure horizontal pattern: negacyclic NTT over one 62-bit prime,
 // canonical-embedding encoding/decoding, public-key encryption, addition and
 // decryption (see include/ckks.h).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -104,8 +105,10 @@ __device__ __forceinline__ void gs_last(u64& x, u64& y, const NttConst& C) {
   x = mmul(s, C.ninv, C.q, C.qn);
 }
 
-__device__ void ntt_fwd(u64* a, const u64* tw, const NttConst& C) {
-  const int L = C.log_n, N = 1 << L;
+// L: log2 of the transformed length (C.log_n for a whole polynomial; less for
+// the slice of one CTA of a cluster, see below).
+__device__ void ntt_fwd(u64* a, const u64* tw, const NttConst& C, int L) {
+  const int N = 1 << L;
   int lt = L - 1;  // log2 of the butterfly distance of the next stage
   for (; lt >= 2; lt -= 3) {
     // distances t, t/2, t/4 on e_k = 2t i + j + k t/4 (k < 8, j < t/4)
@@ -145,8 +148,8 @@ __device__ void ntt_fwd(u64* a, const u64* tw, const NttConst& C) {
 }
 
 // inverse transform of one or two polynomials (b may be NULL)
-__device__ void ntt_inv(u64* a, u64* b, const u64* itw, const NttConst& C) {
-  const int L = C.log_n, N = 1 << L;
+__device__ void ntt_inv(u64* a, u64* b, const u64* itw, const NttConst& C, int L) {
+  const int N = 1 << L;
   int lt = 0;
   for (; lt < L % 3; ++lt) {  // leading radix-2 stages (never the last one: L >= 4)
     const int h = N >> (lt + 1);
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(kThreads)
   stage_table(t, tw, N);
   for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = to_q(src[i], C.q);
   __syncthreads();
-  ntt_fwd(sm, t, C);
+  ntt_fwd(sm, t, C, C.log_n);
   u64* p = dst + (size_t)blockIdx.x * N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) p[i] = mont ? mmul(sm[i], C.r2, C.q, C.qn) : sm[i];
 }
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(kThreads)
   stage_table(t, tw, N);
   for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = smod(v[p * N + i], C.q);
   __syncthreads();
-  ntt_fwd(x, t, C);
+  ntt_fwd(x, t, C, C.log_n);
   stage_table(t, itw, N);
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const u64 xv = x[i];
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(kThreads)
     y[i] = mmul(xv, pk[N + i], C.q, C.qn);
   }
   __syncthreads();
-  ntt_inv(x, y, t, C);
+  ntt_inv(x, y, t, C, C.log_n);
   u64* c0 = c + p * 2 * N;
   u64* c1 = c0 + N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -272,12 +275,12 @@ __global__ void __launch_bounds__(kThreads)
   stage_table(t, tw, N);
   for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = c0[N + i];
   __syncthreads();
-  ntt_fwd(sm, t, C);
+  ntt_fwd(sm, t, C, C.log_n);
   stage_table(t, itw, N);
   for (int i = threadIdx.x; i < N; i += blockDim.x)
     sm[i] = mmul(sm[i], shat[i], C.q, C.qn);
   __syncthreads();
-  ntt_inv(sm, nullptr, t, C);
+  ntt_inv(sm, nullptr, t, C, C.log_n);
   for (int i = threadIdx.x; i < N; i += blockDim.x) m[p * N + i] = addm(c0[i], sm[i], C.q);
 }
 
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(kThreads)
   for (int i = threadIdx.x; i < N; i += blockDim.x)
     sm[i] = mmul(ahat[i], shat[i], C.q, C.qn);
   __syncthreads();
-  ntt_inv(sm, nullptr, t, C);
+  ntt_inv(sm, nullptr, t, C, C.log_n);
   for (int i = threadIdx.x; i < N; i += blockDim.x) b[i] = addm(subm(0, sm[i], C.q), smod(e[i], C.q), C.q);
 }
 
@@ -393,6 +396,262 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// ---- one polynomial per cluster of kCl CTAs (distributed shared memory) ----
+// For a small batch, one CTA per polynomial leaves most SMs idle.  The cluster
+// kernels split each polynomial over kCl CTAs.  With M = (length) / kCl:
+//   cyclic layout: CTA r holds global indices r + kCl u (u < M);
+//   block layout:  CTA r holds global indices r M + v (v < M).
+// Forward NTT (distances t = N/2 .. 1): the stages with t >= kCl pair indices of
+// one residue class mod kCl, and on the cyclic slice they are exactly the stages
+// of a length-M transform with the same twiddle entries tw[m + i], m < M; the
+// last log2 kCl stages (t < kCl <= M) are local in the block layout.  One
+// exchange through distributed shared memory (cyclic -> block) sits between
+// them.  The inverse runs the mirror image (block stages t = 1 .. kCl/2, block
+// -> cyclic, then a length-M inverse on the cyclic slice, N^-1 folded into its
+// last stage as for a whole polynomial).  The canonical-embedding FFT (decimation
+// in time on a bit-reversed load) does its small distances in the block layout
+// and its large ones in the cyclic layout.  Every cluster barrier is a hardware
+// barrier (no polling).
+namespace cg = cooperative_groups;
+
+constexpr int kCl = 8, kClLog = 3;
+constexpr int kClNttThreads = 128, kClFftThreads = 256;
+
+// forward stages t = kCl/2 .. 1 on the block slice of CTA r (twiddles from global)
+__device__ void ntt_fwd_tail(u64* a, const u64* __restrict__ tw, const NttConst& C, int r, int logM) {
+  const int M = 1 << logM, N = 1 << C.log_n;
+  for (int lt = kClLog - 1; lt >= 0; --lt) {
+    const int m = N >> (lt + 1), base = (r << logM) >> (lt + 1);  // global block of local block 0: r M / 2t
+    for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
+      const int i = b >> lt, idx = (i << (lt + 1)) + (b & ((1 << lt) - 1));
+      u64 x = a[idx], y = a[idx + (1 << lt)];
+      ct_bfly(x, y, tw[m + base + i], C);
+      a[idx] = x;
+      a[idx + (1 << lt)] = y;
+    }
+    __syncthreads();
+  }
+}
+
+// inverse stages t = 1 .. kCl/2 on the block slice (one or two polynomials)
+__device__ void ntt_inv_head(u64* a, u64* b, const u64* __restrict__ itw, const NttConst& C, int r, int logM) {
+  const int M = 1 << logM, N = 1 << C.log_n;
+  for (int lt = 0; lt < kClLog; ++lt) {
+    const int h = N >> (lt + 1), base = (r << logM) >> (lt + 1);
+    for (int k = threadIdx.x; k < M / 2; k += blockDim.x) {
+      const int i = k >> lt, idx = (i << (lt + 1)) + (k & ((1 << lt) - 1));
+      const u64 w = itw[h + base + i];
+      for (u64* p = a; p; p = (p == a ? b : nullptr)) {
+        u64 x = p[idx], y = p[idx + (1 << lt)];
+        gs_bfly(x, y, w, C);
+        p[idx] = x;
+        p[idx + (1 << lt)] = y;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// block slice of CTA r <- the cluster's cyclic slices (global index r M + v
+// lives in CTA (r M + v) mod kCl at (r M + v) / kCl)
+template <typename E>
+__device__ void gather_block(cg::cluster_group& cl, E* dst, E* cyc, int r, int logM) {
+  for (int v = threadIdx.x; v < (1 << logM); v += blockDim.x) {
+    const int idx = (r << logM) + v;
+    dst[v] = cl.map_shared_rank(cyc, idx & (kCl - 1))[idx >> kClLog];
+  }
+}
+
+// cyclic slice of CTA r <- the cluster's block slices (global index r + kCl u
+// lives in CTA (r + kCl u) / M at (r + kCl u) mod M)
+template <typename E>
+__device__ void gather_cyclic(cg::cluster_group& cl, E* dst, E* blk, int r, int logM) {
+  for (int u = threadIdx.x; u < (1 << logM); u += blockDim.x) {
+    const int idx = r + (u << kClLog);
+    dst[u] = cl.map_shared_rank(blk, idx >> logM)[idx & ((1 << logM) - 1)];
+  }
+}
+
+// smem: x0, x1 (cyclic), y0, y1 (block), twiddles: M words each
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
+    k_encrypt_cl(const u64* __restrict__ pk, const int64_t* __restrict__ m, const int8_t* __restrict__ v,
+                 const int32_t* __restrict__ e0, const int32_t* __restrict__ e1, const u64* __restrict__ tw,
+                 const u64* __restrict__ itw, NttConst C, u64* __restrict__ c) {
+  extern __shared__ u64 sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank();
+  const size_t p = blockIdx.x / kCl;
+  const int N = 1 << C.log_n, logM = C.log_n - kClLog, M = 1 << logM;
+  u64 *x0 = sm, *x1 = sm + M, *y0 = sm + 2 * M, *y1 = sm + 3 * M, *t = sm + 4 * M;
+  stage_table(t, tw, M);
+  for (int u = threadIdx.x; u < M; u += blockDim.x) x0[u] = smod(v[p * N + r + (u << kClLog)], C.q);
+  __syncthreads();
+  ntt_fwd(x0, t, C, logM);  // stages t >= kCl
+  cl.sync();
+  gather_block(cl, y0, x0, r, logM);
+  __syncthreads();
+  ntt_fwd_tail(y0, tw, C, r, logM);  // stages t < kCl
+  stage_table(t, itw, M);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const u64 xv = y0[i];
+    const int g = (r << logM) + i;
+    y0[i] = mmul(xv, pk[g], C.q, C.qn);
+    y1[i] = mmul(xv, pk[N + g], C.q, C.qn);
+  }
+  __syncthreads();
+  ntt_inv_head(y0, y1, itw, C, r, logM);
+  cl.sync();  // every block slice done; every read of the cyclic slices done
+  gather_cyclic(cl, x0, y0, r, logM);
+  gather_cyclic(cl, x1, y1, r, logM);
+  cl.sync();  // no CTA reads another's block slice after this
+  ntt_inv(x0, x1, t, C, logM);
+  u64* c0 = c + p * 2 * N;
+  u64* c1 = c0 + N;
+  for (int u = threadIdx.x; u < M; u += blockDim.x) {
+    const size_t g = (size_t)r + ((size_t)u << kClLog);
+    c0[g] = addm(addm(x0[u], smod(e0[p * N + g], C.q), C.q), smod(m[p * N + g], C.q), C.q);
+    c1[g] = addm(x1[u], smod(e1[p * N + g], C.q), C.q);
+  }
+}
+
+// smem: x (cyclic), y (block), twiddles: M words each
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
+    k_decrypt_cl(const u64* __restrict__ c, const u64* __restrict__ shat, const u64* __restrict__ tw,
+                 const u64* __restrict__ itw, NttConst C, u64* __restrict__ m) {
+  extern __shared__ u64 sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank();
+  const size_t p = blockIdx.x / kCl;
+  const int N = 1 << C.log_n, logM = C.log_n - kClLog, M = 1 << logM;
+  u64 *x = sm, *y = sm + M, *t = sm + 2 * M;
+  const u64* c0 = c + p * 2 * N;
+  stage_table(t, tw, M);
+  for (int u = threadIdx.x; u < M; u += blockDim.x) x[u] = c0[N + r + (u << kClLog)];
+  __syncthreads();
+  ntt_fwd(x, t, C, logM);
+  cl.sync();
+  gather_block(cl, y, x, r, logM);
+  __syncthreads();
+  ntt_fwd_tail(y, tw, C, r, logM);
+  stage_table(t, itw, M);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) y[i] = mmul(y[i], shat[(r << logM) + i], C.q, C.qn);
+  __syncthreads();
+  ntt_inv_head(y, nullptr, itw, C, r, logM);
+  cl.sync();
+  gather_cyclic(cl, x, y, r, logM);
+  cl.sync();
+  ntt_inv(x, nullptr, t, C, logM);
+  for (int u = threadIdx.x; u < M; u += blockDim.x) {
+    const size_t g = (size_t)r + ((size_t)u << kClLog);
+    m[p * N + g] = addm(c0[g], x[u], C.q);
+  }
+}
+
+// FFT stages in the block layout: lg = 1 .. logM (half size h = 2^(lg-1) < M);
+// w[j] = W^j of the length-n transform (log_n2 = log2 n)
+__device__ void fft_block_stages(double2* a, const double2* w, int logM, int log_n2, double sign) {
+  const int M = 1 << logM;
+  for (int lg = 1; lg <= logM; ++lg) {
+    const int half = 1 << (lg - 1);
+    for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
+      const int g = b >> (lg - 1), j = b & (half - 1);
+      const int i0 = (g << lg) + j;
+      const double2 t = w[j << (log_n2 - lg)];
+      const double wr = t.x, wi = sign * t.y;
+      const double2 u = a[i0], x = a[i0 + half];
+      const double vr = x.x * wr - x.y * wi, vi = x.x * wi + x.y * wr;
+      a[i0] = make_double2(u.x + vr, u.y + vi);
+      a[i0 + half] = make_double2(u.x - vr, u.y - vi);
+    }
+    __syncthreads();
+  }
+}
+
+// FFT stages in the cyclic layout of CTA r: lg = logM + 1 .. log_n2 (global half
+// size h >= M, local half size h / kCl; the pair's global offset in its group
+// is r + kCl j')
+__device__ void fft_cyclic_stages(double2* a, const double2* w, int r, int logM, int log_n2, double sign) {
+  const int M = 1 << logM;
+  for (int lg = logM + 1; lg <= log_n2; ++lg) {
+    const int lh = lg - 1 - kClLog;  // log2 of the local half size
+    for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
+      const int g = b >> lh, jl = b & ((1 << lh) - 1);
+      const int i0 = (g << (lh + 1)) + jl;
+      const double2 t = w[(r + (jl << kClLog)) << (log_n2 - lg)];
+      const double wr = t.x, wi = sign * t.y;
+      const double2 u = a[i0], x = a[i0 + (1 << lh)];
+      const double vr = x.x * wr - x.y * wi, vi = x.x * wi + x.y * wr;
+      a[i0] = make_double2(u.x + vr, u.y + vi);
+      a[i0 + (1 << lh)] = make_double2(u.x - vr, u.y - vi);
+    }
+    __syncthreads();
+  }
+}
+
+// smem: block [M] + cyclic [M] + twiddles [n/2] double2 (n = N/2, M = n / kCl)
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClFftThreads)
+    k_encode_cl(const double* __restrict__ re, const double* __restrict__ im, int log_n,
+                const int32_t* __restrict__ invpos, const double2* __restrict__ fftw,
+                const double2* __restrict__ twist, double scale, int64_t* __restrict__ m) {
+  extern __shared__ double2 z[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank();
+  const size_t p = blockIdx.x / kCl;
+  const int log_m = log_n - 1, n = 1 << log_m, N = 2 * n, logM = log_m - kClLog, M = 1 << logM;
+  double2 *blk = z, *cyc = z + M, *w = z + 2 * M;
+  for (int j = threadIdx.x; j < n / 2; j += blockDim.x) w[j] = fftw[j];
+  for (int v = threadIdx.x; v < M; v += blockDim.x) {  // bit-reversed load: Y[t] = z_j at t = pos_j
+    const int j = invpos[brev((r << logM) + v, log_m)];
+    blk[v] = make_double2(re[p * n + j], im[p * n + j]);
+  }
+  __syncthreads();
+  fft_block_stages(blk, w, logM, log_m, -1.0);
+  cl.sync();
+  gather_cyclic(cl, cyc, blk, r, logM);
+  cl.sync();
+  fft_cyclic_stages(cyc, w, r, logM, log_m, -1.0);
+  const double f = scale / n;
+  for (int u = threadIdx.x; u < M; u += blockDim.x) {
+    const int k = r + (u << kClLog);
+    const double2 t = twist[k], v = cyc[u];
+    m[p * N + k] = (int64_t)rint((v.x * t.x + v.y * t.y) * f);
+    m[p * N + k + n] = (int64_t)rint((v.y * t.x - v.x * t.y) * f);
+  }
+}
+
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClFftThreads)
+    k_decode_cl(const u64* __restrict__ mq, int log_n, u64 q, const int32_t* __restrict__ invpos,
+                const double2* __restrict__ fftw, const double2* __restrict__ twist, double scale, double inv,
+                double* __restrict__ re, double* __restrict__ im) {
+  extern __shared__ double2 z[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank();
+  const size_t p = blockIdx.x / kCl;
+  const int log_m = log_n - 1, n = 1 << log_m, N = 2 * n, logM = log_m - kClLog, M = 1 << logM;
+  double2 *blk = z, *cyc = z + M, *w = z + 2 * M;
+  for (int j = threadIdx.x; j < n / 2; j += blockDim.x) w[j] = fftw[j];
+  for (int v = threadIdx.x; v < M; v += blockDim.x) {  // bit-reversed load of the twisted w_k
+    const int k = brev((r << logM) + v, log_m);
+    const u64 a = mq[p * N + k], b = mq[p * N + k + n];
+    const double x = a > q / 2 ? -(double)(q - a) : (double)a;
+    const double y = b > q / 2 ? -(double)(q - b) : (double)b;
+    const double2 t = twist[k];
+    blk[v] = make_double2(x * t.x - y * t.y, x * t.y + y * t.x);
+  }
+  __syncthreads();
+  fft_block_stages(blk, w, logM, log_m, 1.0);
+  cl.sync();
+  gather_cyclic(cl, cyc, blk, r, logM);
+  cl.sync();
+  fft_cyclic_stages(cyc, w, r, logM, log_m, 1.0);
+  for (int u = threadIdx.x; u < M; u += blockDim.x) {
+    const int j = invpos[r + (u << kClLog)];
+    const double2 v = cyc[u];
+    re[p * n + j] = inv != 0.0 ? v.x * inv : v.x / scale;
+    im[p * n + j] = inv != 0.0 ? v.y * inv : v.y / scale;
+  }
+}
+
 int ew_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, (size_t)pl::sm_count() * 8); }
 
 template <typename K>
@@ -410,6 +669,7 @@ struct ckks_ctx {
   u64* d_tw = nullptr;   // forward twiddles psi^bitrev(i), Montgomery form
   u64* d_itw = nullptr;  // inverse twiddles psi^-bitrev(i), Montgomery form
   int32_t* d_pos = nullptr;    // slot j -> (r_j - 1) / 4
+  int32_t* d_invpos = nullptr; // (r_j - 1) / 4 -> slot j
   double2* d_fftw = nullptr;   // W^j = exp(2 pi i j / n), j < n / 2
   double2* d_twist = nullptr;  // omega^k = exp(i pi k / N), k < n
   pl::Scratch scratch;
@@ -422,26 +682,40 @@ struct ckks_ctx {
     cudaFree(d_tw);
     cudaFree(d_itw);
     cudaFree(d_pos);
+    cudaFree(d_invpos);
     cudaFree(d_fftw);
     cudaFree(d_twist);
   }
   int threads() const { return std::min(N / 2, kThreads); }
+  // a small batch spreads each polynomial over a cluster of kCl CTAs; a large
+  // one (or a small N) keeps one polynomial per CTA
+  static constexpr size_t kClusterMaxBatch = 64;
+  bool clustered(size_t batch) const { return log_n >= 10 && batch <= kClusterMaxBatch; }
 
   pl_status launch_encrypt(const u64* pk, const int64_t* d_m, const int8_t* d_v, const int32_t* d_e0,
                            const int32_t* d_e1, size_t batch, u64* d_c, cudaStream_t s) {
-    k_encrypt<<<(unsigned)batch, threads(), 3 * poly_bytes(), s>>>(pk, d_m, d_v, d_e0, d_e1, d_tw, d_itw, C, d_c);
+    if (clustered(batch))
+      k_encrypt_cl<<<(unsigned)(batch * kCl), kClNttThreads, 5 * poly_bytes() / kCl, s>>>(pk, d_m, d_v, d_e0, d_e1,
+                                                                                         d_tw, d_itw, C, d_c);
+    else
+      k_encrypt<<<(unsigned)batch, threads(), 3 * poly_bytes(), s>>>(pk, d_m, d_v, d_e0, d_e1, d_tw, d_itw, C, d_c);
     pl::note_launch();
     PL_CUDA_TRY(cudaGetLastError());
     return PL_OK;
   }
   pl_status launch_decrypt(const u64* d_c, const u64* shat, size_t batch, u64* d_m, cudaStream_t s) {
-    k_decrypt<<<(unsigned)batch, threads(), 2 * poly_bytes(), s>>>(d_c, shat, d_tw, d_itw, C, d_m);
+    if (clustered(batch))
+      k_decrypt_cl<<<(unsigned)(batch * kCl), kClNttThreads, 3 * poly_bytes() / kCl, s>>>(d_c, shat, d_tw, d_itw, C,
+                                                                                         d_m);
+    else
+      k_decrypt<<<(unsigned)batch, threads(), 2 * poly_bytes(), s>>>(d_c, shat, d_tw, d_itw, C, d_m);
     pl::note_launch();
     PL_CUDA_TRY(cudaGetLastError());
     return PL_OK;
   }
   int fft_threads() const { return std::min(N / 4, kThreads); }
   size_t fft_smem() const { return (size_t)(N / 2 + N / 4) * sizeof(double2); }
+  size_t fft_cl_smem() const { return (size_t)(2 * (N / 2 / kCl) + N / 4) * sizeof(double2); }
   size_t poly_bytes() const { return (size_t)N * sizeof(u64); }
 
   // dst [2][N] = NTT(src0), NTT(src1) (src1 may be NULL: one polynomial),
@@ -497,9 +771,10 @@ pl_status ckks_create(int log_n, uint64_t q, double scale, ckks_ctx** out) {
   c->C.last = h_mul(itw[1], ninv, q);
   c->C.log_n = log_n;
   const int n = N / 2;
-  std::vector<int32_t> pos(n);
+  std::vector<int32_t> pos(n), invpos(n);
   u64 x = 1;  // r_j = 5^j mod 2N
   for (int j = 0; j < n; ++j) { pos[j] = (int32_t)((x - 1) / 4); x = x * 5 % (2ull * N); }
+  for (int j = 0; j < n; ++j) invpos[pos[j]] = j;
   std::vector<double2> fftw(n / 2), twist(n);
   for (int j = 0; j < n / 2; ++j) fftw[j] = make_double2(std::cos(M_PI * 4 * j / N), std::sin(M_PI * 4 * j / N));
   for (int k = 0; k < n; ++k) twist[k] = make_double2(std::cos(M_PI * k / N), std::sin(M_PI * k / N));
@@ -512,10 +787,13 @@ pl_status ckks_create(int log_n, uint64_t q, double scale, ckks_ctx** out) {
   up((void**)&c->d_tw, tw.data(), N * sizeof(u64));
   up((void**)&c->d_itw, itw.data(), N * sizeof(u64));
   up((void**)&c->d_pos, pos.data(), pos.size() * sizeof(int32_t));
+  up((void**)&c->d_invpos, invpos.data(), invpos.size() * sizeof(int32_t));
   up((void**)&c->d_fftw, fftw.data(), fftw.size() * sizeof(double2));
   up((void**)&c->d_twist, twist.data(), twist.size() * sizeof(double2));
   for (cudaError_t a : {allow_smem(k_ntt<u64>), allow_smem(k_ntt<int8_t>), allow_smem(k_encrypt),
-                        allow_smem(k_decrypt), allow_smem(k_keygen), allow_smem(k_encode), allow_smem(k_decode)})
+                        allow_smem(k_decrypt), allow_smem(k_keygen), allow_smem(k_encode), allow_smem(k_decode),
+                        allow_smem(k_encrypt_cl), allow_smem(k_decrypt_cl), allow_smem(k_encode_cl),
+                        allow_smem(k_decode_cl)})
     if (e == cudaSuccess) e = a;
   if (e != cudaSuccess) { delete c; return cuda_fail(e, "ckks tables"); }
   c->scratch.device = c->device;
@@ -535,8 +813,12 @@ pl_status ckks_encode(ckks_ctx* ctx, const double* d_re, const double* d_im, siz
   if (!batch) return PL_OK;
   if (!d_re || !d_im || !d_m) return fail(PL_EINVAL, "NULL buffer");
   if (batch > 0x7fffffff) return fail(PL_ERANGE, "batch too large");
-  k_encode<<<(unsigned)batch, ctx->fft_threads(), ctx->fft_smem(), static_cast<cudaStream_t>(stream)>>>(
-      d_re, d_im, ctx->log_n, ctx->d_pos, ctx->d_fftw, ctx->d_twist, ctx->scale, d_m);
+  if (ctx->clustered(batch))
+    k_encode_cl<<<(unsigned)(batch * kCl), kClFftThreads, ctx->fft_cl_smem(), static_cast<cudaStream_t>(stream)>>>(
+        d_re, d_im, ctx->log_n, ctx->d_invpos, ctx->d_fftw, ctx->d_twist, ctx->scale, d_m);
+  else
+    k_encode<<<(unsigned)batch, ctx->fft_threads(), ctx->fft_smem(), static_cast<cudaStream_t>(stream)>>>(
+        d_re, d_im, ctx->log_n, ctx->d_pos, ctx->d_fftw, ctx->d_twist, ctx->scale, d_m);
   note_launch();
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
@@ -549,8 +831,12 @@ pl_status ckks_decode(ckks_ctx* ctx, const uint64_t* d_m, size_t batch, double* 
   if (!batch) return PL_OK;
   if (!d_re || !d_im || !d_m) return fail(PL_EINVAL, "NULL buffer");
   if (batch > 0x7fffffff) return fail(PL_ERANGE, "batch too large");
-  k_decode<<<(unsigned)batch, ctx->fft_threads(), ctx->fft_smem(), static_cast<cudaStream_t>(stream)>>>(
-      d_m, ctx->log_n, ctx->C.q, ctx->d_pos, ctx->d_fftw, ctx->d_twist, ctx->scale, ctx->inv_scale, d_re, d_im);
+  if (ctx->clustered(batch))
+    k_decode_cl<<<(unsigned)(batch * kCl), kClFftThreads, ctx->fft_cl_smem(), static_cast<cudaStream_t>(stream)>>>(
+        d_m, ctx->log_n, ctx->C.q, ctx->d_invpos, ctx->d_fftw, ctx->d_twist, ctx->scale, ctx->inv_scale, d_re, d_im);
+  else
+    k_decode<<<(unsigned)batch, ctx->fft_threads(), ctx->fft_smem(), static_cast<cudaStream_t>(stream)>>>(
+        d_m, ctx->log_n, ctx->C.q, ctx->d_pos, ctx->d_fftw, ctx->d_twist, ctx->scale, ctx->inv_scale, d_re, d_im);
   note_launch();
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;

@@ -136,6 +136,50 @@ def test_prepared_keys_bit_exact(log_n, batch):
     assert _u64(d1[i]) == ock.decrypt((c0o, c1o), s, q)
 
 
+def test_large_batch_path_bit_exact():
+    """A batch above 64 polynomials runs one CTA per polynomial (smaller batches
+    spread each polynomial over a cluster of CTAs): both give the oracle's bits."""
+    log_n, batch = 10, 66
+    N = 1 << log_n
+    q = synth.ckks_prime(log_n)
+    ctx = G.Context(log_n, q, 2.0 ** 40)
+    s, a, e, v, e0, e1 = _inputs(N, q, batch, 61)
+    b = ock.keygen(s, a, e, q)
+    b_d = _dev(np.array(b, dtype=np.uint64), torch.int64)
+    a_d, s_d = _dev(a, torch.int64), _dev(s)
+    m = synth.rng_misc(62).integers(-(2 ** 40), 2 ** 40, size=(batch, N), dtype=np.int64)
+    args = (_dev(m), _dev(v), _dev(e0), _dev(e1))
+    c_all = ctx.encrypt(b_d, a_d, *args)  # one CTA per polynomial
+    c_few = ctx.encrypt(b_d, a_d, *(t[:3] for t in args))  # clusters
+    assert torch.equal(c_all[:3], c_few)
+    d_all = ctx.decrypt(c_all, s_d)
+    assert torch.equal(d_all[:3], ctx.decrypt(c_few, s_d))
+    for i in (0, batch - 1):
+        c0, c1 = ock.encrypt(b, a, m[i], v[i], e0[i], e1[i], q)
+        assert _u64(c_all[i, 0]) == c0 and _u64(c_all[i, 1]) == c1
+        assert _u64(d_all[i]) == ock.decrypt((c0, c1), s, q)
+    # the embedding: both paths agree to the last bit on the same inputs? (not
+    # required: different stage orders) -- each within its bound of the oracle
+    rng = synth.rng_misc(63)
+    re, im = rng.normal(size=(batch, N // 2)) * 1e3, rng.normal(size=(batch, N // 2)) * 1e3
+    m_all = ctx.encode(_dev(re), _dev(im)).cpu().numpy()
+    m_few = ctx.encode(_dev(re[:3].copy()), _dev(im[:3].copy())).cpu().numpy()
+    f = 2.0 * 2.0 ** 40 / N
+    for i in (0, 2, batch - 1):
+        want = ock.encode(re[i] + 1j * im[i], N, 2.0 ** 40)
+        terms = (np.abs(re[i]) + np.abs(im[i])).sum() * f
+        z2 = np.sqrt((re[i] ** 2 + im[i] ** 2).sum())
+        tol = 1 + _gamma(N // 2) * terms + f * np.sqrt(N) * z2 * _fft_rel(N) + U * np.abs(want).max()
+        assert np.abs(m_all[i] - want).max() <= tol
+        if i < 3:
+            assert np.abs(m_few[i] - want).max() <= tol
+    zr_all, zi_all = ctx.decode(d_all)
+    zr_few, zi_few = ctx.decode(d_all[:3].contiguous())
+    for i in (0, 2):
+        assert np.allclose(zr_all[i].cpu().numpy(), zr_few[i].cpu().numpy(), rtol=0, atol=1e-6)
+        assert np.allclose(zi_all[i].cpu().numpy(), zi_few[i].cpu().numpy(), rtol=0, atol=1e-6)
+
+
 @pytest.mark.parametrize("log_n,batch,mag", [(4, 2, 1.0), (10, 3, 1e4), (12, 1, 1e5), (13, 1, 1e4)])
 def test_encode_within_float_bound(log_n, batch, mag):
     N, scale = 1 << log_n, 2.0 ** 40
