@@ -41,6 +41,12 @@ typedef struct ckks_ctx ckks_ctx;
 pl_status ckks_create(int log_n, uint64_t q, double scale, ckks_ctx** out);
 void ckks_free(ckks_ctx* ctx);
 
+/* Launch shape (results are identical either way): a call on at most
+ * max_batch polynomials spreads each polynomial over a cluster of 8 CTAs that
+ * exchange data through distributed shared memory (for N >= 1024); a larger
+ * call keeps one polynomial per CTA.  Default 64; 0 never uses clusters. */
+pl_status ckks_set_cluster_limit(ckks_ctx* ctx, size_t max_batch);
+
 /* Slots per polynomial (N/2). */
 int ckks_slots(const ckks_ctx* ctx);
 

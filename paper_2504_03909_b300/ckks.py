@@ -29,6 +29,11 @@ class Context:
             lib().ckks_free(self._h)
             self._h = C.c_void_p()
 
+    def set_cluster_limit(self, max_batch: int) -> None:
+        """Calls on at most max_batch polynomials split each over a cluster of
+        CTAs (N >= 1024); 0: never.  The results do not depend on it."""
+        call("ckks_set_cluster_limit", self._h, max_batch)
+
     def _batch(self, t: torch.Tensor, width: int) -> int:
         if t.shape[-1] != width:
             raise ValueError(f"last dimension must be {width}")

@@ -417,15 +417,20 @@ namespace cg = cooperative_groups;
 constexpr int kCl = 8, kClLog = 3;
 constexpr int kClNttThreads = 128, kClFftThreads = 256;
 
-// forward stages t = kCl/2 .. 1 on the block slice of CTA r (twiddles from global)
-__device__ void ntt_fwd_tail(u64* a, const u64* __restrict__ tw, const NttConst& C, int r, int logM) {
-  const int M = 1 << logM, N = 1 << C.log_n;
+// offset of the block-stage twiddles of distance 2^lt in a CTA's packed table
+// (t = 4, 2, 1 at 0, M/8, M/8 + M/4)
+__device__ __forceinline__ int tail_off(int lt, int M) { return lt == 2 ? 0 : (lt == 1 ? M / 8 : M / 8 + M / 4); }
+
+// forward stages t = kCl/2 .. 1 on the block slice of CTA r; tw: this CTA's
+// packed block-stage twiddles (global entry N/2t + r M/2t + i at tail_off + i)
+__device__ void ntt_fwd_tail(u64* a, const u64* tw, const NttConst& C, int logM) {
+  const int M = 1 << logM;
   for (int lt = kClLog - 1; lt >= 0; --lt) {
-    const int m = N >> (lt + 1), base = (r << logM) >> (lt + 1);  // global block of local block 0: r M / 2t
+    const u64* w = tw + tail_off(lt, M);
     for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
       const int i = b >> lt, idx = (i << (lt + 1)) + (b & ((1 << lt) - 1));
       u64 x = a[idx], y = a[idx + (1 << lt)];
-      ct_bfly(x, y, tw[m + base + i], C);
+      ct_bfly(x, y, w[i], C);
       a[idx] = x;
       a[idx + (1 << lt)] = y;
     }
@@ -433,14 +438,14 @@ __device__ void ntt_fwd_tail(u64* a, const u64* __restrict__ tw, const NttConst&
   }
 }
 
-// inverse stages t = 1 .. kCl/2 on the block slice (one or two polynomials)
-__device__ void ntt_inv_head(u64* a, u64* b, const u64* __restrict__ itw, const NttConst& C, int r, int logM) {
-  const int M = 1 << logM, N = 1 << C.log_n;
+// inverse stages t = 1 .. kCl/2 on the block slice (one or two polynomials);
+// itw: packed like ntt_fwd_tail's
+__device__ void ntt_inv_head(u64* a, u64* b, const u64* itw, const NttConst& C, int logM) {
+  const int M = 1 << logM;
   for (int lt = 0; lt < kClLog; ++lt) {
-    const int h = N >> (lt + 1), base = (r << logM) >> (lt + 1);
     for (int k = threadIdx.x; k < M / 2; k += blockDim.x) {
       const int i = k >> lt, idx = (i << (lt + 1)) + (k & ((1 << lt) - 1));
-      const u64 w = itw[h + base + i];
+      const u64 w = itw[tail_off(lt, M) + i];
       for (u64* p = a; p; p = (p == a ? b : nullptr)) {
         u64 x = p[idx], y = p[idx + (1 << lt)];
         gs_bfly(x, y, w, C);
@@ -472,7 +477,37 @@ __device__ void gather_cyclic(cg::cluster_group& cl, E* dst, E* blk, int r, int 
   }
 }
 
-// smem: x0, x1 (cyclic), y0, y1 (block), twiddles: M words each
+// Asynchronous global -> shared copies (cp.async; completion is awaited with
+// cp.async.wait_all, a hardware wait on the thread's own copies).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// 16-byte copies of n words (n even, both ends 16-byte aligned)
+__device__ __forceinline__ void cp_async_words(u64* dst, const u64* src, int n) {
+  for (int i = threadIdx.x; i < n / 2; i += blockDim.x) cp_async16(dst + 2 * i, src + 2 * i);
+}
+
+// The twiddles of the block-layout stages of CTA r: for t = 4, 2, 1 the
+// M / 2t consecutive entries tab[N / 2t + r M / 2t ..], packed at offsets
+// 0, M/8, M/8 + M/4 (7M/8 words in all).
+__device__ __forceinline__ void cp_async_tail(u64* dst, const u64* tab, int N, int r, int logM) {
+  const int M = 1 << logM;
+  for (int lt = 0; lt < kClLog; ++lt)
+    cp_async_words(dst + tail_off(lt, M), tab + (N >> (lt + 1)) + ((r << logM) >> (lt + 1)), M >> (lt + 1));
+}
+
+// smem (M words each unless noted): x0, x1 (cyclic), y0, y1 (block), t
+// (length-M twiddles), pk0, pk1 (this CTA's key slices), twf, twi (block-stage
+// twiddles, 7M/8 each), em (epilogue m), ee (epilogue e0 | e1, int32)
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
     k_encrypt_cl(const u64* __restrict__ pk, const int64_t* __restrict__ m, const int8_t* __restrict__ v,
                  const int32_t* __restrict__ e0, const int32_t* __restrict__ e1, const u64* __restrict__ tw,
@@ -483,23 +518,37 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
   const size_t p = blockIdx.x / kCl;
   const int N = 1 << C.log_n, logM = C.log_n - kClLog, M = 1 << logM;
   u64 *x0 = sm, *x1 = sm + M, *y0 = sm + 2 * M, *y1 = sm + 3 * M, *t = sm + 4 * M;
+  u64 *pk0 = sm + 5 * M, *pk1 = sm + 6 * M, *twf = sm + 7 * M, *twi = sm + 8 * M, *em = sm + 9 * M;
+  int32_t* ee = reinterpret_cast<int32_t*>(sm + 10 * M);
+  // everything needed after the first phase, in flight while it runs
+  cp_async_words(pk0, pk + (r << logM), M);
+  cp_async_words(pk1, pk + N + (r << logM), M);
+  cp_async_tail(twf, tw, N, r, logM);
+  cp_async_tail(twi, itw, N, r, logM);
+  for (int u = threadIdx.x; u < M; u += blockDim.x) {
+    const size_t g = p * N + r + ((size_t)u << kClLog);
+    cp_async8(em + u, m + g);
+    cp_async4(ee + u, e0 + g);
+    cp_async4(ee + M + u, e1 + g);
+  }
+  cp_async_commit();
   stage_table(t, tw, M);
   for (int u = threadIdx.x; u < M; u += blockDim.x) x0[u] = smod(v[p * N + r + (u << kClLog)], C.q);
   __syncthreads();
   ntt_fwd(x0, t, C, logM);  // stages t >= kCl
   cl.sync();
   gather_block(cl, y0, x0, r, logM);
+  cp_async_wait();
   __syncthreads();
-  ntt_fwd_tail(y0, tw, C, r, logM);  // stages t < kCl
+  ntt_fwd_tail(y0, twf, C, logM);  // stages t < kCl
   stage_table(t, itw, M);
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     const u64 xv = y0[i];
-    const int g = (r << logM) + i;
-    y0[i] = mmul(xv, pk[g], C.q, C.qn);
-    y1[i] = mmul(xv, pk[N + g], C.q, C.qn);
+    y0[i] = mmul(xv, pk0[i], C.q, C.qn);
+    y1[i] = mmul(xv, pk1[i], C.q, C.qn);
   }
   __syncthreads();
-  ntt_inv_head(y0, y1, itw, C, r, logM);
+  ntt_inv_head(y0, y1, twi, C, logM);
   cl.sync();  // every block slice done; every read of the cyclic slices done
   gather_cyclic(cl, x0, y0, r, logM);
   gather_cyclic(cl, x1, y1, r, logM);
@@ -509,12 +558,13 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
   u64* c1 = c0 + N;
   for (int u = threadIdx.x; u < M; u += blockDim.x) {
     const size_t g = (size_t)r + ((size_t)u << kClLog);
-    c0[g] = addm(addm(x0[u], smod(e0[p * N + g], C.q), C.q), smod(m[p * N + g], C.q), C.q);
-    c1[g] = addm(x1[u], smod(e1[p * N + g], C.q), C.q);
+    c0[g] = addm(addm(x0[u], smod(ee[u], C.q), C.q), smod((long long)em[u], C.q), C.q);
+    c1[g] = addm(x1[u], smod(ee[M + u], C.q), C.q);
   }
 }
 
-// smem: x (cyclic), y (block), twiddles: M words each
+// smem: x (cyclic), y (block), t, sh (this CTA's slice of s^), ec0 (epilogue
+// c0): M words each; twf, twi: 7M/8 each (M reserved)
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
     k_decrypt_cl(const u64* __restrict__ c, const u64* __restrict__ shat, const u64* __restrict__ tw,
                  const u64* __restrict__ itw, NttConst C, u64* __restrict__ m) {
@@ -523,27 +573,34 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
   const int r = (int)cl.block_rank();
   const size_t p = blockIdx.x / kCl;
   const int N = 1 << C.log_n, logM = C.log_n - kClLog, M = 1 << logM;
-  u64 *x = sm, *y = sm + M, *t = sm + 2 * M;
+  u64 *x = sm, *y = sm + M, *t = sm + 2 * M, *sh = sm + 3 * M, *ec0 = sm + 4 * M, *twf = sm + 5 * M,
+      *twi = sm + 6 * M;
   const u64* c0 = c + p * 2 * N;
+  cp_async_words(sh, shat + (r << logM), M);
+  cp_async_tail(twf, tw, N, r, logM);
+  cp_async_tail(twi, itw, N, r, logM);
+  for (int u = threadIdx.x; u < M; u += blockDim.x) cp_async8(ec0 + u, c0 + r + ((size_t)u << kClLog));
+  cp_async_commit();
   stage_table(t, tw, M);
   for (int u = threadIdx.x; u < M; u += blockDim.x) x[u] = c0[N + r + (u << kClLog)];
   __syncthreads();
   ntt_fwd(x, t, C, logM);
   cl.sync();
   gather_block(cl, y, x, r, logM);
+  cp_async_wait();
   __syncthreads();
-  ntt_fwd_tail(y, tw, C, r, logM);
+  ntt_fwd_tail(y, twf, C, logM);
   stage_table(t, itw, M);
-  for (int i = threadIdx.x; i < M; i += blockDim.x) y[i] = mmul(y[i], shat[(r << logM) + i], C.q, C.qn);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) y[i] = mmul(y[i], sh[i], C.q, C.qn);
   __syncthreads();
-  ntt_inv_head(y, nullptr, itw, C, r, logM);
+  ntt_inv_head(y, nullptr, twi, C, logM);
   cl.sync();
   gather_cyclic(cl, x, y, r, logM);
   cl.sync();
   ntt_inv(x, nullptr, t, C, logM);
   for (int u = threadIdx.x; u < M; u += blockDim.x) {
     const size_t g = (size_t)r + ((size_t)u << kClLog);
-    m[p * N + g] = addm(c0[g], x[u], C.q);
+    m[p * N + g] = addm(ec0[u], x[u], C.q);
   }
 }
 
@@ -689,13 +746,13 @@ struct ckks_ctx {
   int threads() const { return std::min(N / 2, kThreads); }
   // a small batch spreads each polynomial over a cluster of kCl CTAs; a large
   // one (or a small N) keeps one polynomial per CTA
-  static constexpr size_t kClusterMaxBatch = 64;
-  bool clustered(size_t batch) const { return log_n >= 10 && batch <= kClusterMaxBatch; }
+  size_t cluster_max_batch = 64;
+  bool clustered(size_t batch) const { return log_n >= 10 && batch <= cluster_max_batch; }
 
   pl_status launch_encrypt(const u64* pk, const int64_t* d_m, const int8_t* d_v, const int32_t* d_e0,
                            const int32_t* d_e1, size_t batch, u64* d_c, cudaStream_t s) {
     if (clustered(batch))
-      k_encrypt_cl<<<(unsigned)(batch * kCl), kClNttThreads, 5 * poly_bytes() / kCl, s>>>(pk, d_m, d_v, d_e0, d_e1,
+      k_encrypt_cl<<<(unsigned)(batch * kCl), kClNttThreads, 11 * poly_bytes() / kCl, s>>>(pk, d_m, d_v, d_e0, d_e1,
                                                                                          d_tw, d_itw, C, d_c);
     else
       k_encrypt<<<(unsigned)batch, threads(), 3 * poly_bytes(), s>>>(pk, d_m, d_v, d_e0, d_e1, d_tw, d_itw, C, d_c);
@@ -705,7 +762,7 @@ struct ckks_ctx {
   }
   pl_status launch_decrypt(const u64* d_c, const u64* shat, size_t batch, u64* d_m, cudaStream_t s) {
     if (clustered(batch))
-      k_decrypt_cl<<<(unsigned)(batch * kCl), kClNttThreads, 3 * poly_bytes() / kCl, s>>>(d_c, shat, d_tw, d_itw, C,
+      k_decrypt_cl<<<(unsigned)(batch * kCl), kClNttThreads, 7 * poly_bytes() / kCl, s>>>(d_c, shat, d_tw, d_itw, C,
                                                                                          d_m);
     else
       k_decrypt<<<(unsigned)batch, threads(), 2 * poly_bytes(), s>>>(d_c, shat, d_tw, d_itw, C, d_m);
@@ -802,6 +859,14 @@ pl_status ckks_create(int log_n, uint64_t q, double scale, ckks_ctx** out) {
 }
 
 void ckks_free(ckks_ctx* ctx) { delete ctx; }
+
+pl_status ckks_set_cluster_limit(ckks_ctx* ctx, size_t max_batch) {
+  using namespace pl;
+  clear_error();
+  if (!ctx) return fail(PL_EINVAL, "ctx is NULL");
+  ctx->cluster_max_batch = max_batch;
+  return PL_OK;
+}
 
 int ckks_slots(const ckks_ctx* ctx) { return ctx ? ctx->N / 2 : 0; }
 

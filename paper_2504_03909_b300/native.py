@@ -91,6 +91,7 @@ SIGNATURES.update({
     "ckks_create": (_i, [_i, C.c_uint64, C.c_double, C.POINTER(C.c_void_p)]),
     "ckks_free": (None, [_vp]),
     "ckks_slots": (_i, [_vp]),
+    "ckks_set_cluster_limit": (_i, [_vp, _sz]),
     "ckks_encode": (_i, [_vp, _vp, _vp, _sz, _vp, _vp]),
     "ckks_decode": (_i, [_vp, _vp, _sz, _vp, _vp, _vp]),
     "ckks_keygen": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),

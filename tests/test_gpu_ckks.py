@@ -154,6 +154,12 @@ def test_large_batch_path_bit_exact():
     assert torch.equal(c_all[:3], c_few)
     d_all = ctx.decrypt(c_all, s_d)
     assert torch.equal(d_all[:3], ctx.decrypt(c_few, s_d))
+    ctx.set_cluster_limit(1 << 20)  # the whole batch in clusters
+    assert torch.equal(ctx.encrypt(b_d, a_d, *args), c_all)
+    assert torch.equal(ctx.decrypt(c_all, s_d), d_all)
+    ctx.set_cluster_limit(0)  # small batches without clusters
+    assert torch.equal(ctx.encrypt(b_d, a_d, *(t[:3] for t in args)), c_few)
+    ctx.set_cluster_limit(64)
     for i in (0, batch - 1):
         c0, c1 = ock.encrypt(b, a, m[i], v[i], e0[i], e1[i], q)
         assert _u64(c_all[i, 0]) == c0 and _u64(c_all[i, 1]) == c1
