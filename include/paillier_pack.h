@@ -26,7 +26,8 @@
 extern "C" {
 #endif
 
-/* Cells per packed ciphertext for a key and a slot width B (1 <= B <= 64). */
+/* Cells per packed ciphertext for a key and a slot width B (1 <= B <= 128;
+ * widths above 64 serve g/h-packed cells, below). */
 int paillier_pack_slots(const pl_key* key, int slot_bits);
 
 /* Packs d_ct [count][2L] (canonical ciphertexts, e.g. histogram cells) into
@@ -36,10 +37,51 @@ pl_status paillier_pack(const pl_key* key, const uint32_t* d_ct, size_t count, i
                         void* stream);
 
 /* Decrypts packed ciphertexts and writes the `count` original plaintexts as
- * uint64: d_m[i] = slot (i mod slots) of packed ciphertext i / slots.
- * Needs the private key; uses the key's scratch like paillier_decrypt. */
+ * uint64: d_m[i] = slot (i mod slots) of packed ciphertext i / slots
+ * (slot_bits <= 64).  Needs the private key; uses the key's scratch like
+ * paillier_decrypt. */
 pl_status paillier_decrypt_packed_u64(const pl_key* key, const uint32_t* d_packed, size_t count, int slot_bits,
                                       uint64_t* d_m, void* stream);
+
+/* ---- g/h packing: one plaintext per sample ----------------------------------
+ * Sec. III.C has one encryption per g and per h (M x 2) because Paillier
+ * encrypts a single number.  A Paillier plaintext has n_bits, so both fit:
+ *     m = enc(g) + 2^B enc(h),   enc(v) = rint(v 2^24) + 2^24 (as paillier_encode)
+ * and a histogram cell's product decrypts to S_g + 2^B S_h, which splits into
+ * the two sums when S_g < 2^B and S_h < 2^B (M samples of at most 2^25 each
+ * need B >= 25 + log2(M)).  One encryption, one product per (sample, feature)
+ * and one decryption per cell then serve g and h: half of each.  26 <= B <= 64
+ * (the paper has no counterpart; a decrypt-count reduction like the above).
+ * Out-of-range inputs follow paillier_encode; enc(g) >= 2^B sets PL_ERANGE in
+ * the device status word.
+ *
+ * d_m [count][2] uint64: m's low and high 64-bit words. */
+pl_status paillier_encode_gh(const float* d_g, const float* d_h, size_t count, int B, uint64_t* d_m, void* stream);
+
+/* As paillier_encrypt, with plaintexts of two 64-bit words (d_m [count][2],
+ * e.g. from paillier_encode_gh) -> d_ct [count][2L]. */
+pl_status paillier_encrypt_gh(const pl_key* key, const uint64_t* d_m, const uint32_t* d_r, size_t count,
+                              uint32_t* d_ct, void* stream);
+
+/* As paillier_hist_aggregate over ONE Montgomery-form ciphertext array
+ * d_ctm [M][2L] (g/h packed): d_hist [num_nodes][F][K][2L], d_count
+ * [num_nodes][F][K] (may be NULL). */
+pl_status paillier_hist_aggregate_gh(const pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t* d_bins,
+                                     int F, int K, const int32_t* d_node, int num_nodes, uint32_t* d_hist,
+                                     int32_t* d_count, void* stream);
+
+/* Decrypts g/h-packed cells d_ct [count][2L] into d_sums [count][2] uint64
+ * (S_g, S_h), the layout paillier_decrypt_u64 gives for separate g and h
+ * cells.  A plaintext with bits at or above 2B sets PL_ERANGE in the device
+ * status word. */
+pl_status paillier_decrypt_gh(const pl_key* key, const uint32_t* d_ct, size_t count, int B, uint64_t* d_sums,
+                              void* stream);
+
+/* The two packings together: cells packed by paillier_pack with slot_bits =
+ * 2B (slots = paillier_pack_slots(key, 2B) cells per ciphertext); d_packed
+ * holds ceil(cells / slots) ciphertexts; d_sums [cells][2] as above. */
+pl_status paillier_decrypt_packed_gh(const pl_key* key, const uint32_t* d_packed, size_t cells, int B,
+                                     uint64_t* d_sums, void* stream);
 
 #ifdef __cplusplus
 }

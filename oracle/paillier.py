@@ -42,7 +42,7 @@ __all__ = [
     "is_probable_prime", "check_key", "PublicKey", "PrivateKey", "keypair",
     "L", "encode", "decode", "encrypt", "decrypt", "decrypt_crt", "add",
     "plain_histogram", "encrypted_histogram_cell", "encrypted_histogram",
-    "mont_product", "plain_histogram_np",
+    "mont_product", "plain_histogram_np", "encode_gh", "split_gh",
 ]
 
 SCALE_BITS = 24
@@ -137,6 +137,20 @@ def encode(v) -> int:
     if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and fl % 2 == 1):
         fl += 1
     return fl + OFFSET
+
+
+def encode_gh(g, h, B: int) -> int:
+    """g/h packing (a decrypt-count reduction; the paper encrypts g and h as two
+    numbers): one plaintext encode(g) + 2^B encode(h)."""
+    eg = encode(g)
+    if eg >= 1 << B:
+        raise ValueError("encode(g) must be below 2^B")
+    return eg + (encode(h) << B)
+
+
+def split_gh(s: int, B: int):
+    """(S_g, S_h) of a decrypted g/h-packed sum S_g + 2^B S_h."""
+    return s & ((1 << B) - 1), s >> B
 
 
 def decode(s: int, count: int) -> Fraction:

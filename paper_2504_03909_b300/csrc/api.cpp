@@ -302,7 +302,7 @@ pl_status paillier_decrypt_u64(const pl_key* key, const uint32_t* d_ct, size_t c
 }
 
 int paillier_pack_slots(const pl_key* key, int slot_bits) {
-  if (!key || slot_bits < 1 || slot_bits > 64) return 0;
+  if (!key || slot_bits < 1 || slot_bits > 128) return 0;
   return (key->n_bits - 2) / slot_bits;
 }
 
@@ -311,7 +311,7 @@ pl_status paillier_pack(const pl_key* key, const uint32_t* d_ct, size_t count, i
   clear_error();
   if (!key) return fail(PL_EINVAL, "key is NULL");
   const int slots = paillier_pack_slots(key, slot_bits);
-  if (slots < 1) return fail(PL_EINVAL, "slot_bits must be 1..64");
+  if (slots < 1) return fail(PL_EINVAL, "slot_bits must be 1..128");
   if (count == 0) return PL_OK;
   if (!d_ct || !d_packed) return fail(PL_EINVAL, "NULL buffer");
   if (!aligned16(d_ct) || !aligned16(d_packed)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
@@ -324,7 +324,7 @@ pl_status paillier_decrypt_packed_u64(const pl_key* key, const uint32_t* d_packe
   clear_error();
   if (!key) return fail(PL_EINVAL, "key is NULL");
   if (!key->priv) return fail(PL_EINVAL, "decryption needs the private key");
-  const int slots = paillier_pack_slots(key, slot_bits);
+  const int slots = slot_bits <= 64 ? paillier_pack_slots(key, slot_bits) : 0;
   if (slots < 1) return fail(PL_EINVAL, "slot_bits must be 1..64");
   if (count == 0) return PL_OK;
   if (!d_packed || !d_m) return fail(PL_EINVAL, "NULL buffer");
@@ -340,6 +340,93 @@ pl_status paillier_decrypt_packed_u64(const pl_key* key, const uint32_t* d_packe
   pl_status rc = launch_decrypt(k, d_packed, npacked, plain, false, st, s);
   if (rc) return rc;
   return launch_unpack(plain, key->L, count, slots, slot_bits, d_m, st, s);
+}
+
+pl_status paillier_encode_gh(const float* d_g, const float* d_h, size_t count, int B, uint64_t* d_m, void* stream) {
+  clear_error();
+  if (B < 26 || B > 64) return fail(PL_EINVAL, "B must be 26..64");
+  if (count == 0) return PL_OK;
+  if (!d_g || !d_h || !d_m) return fail(PL_EINVAL, "NULL buffer");
+  if (count > (size_t)1 << 30) return fail(PL_EINVAL, "count too large");
+  int* st = current_status();
+  if (!st) return fail(PL_ECUDA, "no usable CUDA device");
+  return launch_encode_gh(d_g, d_h, count, B, d_m, st, static_cast<cudaStream_t>(stream));
+}
+
+pl_status paillier_encrypt_gh(const pl_key* key, const uint64_t* d_m, const uint32_t* d_r, size_t count,
+                              uint32_t* d_ct, void* stream) {
+  clear_error();
+  if (!key) return fail(PL_EINVAL, "key is NULL");
+  if (!key->priv) return fail(PL_EINVAL, "encryption here needs the private key (CRT split of r^n)");
+  if (count == 0) return PL_OK;
+  if (!d_m || !d_r || !d_ct) return fail(PL_EINVAL, "NULL buffer");
+  if (!aligned16(d_r) || !aligned16(d_ct)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
+  if (count > (size_t)1 << 30) return fail(PL_EINVAL, "count too large");
+  if (!current_status()) return fail(PL_ECUDA, "no usable CUDA device");
+  return launch_encrypt(const_cast<pl_key*>(key), d_m, d_r, count, d_ct, static_cast<cudaStream_t>(stream), nullptr,
+                        2);
+}
+
+pl_status paillier_hist_aggregate_gh(const pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t* d_bins,
+                                     int F, int K, const int32_t* d_node, int num_nodes, uint32_t* d_hist,
+                                     int32_t* d_count, void* stream) {
+  clear_error();
+  if (!key) return fail(PL_EINVAL, "key is NULL");
+  if (F < 1 || K < 1 || K > 256 || num_nodes < 1) return fail(PL_EINVAL, "need F >= 1, 1 <= K <= 256, num_nodes >= 1");
+  if ((long long)num_nodes * K > (1ll << 20)) return fail(PL_EINVAL, "num_nodes * K must be <= 2^20");
+  if ((long long)F * num_nodes * K > (1ll << 28)) return fail(PL_EINVAL, "F * num_nodes * K too large");
+  if (M > (size_t)1 << 30) return fail(PL_EINVAL, "M too large");
+  if (!d_hist) return fail(PL_EINVAL, "NULL histogram buffer");
+  if (M && (!d_ctm || !d_bins || !d_node)) return fail(PL_EINVAL, "NULL input buffer");
+  if (!aligned16(d_hist) || (d_ctm && !aligned16(d_ctm))) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
+  int* st = current_status();
+  if (!st) return fail(PL_ECUDA, "no usable CUDA device");
+  return launch_hist(const_cast<pl_key*>(key), d_ctm, M, 0, d_bins, M, F, K, d_node, num_nodes, d_hist, d_count,
+                     false, st, static_cast<cudaStream_t>(stream), nullptr, 1);
+}
+
+// decrypt `nct` ciphertexts into the aux scratch, then split each plaintext
+// into `per` cells of 2B bits, each into (low B bits, next B bits)
+static pl_status decrypt_split(const pl_key* key, const uint32_t* d_ct, size_t nct, size_t cells, int per, int B,
+                               uint64_t* d_sums, void* stream) {
+  int* st = current_status();
+  if (!st) return fail(PL_ECUDA, "no usable CUDA device");
+  pl_key* k = const_cast<pl_key*>(key);
+  Scratch* aux = k->scratch_for_current_device(true);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto* plain = static_cast<uint32_t*>(aux ? aux->get(nct * key->L * sizeof(uint32_t), s) : nullptr);
+  if (!plain) return fail(PL_ENOMEM, "scratch allocation failed");
+  pl_status rc = launch_decrypt(k, d_ct, nct, plain, false, st, s);
+  if (rc) return rc;
+  return launch_unpack(plain, key->L, 2 * cells, 2 * per, B, d_sums, st, s);
+}
+
+pl_status paillier_decrypt_gh(const pl_key* key, const uint32_t* d_ct, size_t count, int B, uint64_t* d_sums,
+                              void* stream) {
+  clear_error();
+  if (!key) return fail(PL_EINVAL, "key is NULL");
+  if (!key->priv) return fail(PL_EINVAL, "decryption needs the private key");
+  if (B < 26 || B > 64) return fail(PL_EINVAL, "B must be 26..64");
+  if (count == 0) return PL_OK;
+  if (!d_ct || !d_sums) return fail(PL_EINVAL, "NULL buffer");
+  if (!aligned16(d_ct)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
+  if (count > (size_t)1 << 30) return fail(PL_EINVAL, "count too large");
+  return decrypt_split(key, d_ct, count, count, 1, B, d_sums, stream);
+}
+
+pl_status paillier_decrypt_packed_gh(const pl_key* key, const uint32_t* d_packed, size_t cells, int B,
+                                     uint64_t* d_sums, void* stream) {
+  clear_error();
+  if (!key) return fail(PL_EINVAL, "key is NULL");
+  if (!key->priv) return fail(PL_EINVAL, "decryption needs the private key");
+  if (B < 26 || B > 64) return fail(PL_EINVAL, "B must be 26..64");
+  const int slots = paillier_pack_slots(key, 2 * B);
+  if (slots < 1) return fail(PL_EINVAL, "no slot of 2B bits fits the key");
+  if (cells == 0) return PL_OK;
+  if (!d_packed || !d_sums) return fail(PL_EINVAL, "NULL buffer");
+  if (!aligned16(d_packed)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
+  if (cells > (size_t)1 << 30) return fail(PL_EINVAL, "count too large");
+  return decrypt_split(key, d_packed, (cells + slots - 1) / slots, cells, slots, B, d_sums, stream);
 }
 
 }  // extern "C"

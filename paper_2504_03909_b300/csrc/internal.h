@@ -88,7 +88,7 @@ struct pl_key {
   // launch configuration
   pl::ModexpCfg enc_cfg, dec_cfg;
   pl::AggCfg agg_cfg;
-  // per-window exponent digit tables (built on demand)
+  // per-window exponentiation schedules (built on demand)
   std::map<int, std::unique_ptr<pl::ModexpParams>> enc_params, dec_params;
   std::mutex mu;
   // scratch per device (the second one holds results that outlive a call's
@@ -102,9 +102,11 @@ struct pl_key {
 namespace pl {
 // launchers (kernels translation units)
 pl_status launch_encode(const float* d_v, size_t count, uint64_t* d_m, int* st, cudaStream_t s);
+pl_status launch_encode_gh(const float* d_g, const float* d_h, size_t count, int B, uint64_t* d_m, int* st,
+                           cudaStream_t s);
 pl_status launch_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t count, double* d_out, cudaStream_t s);
 pl_status launch_encrypt(pl_key* key, const uint64_t* d_m, const uint32_t* d_r, size_t count, uint32_t* d_ct,
-                         cudaStream_t s, Scratch* scratch = nullptr);
+                         cudaStream_t s, Scratch* scratch = nullptr, int mw = 1);
 pl_status launch_decrypt(pl_key* key, const uint32_t* d_ct, size_t count, void* d_out, bool u64, int* st,
                          cudaStream_t s, Scratch* scratch = nullptr);
 size_t decrypt_scratch_bytes(const pl_key* key, size_t count);
@@ -116,9 +118,12 @@ int sliding_schedule(const plh::Big& e, int w, uint8_t* op, int maxops);
 // Window-table entries per instance (the odd powers below 2^w).
 __host__ __device__ constexpr size_t table_entries(int w) { return (size_t)1 << (w - 1); }
 pl_status launch_ct_prepare(pl_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_ctm, cudaStream_t s);
+// ngh: ciphertext arrays per sample (2: g and h at stride ghs; 1: one g/h-packed
+// array); d_hist [num_nodes][F][K][ngh][2L]
 pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, size_t ghs, const uint8_t* d_bins,
                       size_t bstride, int F, int K, const int32_t* d_node, int num_nodes, uint32_t* d_hist,
-                      int32_t* d_count, bool per_node, int* st, cudaStream_t s, Scratch* scratch = nullptr);
+                      int32_t* d_count, bool per_node, int* st, cudaStream_t s, Scratch* scratch = nullptr,
+                      int ngh = 2);
 int sm_count();
 pl_status launch_pack(const pl_key* key, const uint32_t* ct, size_t count, int slots, int B, uint32_t* packed,
                       cudaStream_t s);
@@ -145,7 +150,8 @@ HistBufs hist_bufs(const HistLayout& h, void* base);
 pl_status launch_set_desc(HistDesc* D, int num_nodes, int NK, int only_node, cudaStream_t s);
 pl_status hist_enqueue(const pl_key* key, const AggCfg& cfg, const HistBufs& B, int NK_max, const uint32_t* d_ctm,
                        size_t M, size_t ghs, const uint8_t* d_bins, size_t bstride, int F, int K,
-                       const int32_t* d_node, uint32_t* d_hist, int32_t* d_count, int* st, cudaStream_t s);
+                       const int32_t* d_node, uint32_t* d_hist, int32_t* d_count, int* st, cudaStream_t s,
+                       int ngh = 2);
 
 // ---- tracing: launch counter and optional per-kernel CUDA-event timing ----
 void note_launch();

@@ -175,10 +175,11 @@ __global__ void __launch_bounds__(kBlock) k_to_mont(const __grid_constant__ N2Co
   }
 }
 
-// Segmented product over the work list of chunks.  Item = (chunk, g/h).
+// Segmented product over the work list of chunks.  Item = (chunk, g/h): ngh
+// ciphertext arrays (2: g and h; 1: g/h packed), item = chunk ngh + gh.
 template <int S, int T>
 __global__ void __launch_bounds__(kBlock) k_seg_product(const __grid_constant__ N2Const P,
-                                                        const uint32_t* __restrict__ ctm, size_t M, size_t ghs,
+                                                        const uint32_t* __restrict__ ctm, size_t M, size_t ghs, int ngh,
                                                         const int* __restrict__ idx, const int* __restrict__ off,
                                                         const int* __restrict__ choff,
                                                         const int* __restrict__ featoff, int F,
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(kBlock) k_seg_product(const __grid_constant__ 
   uint32_t n[S], a[S], t[S];
   const_slice<S>(n, P.N, k);
   const uint32_t np = P.np;
-  const long long total = 2ll * featoff[F];
+  const long long total = (long long)ngh * featoff[F];
   const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long base = warp0 * IPW; base < total; base += nwarps * IPW) {
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(kBlock) k_seg_product(const __grid_constant__ 
     const uint32_t* src = ctm;
     const int* ids = idx;
     if (valid) {
-      const int c = (int)(item >> 1), gh = (int)(item & 1);
+      const int c = (int)(ngh == 2 ? item >> 1 : item), gh = (int)(ngh == 2 ? item & 1 : 0);
       const int f = last_le(featoff, F, c);
       const int local = c - featoff[f];
       const int* co = choff + (size_t)f * (NK + 1);
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(kBlock) k_combine(const __grid_constant__ N2Co
                                                     const uint32_t* __restrict__ partial,
                                                     const int* __restrict__ off, const int* __restrict__ choff,
                                                     const int* __restrict__ featoff, int F,
-                                                    const HistDesc* __restrict__ D, int K,
+                                                    const HistDesc* __restrict__ D, int K, int ngh,
                                                     uint32_t* __restrict__ hist, int32_t* __restrict__ count_out) {
   constexpr int NL = S * T;
   const int NK = D->NK, only_node = D->only_node;
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(kBlock) k_combine(const __grid_constant__ N2Co
   uint32_t n[S], a[S], t[S];
   const_slice<S>(n, P.N, k);
   const uint32_t np = P.np;
-  const long long total = 2ll * F * NK;
+  const long long total = (long long)ngh * F * NK;
   const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long base = warp0 * IPW; base < total; base += nwarps * IPW) {
@@ -263,8 +264,8 @@ __global__ void __launch_bounds__(kBlock) k_combine(const __grid_constant__ N2Co
     const bool valid = item < total;
     int nch = 0, first = 0, gh = 0, f = 0, key = 0;
     if (valid) {
-      const long long cell = item >> 1;
-      gh = (int)(item & 1);
+      const long long cell = ngh == 2 ? item >> 1 : item;
+      gh = (int)(ngh == 2 ? item & 1 : 0);
       f = (int)(cell / NK);
       key = (int)(cell % NK);
       const int* co = choff + (size_t)f * (NK + 1);
@@ -272,12 +273,12 @@ __global__ void __launch_bounds__(kBlock) k_combine(const __grid_constant__ N2Co
       first = featoff[f] + co[key];
     }
     const int maxn = __reduce_max_sync(kFull, nch);
-    if (nch > 0) load_slice_rw<S>(a, partial + ((size_t)first * 2 + gh) * NL, k);
+    if (nch > 0) load_slice_rw<S>(a, partial + ((size_t)first * ngh + gh) * NL, k);
     for (int j = 1; j < maxn; ++j) {
       const bool act = j < nch;
       const unsigned mask = __ballot_sync(kFull, act);
       if (act) {
-        load_slice_rw<S>(t, partial + ((size_t)(first + j) * 2 + gh) * NL, k);
+        load_slice_rw<S>(t, partial + ((size_t)(first + j) * ngh + gh) * NL, k);
         __syncwarp(mask);
         stage<S>(bs, st, t, k);
         __syncwarp(mask);
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(kBlock) k_combine(const __grid_constant__ N2Co
       const int v = only_node >= 0 ? only_node : key / K;
       const int b = only_node >= 0 ? key : key % K;
       const size_t cellrow = ((size_t)v * F + f) * K + b;
-      store_slice<S>(hist + (cellrow * 2 + gh) * NL, t, k);
+      store_slice<S>(hist + (cellrow * ngh + gh) * NL, t, k);
       if (count_out && gh == 0 && k == 0) {
         const int* o = off + (size_t)f * (NK + 1);
         count_out[cellrow] = o[key + 1] - o[key];
@@ -338,7 +339,7 @@ pl_status run_prepare(const N2Const& P, const uint32_t* ct, size_t count, uint32
 }
 
 template <int S, int T>
-pl_status run_hist_products(const N2Const& P, const uint32_t* ctm, size_t M, size_t ghs, const HistBufs& B,
+pl_status run_hist_products(const N2Const& P, const uint32_t* ctm, size_t M, size_t ghs, int ngh, const HistBufs& B,
                             const HistDesc* D, int F, int NK_max, int K, int tile, uint32_t* hist, int32_t* count_out,
                             cudaStream_t s) {
   const size_t smem = (size_t)S * T * (kBlock / T) * sizeof(uint32_t);
@@ -347,17 +348,17 @@ pl_status run_hist_products(const N2Const& P, const uint32_t* ctm, size_t M, siz
   if (!grid_comb) grid_comb = occupancy_grid<S, T>((const void*)k_combine<S, T>, smem);
   {
     ProfScope _ps("seg_product", s);
-    k_seg_product<S, T><<<grid_seg, kBlock, smem, s>>>(P, ctm, M, ghs, B.idx, B.off, B.choff, B.featoff, F, D, tile,
-                                                       B.partial);
+    k_seg_product<S, T><<<grid_seg, kBlock, smem, s>>>(P, ctm, M, ghs, ngh, B.idx, B.off, B.choff, B.featoff, F, D,
+                                                       tile, B.partial);
   }
   PL_CUDA_TRY(cudaGetLastError());
   const size_t ipw = 32 / T;
-  const size_t items = 2ull * F * NK_max;
+  const size_t items = (size_t)ngh * F * NK_max;
   const size_t blocks_needed = ((items + ipw - 1) / ipw + (kBlock / 32) - 1) / (kBlock / 32);
   const int gc = (int)std::min<size_t>((size_t)grid_comb, blocks_needed);
   {
     ProfScope _ps("combine", s);
-    k_combine<S, T><<<gc, kBlock, smem, s>>>(P, B.partial, B.off, B.choff, B.featoff, F, D, K, hist, count_out);
+    k_combine<S, T><<<gc, kBlock, smem, s>>>(P, B.partial, B.off, B.choff, B.featoff, F, D, K, ngh, hist, count_out);
   }
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
@@ -374,12 +375,12 @@ pl_status dispatch_prepare(int NL, int T, const N2Const& P, const uint32_t* ct, 
   return fail(PL_EINVAL, "no mod n^2 kernel for this (limbs, lanes) pair");
 }
 
-pl_status dispatch_products(int NL, int T, const N2Const& P, const uint32_t* ctm, size_t M, size_t ghs,
+pl_status dispatch_products(int NL, int T, const N2Const& P, const uint32_t* ctm, size_t M, size_t ghs, int ngh,
                             const HistBufs& B, const HistDesc* D, int F, int NK_max, int K, int tile, uint32_t* hist,
                             int32_t* count_out, cudaStream_t s) {
-#define PL_CASE(LL, TT)                                                                                   \
-  if (NL == LL && T == TT)                                                                                \
-    return run_hist_products<LL / TT, TT>(P, ctm, M, ghs, B, D, F, NK_max, K, tile, hist, count_out, s);
+#define PL_CASE(LL, TT)                                                                                        \
+  if (NL == LL && T == TT)                                                                                     \
+    return run_hist_products<LL / TT, TT>(P, ctm, M, ghs, ngh, B, D, F, NK_max, K, tile, hist, count_out, s);
   PL_N2_CASES(PL_CASE)
 #undef PL_CASE
   return fail(PL_EINVAL, "no mod n^2 kernel for this (limbs, lanes) pair");
@@ -430,7 +431,7 @@ pl_status launch_set_desc(HistDesc* D, int num_nodes, int NK, int only_node, cud
 // from B.desc on the device, buffers are sized for NK_max.
 pl_status hist_enqueue(const pl_key* key, const AggCfg& cfg, const HistBufs& B, int NK_max, const uint32_t* d_ctm,
                        size_t M, size_t ghs, const uint8_t* d_bins, size_t bstride, int F, int K,
-                       const int32_t* d_node, uint32_t* d_hist, int32_t* d_count, int* st, cudaStream_t s) {
+                       const int32_t* d_node, uint32_t* d_hist, int32_t* d_count, int* st, cudaStream_t s, int ngh) {
   const int tile = cfg.tile;
   PL_CUDA_TRY(cudaMemsetAsync(B.cnt, 0, sizeof(int) * (size_t)F * NK_max, s));
   const int gx = (int)std::min<size_t>((M + 255) / 256, 1024);
@@ -456,7 +457,7 @@ pl_status hist_enqueue(const pl_key* key, const AggCfg& cfg, const HistBufs& B, 
     k_hist_scatter<<<grid, 256, 0, s>>>(d_bins, bstride, d_node, M, K, B.desc, B.off, B.cnt, B.idx, st);
   }
   PL_CUDA_TRY(cudaGetLastError());
-  return dispatch_products(2 * key->L, cfg.T, key->n2c, d_ctm, M, ghs, B, B.desc, F, NK_max, K, tile, d_hist,
+  return dispatch_products(2 * key->L, cfg.T, key->n2c, d_ctm, M, ghs, ngh, B, B.desc, F, NK_max, K, tile, d_hist,
                            d_count, s);
 }
 
@@ -467,7 +468,7 @@ pl_status launch_ct_prepare(pl_key* key, const uint32_t* d_ct, size_t count, uin
 
 pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, size_t ghs, const uint8_t* d_bins,
                       size_t bstride, int F, int K, const int32_t* d_node, int num_nodes, uint32_t* d_hist,
-                      int32_t* d_count, bool per_node, int* st, cudaStream_t s, Scratch* scratch) {
+                      int32_t* d_count, bool per_node, int* st, cudaStream_t s, Scratch* scratch, int ngh) {
   const AggCfg cfg = key->agg_cfg;
   const int NK_max = per_node ? K : num_nodes * K;
   const HistLayout h = hist_layout(M, F, NK_max, per_node ? kWholeCell : cfg.tile, 2 * key->L);
@@ -479,7 +480,8 @@ pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, size_t ghs, 
   if (!per_node) {
     pl_status rc = launch_set_desc(B.desc, num_nodes, num_nodes * K, -1, s);
     if (rc) return rc;
-    return hist_enqueue(key, cfg, B, NK_max, d_ctm, M, ghs, d_bins, bstride, F, K, d_node, d_hist, d_count, st, s);
+    return hist_enqueue(key, cfg, B, NK_max, d_ctm, M, ghs, d_bins, bstride, F, K, d_node, d_hist, d_count, st, s,
+                        ngh);
   }
   // the plain per-node method: one set of launches per node and one work
   // item (one lane group) per whole cell, no splitting of large cells
@@ -487,7 +489,8 @@ pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, size_t ghs, 
   for (int v = 0; v < num_nodes; ++v) {
     pl_status rc = launch_set_desc(B.desc, num_nodes, K, v, s);
     if (rc) return rc;
-    rc = hist_enqueue(key, plain, B, NK_max, d_ctm, M, ghs, d_bins, bstride, F, K, d_node, d_hist, d_count, st, s);
+    rc = hist_enqueue(key, plain, B, NK_max, d_ctm, M, ghs, d_bins, bstride, F, K, d_node, d_hist, d_count, st, s,
+                      ngh);
     if (rc) return rc;
   }
   return PL_OK;

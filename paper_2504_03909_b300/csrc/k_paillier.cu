@@ -31,6 +31,26 @@ __global__ void k_encode(const float* __restrict__ v, size_t count, uint64_t* __
   }
 }
 
+// g/h packing: m = enc(g) + 2^B enc(h) as two little-endian 64-bit words
+// (enc as k_encode), 26 <= B <= 64.
+__global__ void k_encode_gh(const float* __restrict__ g, const float* __restrict__ h, size_t count, int B,
+                            uint64_t* __restrict__ m, int* status) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const float x = g[i], y = h[i];
+    uint64_t eg = 0, eh = 0;
+    if (x >= -1.0f && x <= 32768.0f && y >= -1.0f && y <= 32768.0f) {
+      eg = (uint64_t)(__float2ll_rn(x * 16777216.0f) + (1ll << 24));
+      eh = (uint64_t)(__float2ll_rn(y * 16777216.0f) + (1ll << 24));
+      if (B < 64 && (eg >> B) != 0) atomicOr(status, kStatusRange);
+    } else {
+      atomicOr(status, kStatusEncode);
+    }
+    // eg + eh 2^B, eg < 2^B
+    m[2 * i] = eg | (B < 64 ? eh << B : 0);
+    m[2 * i + 1] = B < 64 ? eh >> (64 - B) : eh;
+  }
+}
+
 __global__ void k_decode(const uint64_t* __restrict__ s, const int32_t* __restrict__ cnt, size_t count,
                          double* __restrict__ out) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
@@ -102,7 +122,7 @@ PL_DEV void window_exp(uint32_t (&acc)[S], const uint32_t (&n)[S], uint32_t np, 
 template <int S, int T, bool DEC>
 __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ ModexpParams P,
                                                    const uint32_t* __restrict__ in, const uint64_t* __restrict__ msg,
-                                                   uint32_t* __restrict__ out, uint32_t* __restrict__ tbl,
+                                                   int mw, uint32_t* __restrict__ out, uint32_t* __restrict__ tbl,
                                                    size_t count) {
   constexpr int NL = S * T;
   constexpr int IPW = 32 / T;
@@ -133,13 +153,16 @@ __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ Modex
     uint32_t* yrow = out + ((size_t)h * count + ii) * NL;
 
     if constexpr (!DEC) {
-      // post-factor (1 + m n) mod x^2 = mont(nR, m) + 1, parked in the output row
-      const uint64_t m = msg[ii];
+      // post-factor (1 + m n) mod x^2 = mont(nR, m) + 1, parked in the output row;
+      // m has mw (1 or 2) little-endian 64-bit words
+      const uint64_t m = msg[ii * mw];
+      const uint64_t mh = mw == 2 ? msg[ii * 2 + 1] : 0;
       __syncwarp();
 #pragma unroll
       for (int j = 0; j < S; ++j) {
         const int idx = k * S + j;
-        bs[idx * st] = idx == 0 ? (uint32_t)m : (idx == 1 ? (uint32_t)(m >> 32) : 0u);
+        const uint64_t word = idx < 2 ? m : mh;
+        bs[idx * st] = idx < 4 ? (uint32_t)(word >> (32 * (idx & 1))) : 0u;
       }
       __syncwarp();
       const_slice<S>(a, H.nR, k);
@@ -325,13 +348,13 @@ __global__ void __launch_bounds__(kBlock) k_dec_crt(const __grid_constant__ DecC
 // launch helpers
 
 template <int S, int T, bool DEC>
-pl_status run_modexp(const ModexpParams* P, const uint32_t* in, const uint64_t* msg, uint32_t* y, uint32_t* tbl,
-                     int grid, size_t count, cudaStream_t s) {
+pl_status run_modexp(const ModexpParams* P, const uint32_t* in, const uint64_t* msg, int mw, uint32_t* y,
+                     uint32_t* tbl, int grid, size_t count, cudaStream_t s) {
   const int ipb = kBlock / T;
   const size_t smem = (size_t)S * T * ipb * sizeof(uint32_t);
   {
     ProfScope _ps((DEC ? "modexp_dec" : "modexp_enc"), s);
-    k_modexp<S, T, DEC><<<grid, kBlock, smem, s>>>(*P, in, msg, y, tbl, count);
+    k_modexp<S, T, DEC><<<grid, kBlock, smem, s>>>(*P, in, msg, mw, y, tbl, count);
   }
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
@@ -354,11 +377,12 @@ int modexp_grid() {
 // dispatch on (limbs per half L, lanes per instance T)
 template <bool DEC>
 pl_status modexp_dispatch(int L, int T, int* grid_out, bool launch, const ModexpParams* P, const uint32_t* in,
-                          const uint64_t* msg, uint32_t* y, uint32_t* tbl, size_t count, cudaStream_t s) {
+                          const uint64_t* msg, uint32_t* y, uint32_t* tbl, size_t count, cudaStream_t s,
+                          int mw = 1) {
 #define PL_CASE(LL, TT)                                                            \
   if (L == LL && T == TT) {                                                        \
     if (!launch) { *grid_out = modexp_grid<LL / TT, TT, DEC>(); return PL_OK; }     \
-    return run_modexp<LL / TT, TT, DEC>(P, in, msg, y, tbl, *grid_out, count, s);   \
+    return run_modexp<LL / TT, TT, DEC>(P, in, msg, mw, y, tbl, *grid_out, count, s); \
   }
   PL_CASE(32, 2)
   PL_CASE(32, 4)
@@ -389,6 +413,18 @@ pl_status launch_encode(const float* d_v, size_t count, uint64_t* d_m, int* st, 
   return PL_OK;
 }
 
+pl_status launch_encode_gh(const float* d_g, const float* d_h, size_t count, int B, uint64_t* d_m, int* st,
+                           cudaStream_t s) {
+  if (count == 0) return PL_OK;
+  const int grid = (int)std::min<size_t>((count + 255) / 256, (size_t)sm_count() * 8);
+  {
+    ProfScope _ps("encode", s);
+    k_encode_gh<<<grid, 256, 0, s>>>(d_g, d_h, count, B, d_m, st);
+  }
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+}
+
 pl_status launch_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t count, double* d_out, cudaStream_t s) {
   if (count == 0) return PL_OK;
   const int grid = (int)std::min<size_t>((count + 255) / 256, (size_t)sm_count() * 8);
@@ -403,7 +439,7 @@ pl_status launch_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t count,
 // Shared by encrypt and decrypt: scratch = y [2][count][L] + window tables.
 template <bool DEC>
 static pl_status modexp_phase(pl_key* key, const ModexpCfg& cfg, const uint32_t* in, const uint64_t* msg,
-                              size_t count, uint32_t** y_out, cudaStream_t s, Scratch* scratch) {
+                              size_t count, uint32_t** y_out, cudaStream_t s, Scratch* scratch, int mw = 1) {
   const ModexpParams* P = key->modexp_params(DEC, cfg.w);
   if (!P) return fail(PL_EINVAL, "unsupported window width");
   const int L = key->L;
@@ -425,16 +461,16 @@ static pl_status modexp_phase(pl_key* key, const ModexpCfg& cfg, const uint32_t*
   if (!base) return fail(PL_ENOMEM, "scratch allocation failed");
   uint32_t* y = reinterpret_cast<uint32_t*>(base + off_y);
   uint32_t* tbl = reinterpret_cast<uint32_t*>(base + off_t);
-  rc = modexp_dispatch<DEC>(L, cfg.T, &grid, true, P, in, msg, y, tbl, count, s);
+  rc = modexp_dispatch<DEC>(L, cfg.T, &grid, true, P, in, msg, y, tbl, count, s, mw);
   *y_out = y;
   return rc;
 }
 
 pl_status launch_encrypt(pl_key* key, const uint64_t* d_m, const uint32_t* d_r, size_t count, uint32_t* d_ct,
-                         cudaStream_t s, Scratch* scratch) {
+                         cudaStream_t s, Scratch* scratch, int mw) {
   if (count == 0) return PL_OK;
   uint32_t* y = nullptr;
-  pl_status rc = modexp_phase<false>(key, key->enc_cfg, d_r, d_m, count, &y, s, scratch);
+  pl_status rc = modexp_phase<false>(key, key->enc_cfg, d_r, d_m, count, &y, s, scratch, mw);
   if (rc) return rc;
   {
     ProfScope _ps("enc_crt", s);

@@ -72,6 +72,11 @@ SIGNATURES.update({
     "paillier_pack_slots": (_i, [_vp, _i]),
     "paillier_pack": (_i, [_vp, _vp, _sz, _i, _vp, _vp]),
     "paillier_decrypt_packed_u64": (_i, [_vp, _vp, _sz, _i, _vp, _vp]),
+    "paillier_encode_gh": (_i, [_vp, _vp, _sz, _i, _vp, _vp]),
+    "paillier_encrypt_gh": (_i, [_vp, _vp, _vp, _sz, _vp, _vp]),
+    "paillier_hist_aggregate_gh": (_i, [_vp, _vp, _sz, _vp, _i, _i, _vp, _i, _vp, _vp, _vp]),
+    "paillier_decrypt_gh": (_i, [_vp, _vp, _sz, _i, _vp, _vp]),
+    "paillier_decrypt_packed_gh": (_i, [_vp, _vp, _sz, _i, _vp, _vp]),
     "paillier_split_find": (_i, [_vp, _vp, _i, _i, _i, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp, _vp]),
     "paillier_split_apply": (_i, [_vp, _sz, _vp, _vp, _vp, _vp, _vp]),
     "paillier_tree_decide": (_i, [_vp, _i, _i, _sz, _vp, _vp, _i, _vp, _vp]),

@@ -305,6 +305,65 @@ def decrypt_packed_u64(key: Key, packed: torch.Tensor, count: int, slot_bits: in
     return out
 
 
+# ---- g/h packing: one plaintext per sample (include/paillier_pack.h) --------
+
+def encode_gh(g: torch.Tensor, h: torch.Tensor, B: int, out: torch.Tensor | None = None, stream=None):
+    """m = enc(g) + 2^B enc(h): [count, 2] int64 (bits of the two uint64 words)."""
+    assert g.dtype == torch.float32 and h.dtype == torch.float32 and g.shape == h.shape
+    count = g.numel()
+    if out is None:
+        out = torch.empty((count, 2), dtype=torch.int64, device=g.device)
+    call("paillier_encode_gh", _ptr(g), _ptr(h), count, B, _ptr(out), _stream(stream))
+    return out
+
+
+def encrypt_gh(key: Key, m: torch.Tensor, r: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """Ciphertexts [count, 2L] of two-word plaintexts m [count, 2]."""
+    assert m.dtype == torch.int64 and m.shape[-1] == 2
+    count = m.numel() // 2
+    assert r.dtype == torch.int32 and r.numel() == count * key.L
+    if out is None:
+        out = torch.empty((count, 2 * key.L), dtype=torch.int32, device=m.device)
+    call("paillier_encrypt_gh", key.handle, _ptr(m), _ptr(r), count, _ptr(out), _stream(stream))
+    return out
+
+
+def hist_aggregate_gh(key: Key, ctm: torch.Tensor, bins: torch.Tensor, node: torch.Tensor, num_nodes: int, K: int,
+                      hist: torch.Tensor | None = None, count: torch.Tensor | None = None, stream=None):
+    """Encrypted histogram [num_nodes, F, K, 2L] and counts of ONE g/h-packed
+    Montgomery-form array ctm [M, 2L]."""
+    M = node.numel()
+    F = bins.shape[0]
+    assert ctm.dtype == torch.int32 and ctm.shape == (M, 2 * key.L)
+    assert bins.dtype == torch.uint8 and bins.shape == (F, M) and node.dtype == torch.int32
+    if hist is None:
+        hist = torch.empty((num_nodes, F, K, 2 * key.L), dtype=torch.int32, device=ctm.device)
+    if count is None:
+        count = torch.empty((num_nodes, F, K), dtype=torch.int32, device=ctm.device)
+    call("paillier_hist_aggregate_gh", key.handle, _ptr(ctm), M, _ptr(bins), F, K, _ptr(node), num_nodes,
+         _ptr(hist), _ptr(count), _stream(stream))
+    return hist, count
+
+
+def decrypt_gh(key: Key, ct: torch.Tensor, B: int, out: torch.Tensor | None = None, stream=None):
+    """(S_g, S_h) [count, 2] (int64 bits of uint64) of g/h-packed cells ct [..., 2L]."""
+    assert ct.dtype == torch.int32 and ct.shape[-1] == 2 * key.L
+    count = ct.numel() // (2 * key.L)
+    if out is None:
+        out = torch.empty((count, 2), dtype=torch.int64, device=ct.device)
+    call("paillier_decrypt_gh", key.handle, _ptr(ct), count, B, _ptr(out), _stream(stream))
+    return out
+
+
+def decrypt_packed_gh(key: Key, packed: torch.Tensor, cells: int, B: int, out: torch.Tensor | None = None,
+                      stream=None):
+    """(S_g, S_h) [cells, 2] of g/h-packed cells packed with pack(slot_bits = 2B)."""
+    if out is None:
+        out = torch.empty((cells, 2), dtype=torch.int64, device=packed.device)
+    call("paillier_decrypt_packed_gh", key.handle, _ptr(packed), cells, B, _ptr(out), _stream(stream))
+    return out
+
+
 def split_find(sums: torch.Tensor, counts: torch.Tensor, lam: float = 1.0, gamma: float = 0.0,
                min_child_weight: float = 0.0, stream=None):
     """Best split per node from decrypted sums [nodes, F, K, 2] (int64 bits of

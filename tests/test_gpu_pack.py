@@ -62,3 +62,84 @@ def test_overflowing_slot_is_reported(cells):
     with pytest.raises(native.PaillierError) as e:
         P.sync()
     assert e.value.code == native.PL_ERANGE
+
+
+# ---- g/h packing: one plaintext per sample -----------------------------------
+
+@pytest.fixture(scope="module", params=[1024, 2048])
+def gh_case(request):
+    n_bits = request.param
+    p, q = synth.gen_primes(n_bits, 7)
+    key = P.Key.from_primes(n_bits, p, q)
+    M, F, K, nodes = 3000, 5, 16, 3
+    gh = synth.gen_gh(M, 7)
+    bins = synth.gen_bins_uniform(F, M, K, 7)
+    node = synth.rng_misc(70).integers(-1, nodes, size=M).astype(np.int32)
+    r = synth.gen_r(p * q, n_bits, M, 7, p, q)
+    B = 25 + int(np.ceil(np.log2(M))) + 1
+    g_d, h_d = torch.from_numpy(gh[0].copy()).cuda(), torch.from_numpy(gh[1].copy()).cuda()
+    m2 = P.encode_gh(g_d, h_d, B)
+    ct = P.encrypt_gh(key, m2, P.to_limb_tensor(r))
+    ctm = P.ct_prepare(key, ct)
+    hist, cnt = P.hist_aggregate_gh(key, ctm, torch.from_numpy(bins).cuda(), torch.from_numpy(node).cuda(), nodes, K)
+    P.sync()
+    return dict(key=key, p=p, q=q, M=M, F=F, K=K, nodes=nodes, gh=gh, bins=bins, node=node, r=r, B=B, m2=m2,
+                ct=ct, hist=hist, cnt=cnt)
+
+
+def test_gh_encode_and_encrypt_bit_exact(gh_case):
+    c = gh_case
+    g, h, B = c["gh"][0], c["gh"][1], c["B"]
+    words = c["m2"].cpu().numpy().view(np.uint64)
+    got = [int(lo) + (int(hi) << 64) for lo, hi in words]
+    want = [oracle.encode_gh(g[i], h[i], B) for i in range(c["M"])]
+    assert got == want
+    pub = oracle.PublicKey(c["p"] * c["q"])
+    cts = synth.limbs_to_ints(P.from_limb_tensor(c["ct"]))
+    rs = synth.limbs_to_ints(c["r"])
+    for i in [0, 1, c["M"] - 1] + list(synth.rng_misc(71).integers(0, c["M"], size=20)):
+        assert cts[i] == oracle.encrypt(pub, want[i], rs[i]), i
+
+
+def test_gh_histogram_cells_and_sums(gh_case):
+    c = gh_case
+    key, B, K, F, nodes = c["key"], c["B"], c["K"], c["F"], c["nodes"]
+    pub = oracle.PublicKey(c["p"] * c["q"])
+    cts = synth.limbs_to_ints(P.from_limb_tensor(c["ct"]))
+    cells = synth.limbs_to_ints(P.from_limb_tensor(c["hist"].reshape(-1, 2 * key.L)))
+    for v, f, b in [(0, 0, 0), (nodes - 1, F - 1, K - 1), (1, 2, 7)]:
+        assert cells[(v * F + f) * K + b] == oracle.encrypted_histogram_cell(pub, cts, c["bins"], c["node"], v, f, b)
+    eg = np.array([oracle.encode(x) for x in c["gh"][0]], dtype=np.int64)
+    eh = np.array([oracle.encode(x) for x in c["gh"][1]], dtype=np.int64)
+    want, counts = oracle.plain_histogram_np(eg, eh, c["bins"], c["node"], nodes, K)
+    assert c["cnt"].cpu().numpy().tolist() == counts.tolist()
+    flat = c["hist"].reshape(-1, 2 * key.L)
+    sums = P.decrypt_gh(key, flat, B)
+    P.sync()
+    assert sums.cpu().numpy().reshape(want.shape).tolist() == want.tolist()
+    # with ciphertext packing on top: slots of 2B bits, split at B
+    for cnum in (flat.shape[0], flat.shape[0] - 5):
+        packed = P.pack(key, flat[:cnum], 2 * B)
+        s2 = P.decrypt_packed_gh(key, packed, cnum, B)
+        P.sync()
+        assert packed.shape[0] == -(-cnum // P.pack_slots(key, 2 * B))
+        assert s2.cpu().numpy().tolist() == want.reshape(-1, 2)[:cnum].tolist()
+
+
+def test_gh_ranges(gh_case):
+    key = gh_case["key"]
+    g = torch.full((4,), 4.0, dtype=torch.float32, device="cuda")  # enc(4.0) = 5 2^24 needs 27 bits
+    h = torch.zeros(4, dtype=torch.float32, device="cuda")
+    with pytest.raises(native.PaillierError):
+        P.encode_gh(g, h, 25)  # B below 26
+    P.encode_gh(g, h, 26)
+    with pytest.raises(native.PaillierError) as e:
+        P.sync()
+    assert e.value.code == native.PL_ERANGE
+    # a cell above 2B bits is reported on decryption
+    big = P.encrypt(key, torch.tensor([1 << 62], dtype=torch.int64, device="cuda"),
+                    P.to_limb_tensor(gh_case["r"][:1]))
+    P.decrypt_gh(key, big, 30)
+    with pytest.raises(native.PaillierError) as e:
+        P.sync()
+    assert e.value.code == native.PL_ERANGE

@@ -205,6 +205,34 @@ def test_encrypted_histogram_decrypts_to_plain():
     assert H2 == H
 
 
+def test_gh_packing_decrypts_to_both_plain_histograms():
+    """One plaintext per sample, encode(g) + 2^B encode(h): the decrypted cell
+    splits into the g and h sums of np.bincount (independent of the oracle's
+    histogram code), for B just above the sums' width."""
+    p, q = synth.gen_primes(256, 10)
+    pub, priv = oracle.keypair(p, q)
+    rng = synth.rng_misc(14)
+    M, F, K = 90, 2, 4
+    g = rng.uniform(-1, 1, size=M).astype(np.float32)
+    h = rng.uniform(0, 0.25, size=M).astype(np.float32)
+    bins = rng.integers(0, K, size=(F, M))
+    node = np.zeros(M, dtype=int)
+    B = 25 + int(np.ceil(np.log2(M))) + 1
+    rr = random.Random(5)
+    c = [oracle.encrypt(pub, oracle.encode_gh(g[i], h[i], B), rr.randrange(1, pub.n)) for i in range(M)]
+    eg = np.array([oracle.encode(x) for x in g], dtype=np.int64)
+    eh = np.array([oracle.encode(x) for x in h], dtype=np.int64)
+    for f in range(F):
+        want_g = np.bincount(bins[f], weights=eg, minlength=K).astype(np.int64)
+        want_h = np.bincount(bins[f], weights=eh, minlength=K).astype(np.int64)
+        for b in range(K):
+            cell = oracle.encrypted_histogram_cell(pub, c, bins, node, 0, f, b)
+            sg, sh = oracle.split_gh(oracle.decrypt(priv, cell), B)
+            assert (sg, sh) == (int(want_g[b]), int(want_h[b]))
+    with pytest.raises(ValueError):
+        oracle.encode_gh(1.0, 0.0, 25)  # encode(1.0) = 2^25 needs 26 bits
+
+
 def test_miller_rabin_known_values():
     for e in (521, 607, 1279):  # Mersenne primes
         assert oracle.is_probable_prime(2 ** e - 1)
