@@ -882,12 +882,31 @@ def run_batched(args, cfg):
     stream = torch.cuda.Stream()
 
     pack_bits = args.pack_bits
+    B = args.gh_bits  # g/h packing: one plaintext enc(g) + 2^B enc(h) per sample (0: off)
+    if B:
+        # the histogram slot of a g/h cell holds S_g + 2^B S_h: 2B bits when packed
+        pack_bits = 2 * B if args.pack_bits else 0
+        hist_gh = torch.empty((maxn, F, K, 2 * L), dtype=torch.int32, device=dev)
+        m2 = torch.empty((M, 2), dtype=torch.int64, device=dev)
+        ct1 = torch.empty((M, 2 * L), dtype=torch.int32, device=dev)
+        ctm1 = torch.empty_like(ct1)
     slots = P.pack_slots(key, pack_bits) if pack_bits else 0
     packed = (torch.empty((-(-(maxn * F * K * 2) // slots), 2 * L), dtype=torch.int32, device=dev)
               if pack_bits else None)
     split_nodes = torch.zeros(M, dtype=torch.int32, device=dev)
 
     def decrypt_level(nn):
+        if B:
+            cells = hist_gh[:nn].reshape(-1, 2 * L)
+            nc = cells.shape[0]
+            out = sums[:2 * nc].view(nc, 2)
+            if pack_bits:
+                npk = -(-nc // slots)
+                P.pack(key, cells, pack_bits, out=packed[:npk])
+                P.decrypt_packed_gh(key, packed[:npk], nc, B, out=out)
+            else:
+                P.decrypt_gh(key, cells, B, out=out)
+            return
         cells = hist[:nn].reshape(-1, 2 * L)
         if pack_bits:
             npk = -(-cells.shape[0] // slots)
@@ -896,10 +915,22 @@ def run_batched(args, cfg):
         else:
             P.decrypt_u64(key, cells, out=sums[:cells.shape[0]])
 
+    def level_hist(nn):
+        """This level's encrypted histograms of the nodes in node_buf."""
+        if B:
+            P.hist_aggregate_gh(key, ctm1, bins_d, node_buf, nn, K, hist=hist_gh[:nn], count=cnt[:nn])
+        else:
+            plan.run(ctm.view(2, M, 2 * L), bins_d, node_buf, nn, hist=hist, count=cnt)
+
     def tree_step(with_decrypt=True):
-        m = P.encode(v)
-        P.encrypt(key, m, r_d, out=ct)
-        P.ct_prepare(key, ct, out=ctm)
+        if B:
+            P.encode_gh(v[:M], v[M:], B, out=m2)
+            P.encrypt_gh(key, m2, r_d[:M], out=ct1)
+            P.ct_prepare(key, ct1, out=ctm1)
+        else:
+            m = P.encode(v)
+            P.encrypt(key, m, r_d, out=ct)
+            P.ct_prepare(key, ct, out=ctm)
         if args.splits == "data":
             split_nodes.zero_()
         parent = None
@@ -914,13 +945,13 @@ def run_batched(args, cfg):
                 psums, pcnt, pf, pb = parent
                 small_right, small_node = P.child_select(node_buf, pcnt, pf, pb)
                 node_buf.copy_(small_node)
-                plan.run(ctm.view(2, M, 2 * L), bins_d, node_buf, nn // 2, hist=hist, count=cnt)
+                level_hist(nn // 2)
                 decrypt_level(nn // 2)
                 lsums, lcnt = P.child_subtract(psums, pcnt, sums[:nn // 2 * F * K * 2].view(nn // 2, F, K, 2),
                                                cnt[:nn // 2], small_right)
                 node_buf.copy_(split_nodes)
             else:
-                plan.run(ctm.view(2, M, 2 * L), bins_d, node_buf, nn, hist=hist, count=cnt)
+                level_hist(nn)
                 if not with_decrypt:
                     continue
                 decrypt_level(nn)
@@ -934,7 +965,10 @@ def run_batched(args, cfg):
     def hist_levels(per_node):
         for lvl in range(depth):
             nn = 1 << lvl
-            if per_node:
+            if B:  # g/h packed: one ciphertext array, batched launches only
+                node_buf.copy_(nodes_d[lvl])
+                level_hist(nn)
+            elif per_node:
                 P.hist_aggregate(key, ctm.view(2, M, 2 * L), bins_d, nodes_d[lvl], nn, K, hist=hist[:nn],
                                  count=cnt[:nn], per_node=True)
             else:
@@ -969,7 +1003,7 @@ def run_batched(args, cfg):
             hist_levels(False)
             t_batched = timed(lambda: hist_levels(False), args.steps)
             t_per_node = None
-            if not args.no_compare:
+            if not args.no_compare and not B:
                 hist_levels(True)
                 t_per_node = timed(lambda: hist_levels(True), args.steps)
         P.sync(stream)
@@ -977,7 +1011,7 @@ def run_batched(args, cfg):
     strict = 0
     for lv in levels:
         inn = int((lv >= 0).sum())
-        ct_mults += 2 * F * inn
+        ct_mults += (1 if B else 2) * F * inn
     cells = sum((1 << lvl) * F * K * 2 for lvl in range(depth))
     line = {
         "metric": METRIC, "value": ct_mults / t_batched, "unit": "ct-mults/s", "n_gpus": world,
@@ -999,6 +1033,7 @@ def run_batched(args, cfg):
                                "decrypt": prof["modexp_dec"] + prof["dec_crt"] + prof["unpack"]},
         "decrypted_cells_per_tree": cells,
         "pack_bits": pack_bits, "pack_slots": slots, "splits": args.splits, "subtract": bool(args.subtract),
+        "gh_bits": B, "encryptions_per_tree": M if B else 2 * M,
         "cells_decoded_per_s": cells / ((prof["modexp_dec"] + prof["dec_crt"] + prof["unpack"] + prof["pack"]) * 1e-3),
         "graph": plan.stats(),
         "clocks": clk.summary(),
@@ -1141,6 +1176,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nodes", type=int, default=1, help="horizontal: node histograms per round")
+    ap.add_argument("--gh-bits", type=int, default=0,
+                    help="tree modes: g/h packing, one plaintext enc(g) + 2^B enc(h) per sample (B bits; 0 = off)")
     args = ap.parse_args()
     cfg = synth.CONFIGS.get(args.config, {})
     if args.config == "oracle":
