@@ -1063,10 +1063,17 @@ def run_serving(args, cfg):
         L = n_bits // 32
         gh = synth.gen_gh(NUNIQ, seed)
         r = synth.gen_r(p * q, n_bits, 2 * NUNIQ, seed, p, q)
-        m = P.encode(torch.from_numpy(gh.reshape(-1)).to(dev))
-        ct = P.encrypt(key, m, P.to_limb_tensor(r, dev)).view(2, NUNIQ, 2 * L)
+        if args.gh_bits:  # one g/h-packed ciphertext per sample
+            g_d, h_d = torch.from_numpy(gh[0].copy()).to(dev), torch.from_numpy(gh[1].copy()).to(dev)
+            ct = P.encrypt_gh(key, P.encode_gh(g_d, h_d, args.gh_bits), P.to_limb_tensor(r[:NUNIQ], dev))
+            ct = ct.view(1, NUNIQ, 2 * L)
+        else:
+            m = P.encode(torch.from_numpy(gh.reshape(-1)).to(dev))
+            ct = P.encrypt(key, m, P.to_limb_tensor(r, dev)).view(2, NUNIQ, 2 * L)
         # the resident dataset repeats the NUNIQ encrypted samples up to MMAX rows
         full = ct.repeat(1, (MMAX + NUNIQ - 1) // NUNIQ, 1)[:, :MMAX].contiguous()
+        if args.gh_bits:
+            full = full.view(MMAX, 2 * L)
         keys[n_bits] = key
         ctms[n_bits] = P.ct_prepare(key, full)
         del ct, full
@@ -1087,19 +1094,23 @@ def run_serving(args, cfg):
 
     def submit(srv, rq):
         return srv.submit(keys[rq["nb"]], ctms[rq["nb"]], rq["M"], rq["F"], rq["K"], bins[rq["party"]][rq["K"]],
-                          gh_stride=MMAX, bins_stride=MMAX, pack_bits=args.pack_bits)
+                          gh_stride=MMAX, bins_stride=MMAX, pack_bits=args.pack_bits, gh_bits=args.gh_bits)
+
+    ngh = 1 if args.gh_bits else 2
 
     def work(rq):
         """Modelled multiply-adds of a request: its histogram products mod n^2 plus
         its decryptions (per packed ciphertext when packing)."""
         L = rq["nb"] // 32
-        cells = 2 * rq["F"] * rq["K"]
+        w = 6 if rq["nb"] >= 2048 else 5
+        cells = ngh * rq["F"] * rq["K"]
+        slot_bits = 2 * args.gh_bits if args.gh_bits else args.pack_bits
         if args.pack_bits:
-            slots = (rq["nb"] - 2) // args.pack_bits
-            dec = -(-cells // slots) * dec_imad(rq["nb"], 6 if rq["nb"] >= 2048 else 5) + cells * (args.pack_bits + 2) * mont_imad(2 * L)
+            slots = (rq["nb"] - 2) // slot_bits
+            dec = -(-cells // slots) * dec_imad(rq["nb"], w) + cells * (slot_bits + 2) * mont_imad(2 * L)
         else:
-            dec = cells * dec_imad(rq["nb"], 6 if rq["nb"] >= 2048 else 5)
-        return 2 * rq["M"] * rq["F"] * mont_imad(2 * L) + dec
+            dec = cells * dec_imad(rq["nb"], w)
+        return ngh * rq["M"] * rq["F"] * mont_imad(2 * L) + dec
 
     srv = P.Server(slots=args.slots, hbm_budget=budget)
     # warm-up, then the closed-loop capacity in work units (every slot busy)
@@ -1147,7 +1158,7 @@ def run_serving(args, cfg):
                                "M log-uniform [1e3, 1e6], F uniform [8, 64], K uniform {64..256 step 32}, "
                                "2048/3072-bit keys p = 0.5, resident ciphertexts", "slots": args.slots,
                    "hbm_budget_bytes": budget, "offered_load": args.load, "requests": args.requests,
-                   "pack_bits": args.pack_bits},
+                   "pack_bits": args.pack_bits, "gh_bits": args.gh_bits},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "throughput_req_per_s": len(lat) / wall,
         "capacity_req_per_s": capacity, "arrival_rate_req_per_s": rate,

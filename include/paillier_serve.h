@@ -52,6 +52,11 @@ typedef struct pl_request {
   /* 0: decrypt every cell; B in [1, 64]: pack the cells into B-bit slots
    * before decrypting (see paillier_pack.h; every cell sum must be < 2^B). */
   int pack_bits;
+  /* 0: d_ctm holds separate g and h arrays as above.  G in [26, 64]: d_ctm
+   * holds ONE g/h-packed array [M][2L] (paillier_encrypt_gh with B = G, then
+   * paillier_ct_prepare; gh_stride is not used); the cells split into
+   * (S_g, S_h) at bit G, and a nonzero pack_bits packs them in 2G-bit slots. */
+  int gh_bits;
 } pl_request;
 
 #define PL_REQ_QUEUED    0

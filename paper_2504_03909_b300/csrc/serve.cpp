@@ -42,15 +42,19 @@ size_t round_up(size_t x) { return (x + 255) & ~size_t(255); }
 // device memory one request needs while it runs
 size_t request_bytes(const pl_request& r) {
   const size_t L = (size_t)r.key->L;
-  const size_t cells = (size_t)r.num_nodes * r.F * r.K * 2;
-  size_t b = round_up(cells * 2 * L * 4) + round_up((size_t)r.num_nodes * r.F * r.K * 4) + round_up(cells * 8);
+  const size_t ncell = (size_t)r.num_nodes * r.F * r.K;
+  const size_t hcells = ncell * (r.gh_bits ? 1 : 2);  // histogram ciphertexts
+  size_t b = round_up(hcells * 2 * L * 4) + round_up(ncell * 4) + round_up(ncell * 2 * 8);
   if (!r.d_node) b += round_up(r.M * 4);
   const pl::HistLayout h = pl::hist_layout(r.M, r.F, r.num_nodes * r.K, r.key->agg_cfg.tile, (int)(2 * L));
-  size_t dec_cells = cells;
+  size_t dec_cells = hcells;
   if (r.pack_bits > 0) {
-    const size_t slots = (size_t)(r.key->n_bits - 2) / (size_t)r.pack_bits;
-    dec_cells = (cells + slots - 1) / slots;
+    const int slot_bits = r.gh_bits ? 2 * r.gh_bits : r.pack_bits;
+    const size_t slots = (size_t)(r.key->n_bits - 2) / (size_t)slot_bits;
+    dec_cells = (hcells + slots - 1) / slots;
     b += round_up(dec_cells * 2 * L * 4) + round_up(dec_cells * L * 4);  // packed ciphertexts + plaintexts
+  } else if (r.gh_bits) {
+    b += round_up(dec_cells * L * 4);  // plaintexts before the split
   }
   b += std::max(h.bytes, pl::decrypt_scratch_bytes(r.key, dec_cells));
   return b;
@@ -106,7 +110,9 @@ struct pl_server {
       }
       return sl.allocs[i];
     };
-    auto* hist = static_cast<uint32_t*>(amalloc(0, cells * 2 * L * 4));
+    const int ngh = r.gh_bits ? 1 : 2;
+    const size_t hcells = ncell * ngh;
+    auto* hist = static_cast<uint32_t*>(amalloc(0, hcells * 2 * L * 4));
     auto* counts = static_cast<int32_t*>(amalloc(1, ncell * 4));
     auto* sums = static_cast<uint64_t*>(amalloc(2, cells * 8));
     const int32_t* node = r.d_node;
@@ -115,16 +121,23 @@ struct pl_server {
       cudaMemsetAsync(sl.d_status, 0, sizeof(int), s);
       if (!r.d_node) cudaMemsetAsync(const_cast<int32_t*>(node), 0, r.M * 4, s);
       rc = launch_hist(key, r.d_ctm, r.M, r.gh_stride, r.d_bins, r.bins_stride, r.F, r.K, node, r.num_nodes, hist,
-                       counts, false, sl.d_status, s, &sl.scratch);
+                       counts, false, sl.d_status, s, &sl.scratch, ngh);
     }
     if (rc == PL_OK && r.pack_bits > 0) {
-      const int slots = (key->n_bits - 2) / r.pack_bits;
-      const size_t npacked = (cells + slots - 1) / slots;
+      const int slot_bits = r.gh_bits ? 2 * r.gh_bits : r.pack_bits;
+      const int slots = (key->n_bits - 2) / slot_bits;
+      const size_t npacked = (hcells + slots - 1) / slots;
       auto* packed = static_cast<uint32_t*>(amalloc(4, npacked * 2 * L * 4));
       auto* plain = static_cast<uint32_t*>(amalloc(5, npacked * L * 4));
-      if (rc == PL_OK) rc = launch_pack(key, hist, cells, slots, r.pack_bits, packed, s);
+      if (rc == PL_OK) rc = launch_pack(key, hist, hcells, slots, slot_bits, packed, s);
       if (rc == PL_OK) rc = launch_decrypt(key, packed, npacked, plain, false, sl.d_status, s, &sl.scratch);
-      if (rc == PL_OK) rc = launch_unpack(plain, (int)L, cells, slots, r.pack_bits, sums, sl.d_status, s);
+      if (rc == PL_OK)  // g/h cells: each 2B-bit slot is two B-bit sums
+        rc = r.gh_bits ? launch_unpack(plain, (int)L, cells, 2 * slots, r.gh_bits, sums, sl.d_status, s)
+                       : launch_unpack(plain, (int)L, cells, slots, r.pack_bits, sums, sl.d_status, s);
+    } else if (rc == PL_OK && r.gh_bits) {
+      auto* plain = static_cast<uint32_t*>(amalloc(5, hcells * L * 4));
+      if (rc == PL_OK) rc = launch_decrypt(key, hist, hcells, plain, false, sl.d_status, s, &sl.scratch);
+      if (rc == PL_OK) rc = launch_unpack(plain, (int)L, cells, 2, r.gh_bits, sums, sl.d_status, s);
     } else if (rc == PL_OK) {
       rc = launch_decrypt(key, hist, cells, sums, true, sl.d_status, s, &sl.scratch);
     }
@@ -242,7 +255,8 @@ pl_status pl_server_submit(pl_server* srv, const pl_request* req, uint64_t* tick
   if (r.M < 1 || r.F < 1 || r.K < 1 || r.K > 256 || r.num_nodes < 1) return fail(PL_EINVAL, "bad request sizes");
   if (!r.d_node && r.num_nodes != 1) return fail(PL_EINVAL, "num_nodes must be 1 without a node array");
   if ((long long)r.num_nodes * r.K > (1ll << 20) || r.M > ((size_t)1 << 30)) return fail(PL_EINVAL, "request too large");
-  if (r.gh_stride < r.M || r.bins_stride < r.M) return fail(PL_EINVAL, "strides must be >= M");
+  if ((!r.gh_bits && r.gh_stride < r.M) || r.bins_stride < r.M) return fail(PL_EINVAL, "strides must be >= M");
+  if (r.gh_bits != 0 && (r.gh_bits < 26 || r.gh_bits > 64)) return fail(PL_EINVAL, "gh_bits must be 0 or 26..64");
   if (!r.d_ctm || !r.d_bins || !r.h_sums || !r.h_counts) return fail(PL_EINVAL, "NULL buffer");
   if (reinterpret_cast<uintptr_t>(r.d_ctm) & 15u) return fail(PL_EINVAL, "d_ctm must be 16-byte aligned");
   if (!agg_supported(2 * r.key->L, r.key->agg_cfg.T)) return fail(PL_EINVAL, "key configuration not supported");

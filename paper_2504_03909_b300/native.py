@@ -65,7 +65,7 @@ class Request(C.Structure):
     _fields_ = [("key", C.c_void_p), ("d_ctm", C.c_void_p), ("gh_stride", C.c_size_t), ("M", C.c_size_t),
                 ("F", C.c_int), ("K", C.c_int), ("d_bins", C.c_void_p), ("bins_stride", C.c_size_t),
                 ("d_node", C.c_void_p), ("num_nodes", C.c_int), ("h_sums", C.c_void_p), ("h_counts", C.c_void_p),
-                ("pack_bits", C.c_int)]
+                ("pack_bits", C.c_int), ("gh_bits", C.c_int)]
 
 
 SIGNATURES.update({

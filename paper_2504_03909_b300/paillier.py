@@ -221,16 +221,17 @@ class Server:
 
     def submit(self, key: Key, ctm: torch.Tensor, M: int, F: int, K: int, bins: torch.Tensor,
                node: torch.Tensor | None = None, num_nodes: int = 1, gh_stride: int | None = None,
-               bins_stride: int | None = None, pack_bits: int = 0):
+               bins_stride: int | None = None, pack_bits: int = 0, gh_bits: int = 0):
         """Queues a request over the first M samples / F features of resident
-        arrays; returns (ticket, host sums [num_nodes, F, K, 2] uint64 (pinned),
-        host counts [num_nodes, F, K] int32 (pinned))."""
+        arrays (ctm: g and h arrays gh_stride rows apart, or with gh_bits one
+        g/h-packed array); returns (ticket, host sums [num_nodes, F, K, 2]
+        uint64 (pinned), host counts [num_nodes, F, K] int32 (pinned))."""
         sums = torch.empty((num_nodes, F, K, 2), dtype=torch.int64).pin_memory()
         counts = torch.empty((num_nodes, F, K), dtype=torch.int32).pin_memory()
         req = native.Request(key.handle.value, _ptr(ctm), gh_stride if gh_stride is not None else M, M, F, K,
                              _ptr(bins), bins_stride if bins_stride is not None else M,
                              _ptr(node) if node is not None else None, num_nodes, sums.data_ptr(), counts.data_ptr(),
-                             pack_bits)
+                             pack_bits, gh_bits)
         t = C.c_uint64()
         call("pl_server_submit", self._h, C.byref(req), C.byref(t))
         self._keep[t.value] = (sums, counts, ctm, bins, node, key)
@@ -238,9 +239,10 @@ class Server:
 
     @staticmethod
     def request_bytes(key: Key, ctm: torch.Tensor, M: int, F: int, K: int, bins: torch.Tensor,
-                      node: torch.Tensor | None = None, num_nodes: int = 1) -> int:
+                      node: torch.Tensor | None = None, num_nodes: int = 1, pack_bits: int = 0,
+                      gh_bits: int = 0) -> int:
         req = native.Request(key.handle.value, _ptr(ctm), M, M, F, K, _ptr(bins), M,
-                             _ptr(node) if node is not None else None, num_nodes, 0, 0, 0)
+                             _ptr(node) if node is not None else None, num_nodes, 0, 0, pack_bits, gh_bits)
         b = C.c_size_t()
         call("pl_server_request_bytes", C.byref(req), C.byref(b))
         return b.value

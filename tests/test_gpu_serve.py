@@ -13,6 +13,7 @@ from paper_2504_03909_b300 import native, paillier as P, synth
 pytestmark = pytest.mark.gpu
 
 MFULL, FFULL = 3000, 6
+GH_BITS = 38
 
 
 def _dataset(n_bits, seed):
@@ -23,10 +24,13 @@ def _dataset(n_bits, seed):
     m = P.encode(torch.from_numpy(gh.reshape(-1)).cuda())
     ct = P.encrypt(key, m, P.to_limb_tensor(r))
     ctm = P.ct_prepare(key, ct.view(2, MFULL, -1))
+    # the same g/h values packed one plaintext per sample (B = 38 covers 3000 samples)
+    g_d, h_d = torch.from_numpy(gh[0].copy()).cuda(), torch.from_numpy(gh[1].copy()).cuda()
+    ctm_gh = P.ct_prepare(key, P.encrypt_gh(key, P.encode_gh(g_d, h_d, GH_BITS), P.to_limb_tensor(r[:MFULL])))
     bins = {K: torch.from_numpy(synth.gen_bins_uniform(FFULL, MFULL, K, seed + K)).cuda() for K in (8, 16)}
     node = torch.from_numpy(synth.gen_tree_levels(MFULL, 3, seed)[2]).cuda()
     P.sync()
-    return dict(key=key, ctm=ctm, bins=bins, node=node, m=m.cpu().numpy().view(np.uint64))
+    return dict(key=key, ctm=ctm, ctm_gh=ctm_gh, bins=bins, node=node, m=m.cpu().numpy().view(np.uint64))
 
 
 @pytest.fixture(scope="module")
@@ -93,6 +97,28 @@ def test_packed_requests_equal_unpacked(data):
         t2, s2, c2 = srv.submit(d["key"], d["ctm"], M, F, K, d["bins"][K], pack_bits=40, **kw)
         assert srv.wait(t1)[0] == native.REQ_DONE and srv.wait(t2)[0] == native.REQ_DONE
         assert torch.equal(s1, s2) and torch.equal(c1, c2)
+    srv.close()
+
+
+def test_gh_packed_requests_equal_unpacked(data):
+    """Requests over one g/h-packed ciphertext array (half the histogram
+    products and decryptions) give the sums of the two-array requests, with
+    and without ciphertext packing, mixed with unpacked requests."""
+    srv = P.Server(slots=4, hbm_budget=8 << 30)
+    for rq in REQUESTS[:4]:
+        nb, M, F, K, use_node = rq
+        d = data[nb]
+        node = d["node"] if use_node else None
+        kw = dict(node=node, num_nodes=4 if use_node else 1, bins_stride=MFULL)
+        t1, s1, c1 = srv.submit(d["key"], d["ctm"], M, F, K, d["bins"][K], gh_stride=MFULL, **kw)
+        t2, s2, c2 = srv.submit(d["key"], d["ctm_gh"], M, F, K, d["bins"][K], gh_bits=GH_BITS, **kw)
+        t3, s3, c3 = srv.submit(d["key"], d["ctm_gh"], M, F, K, d["bins"][K], gh_bits=GH_BITS, pack_bits=1, **kw)
+        for t in (t1, t2, t3):
+            assert srv.wait(t)[0] == native.REQ_DONE
+        assert torch.equal(s1, s2) and torch.equal(c1, c2)
+        assert torch.equal(s1, s3) and torch.equal(c1, c3)
+    with pytest.raises(native.PaillierError):
+        srv.submit(data[1024]["key"], data[1024]["ctm_gh"], 10, 1, 8, data[1024]["bins"][8], gh_bits=20)
     srv.close()
 
 
