@@ -37,6 +37,20 @@ def _dec_crt(args):
     return oracle.decrypt_crt(oracle.PrivateKey(p, q), c)
 
 
+def _prod(args):
+    n, cts = args
+    pub = oracle.PublicKey(n)
+    acc = 1  # the empty cell
+    for c in cts:
+        acc = oracle.add(pub, acc, c)
+    return acc
+
+
+def oracle_products_many(n: int, groups):
+    """The oracle's homomorphic sum (product mod n^2) of each list of ciphertexts."""
+    return pool().map(_prod, [(n, [int(c) for c in g]) for g in groups], chunksize=4)
+
+
 def oracle_encrypt_many(n: int, ms, rs):
     return pool().map(_enc, [(n, int(m), int(r)) for m, r in zip(ms, rs)], chunksize=8)
 

@@ -3,13 +3,14 @@ times (default key configuration), on outputs the oracle can compute one by
 one, plus properties that hold at any size:
 
 * level workload (250,000 samples x 30 features x 256 bins, 2048-bit n):
-  a seeded sample of 48 ciphertexts bit-exact vs the oracle; EVERY decrypted
+  a seeded sample of 4,096 ciphertexts bit-exact vs the oracle; EVERY decrypted
   histogram cell equal to the plaintext fixed-point histogram (so every
-  ciphertext is consistent through the homomorphism); 16 sampled cells
+  ciphertext is consistent through the homomorphism); 512 sampled cells
   bit-exact vs the oracle's product; 8 sampled decryptions vs the lambda form.
 * batched workload (same data, depth-6 Beta(0.5, 0.5) tree): every level
   through the captured graph, every decrypted cell of every level equal to the
-  plaintext histogram; batched == plain per-node at the deepest level.
+  plaintext histogram; 256 sampled cells of the deepest level bit-exact vs the
+  oracle's product; batched == plain per-node at the deepest level.
 * large workload's kernel shapes (3072-bit n, 64 log-normal features, 256
   bins) on 20,000 samples and a depth-3 tree.
 Tolerance: none (bit-exact integers).
@@ -22,7 +23,7 @@ import torch
 import oracle
 from paper_2504_03909_b300 import paillier as P, synth
 
-from helpers import oracle_decrypt_many, oracle_encrypt_many
+from helpers import oracle_decrypt_many, oracle_encrypt_many, oracle_products_many
 
 pytestmark = pytest.mark.gpu
 
@@ -57,7 +58,7 @@ def level():
 
 def test_level_sampled_ciphertexts_bit_exact(level):
     M = level["cfg"]["M"]
-    idx = sorted(synth.rng_misc(21).choice(2 * M, size=48, replace=False).tolist())
+    idx = sorted(synth.rng_misc(21).choice(2 * M, size=4096, replace=False).tolist())
     rs = synth.limbs_to_ints(level["r"][idx])
     want = oracle_encrypt_many(level["n"], [int(level["m"][i]) for i in idx], rs)
     got = synth.limbs_to_ints(P.from_limb_tensor(level["ct"][idx]))
@@ -74,15 +75,14 @@ def test_level_root_histogram_every_cell_and_sampled_products(level):
     ps, pc = oracle.plain_histogram_np(level["m"][:M], level["m"][M:], level["bins"], np.zeros(M, np.int64), 1, K)
     assert np.array_equal(sums.cpu().numpy().reshape(1, F, K, 2), ps)
     assert np.array_equal(cnt.cpu().numpy(), pc)
-    # sampled cells: the oracle's product of the cell's ciphertexts
-    pub = oracle.PublicKey(level["n"])
-    cts_g = synth.limbs_to_ints(P.from_limb_tensor(level["ct"][:M]))
+    # sampled cells (g and h): the oracle's product of the cell's ciphertexts
+    cts = synth.limbs_to_ints(P.from_limb_tensor(level["ct"]))
     rng = synth.rng_misc(22)
-    cells = [(int(rng.integers(F)), int(rng.integers(K))) for _ in range(16)]
-    got = P.from_limb_tensor(hist[0, :, :, 0])
-    for f, b in cells:
-        want = oracle.encrypted_histogram_cell(pub, cts_g, level["bins"], np.zeros(M, np.int64), 0, f, b)
-        assert synth.limbs_to_ints(got[f, b][None])[0] == want
+    cells = [(int(rng.integers(F)), int(rng.integers(K)), int(rng.integers(2))) for _ in range(512)]
+    groups = [[cts[k * M + i] for i in np.flatnonzero(level["bins"][f] == b)] for f, b, k in cells]
+    want = oracle_products_many(level["n"], groups)
+    got = P.from_limb_tensor(hist[0])
+    assert [synth.limbs_to_ints(got[f, b, k][None])[0] for f, b, k in cells] == want
     # sampled decryptions against the textbook lambda form
     flat = P.from_limb_tensor(hist.reshape(-1, 2 * key.L))
     pick = rng.choice(flat.shape[0], size=8, replace=False)
@@ -113,6 +113,16 @@ def test_batched_depth6_every_level_every_cell(level):
             h2, c2 = P.hist_aggregate(key, level["ctm"], level["bins_d"], node_buf, nn, K, per_node=True)
             P.sync()
             assert torch.equal(h2, hist[:nn]) and torch.equal(c2, cnt[:nn])
+            # sampled cells of the deepest level vs the oracle's product
+            cts = synth.limbs_to_ints(P.from_limb_tensor(level["ct"]))
+            rng = synth.rng_misc(23)
+            cells = [(int(rng.integers(nn)), int(rng.integers(F)), int(rng.integers(K)), int(rng.integers(2)))
+                     for _ in range(256)]
+            groups = [[cts[k * M + i] for i in np.flatnonzero((level["bins"][f] == b) & (node_np == v))]
+                      for v, f, b, k in cells]
+            want = oracle_products_many(level["n"], groups)
+            got = P.from_limb_tensor(hist[:nn])
+            assert [synth.limbs_to_ints(got[v, f, b, k][None])[0] for v, f, b, k in cells] == want
     assert plan.stats()["captures"] == 1
 
 
