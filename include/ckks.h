@@ -19,7 +19,9 @@
  * All randomness (s ternary, a uniform, e/e0/e1 small, v ternary) is given by
  * the caller.  Polynomials are [.. ][N] arrays of coefficients; ciphertexts
  * are [batch][2][N] uint64 (c0 then c1).  Device pointers, asynchronous on
- * `stream`; errors as in paillier.h.
+ * `stream`; errors as in paillier.h.  A context keeps one scratch area for its
+ * calls: calls on one context run on one stream (or one at a time); use one
+ * context per stream for concurrent work.
  */
 #ifndef PAILLIER_B300_CKKS_H
 #define PAILLIER_B300_CKKS_H

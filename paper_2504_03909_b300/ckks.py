@@ -25,8 +25,12 @@ class Context:
         self.slots = lib().ckks_slots(self._h)
 
     def __del__(self):
-        if getattr(self, "_h", None) and self._h.value:
-            lib().ckks_free(self._h)
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().ckks_free(h)
+            except Exception:  # interpreter shutdown: the library may already be gone
+                pass
             self._h = C.c_void_p()
 
     def set_cluster_limit(self, max_batch: int) -> None:

@@ -2,7 +2,7 @@
 // decryption (Sec. III.B: the active party encrypts g/h and decrypts the
 // returned histograms; Sec. III.C: one single-number encryption per g and h).
 //
-// Both encryption and decryption are dominated by one batched fixed-window
+// Both encryption and decryption are dominated by one batched sliding-window
 // exponentiation in the two CRT halves (mod p^2 and mod q^2, L limbs each),
 // run by k_modexp with T lanes per instance.  The once-per-item steps around
 // it (CRT recombination, exact division L_p) are one thread per item.
@@ -109,7 +109,7 @@ PL_DEV void window_exp(uint32_t (&acc)[S], const uint32_t (&n)[S], uint32_t np, 
 
 // Batched exponentiation in the CRT halves.  Instance (h, i): half h (prime
 // x = p or q), item i.  A warp takes 32/T consecutive items of one half, so the
-// exponent digits are warp-uniform.
+// exponent schedules are warp-uniform.
 //   ENC: y[h][i] = (1 + m_i n) r_i^n mod x^2          (in = r [count][L])
 //        with r^n mod x^2 = ((r mod x)^(x' mod (x - 1)) mod x)^x mod x^2, x' the
 //        other prime: Fermat gives r^x' = r^(x' mod (x-1)) mod x, and z^x mod x^2
@@ -588,7 +588,7 @@ extern "C" pl_status paillier_decrypt_u64_noalloc(const pl_key* key, const uint3
   if (rc) return rc;
   const int L = key->L;
   const int T = key->dec_cfg.T;
-  // schedules of p - 1 and q - 1 at the fixed window, built on the stack
+  // schedules of p - 1 and q - 1 at this path's window width, built on the stack
   ModexpParams P;
   std::memset(&P, 0, sizeof(P));
   for (int h = 0; h < 2; ++h) {

@@ -1,6 +1,6 @@
 // Key generation, import/export and the per-key precomputation: Montgomery
 // constants of n^2, p^2, q^2, the CRT constants of encryption and of
-// decryption (Paillier 1999, Sec. 7), and the exponent window digits.
+// decryption (Paillier 1999, Sec. 7), and the sliding-window exponentiation schedules.
 #include <cstring>
 
 #include "internal.h"
