@@ -23,6 +23,12 @@ extern "C" {
 int paillier_test_mont_mul(int limbs, int lanes, const uint32_t* h_N, const uint32_t* d_a,
                            const uint32_t* d_b, size_t count, uint32_t* d_out, void* stream);
 
+/* Checked builds only (build.py --checked): launches one thread that reports
+ * a failed bounds check at `site` (0..30) without touching any memory, so
+ * that a test can see the report travel to paillier_sync (PL_EDEVICE, the
+ * word then cleared).  Returns PL_EINVAL (1) in the normal build. */
+int paillier_test_bounds_report(int site, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

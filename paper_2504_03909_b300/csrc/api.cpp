@@ -6,9 +6,32 @@
 #include <mutex>
 
 #include "internal.h"
+#include "check.cuh"
 #include "../../include/paillier_pack.h"
 
+#include <cstdio>
+#include <vector>
+
 namespace pl {
+
+#ifdef PL_CHECKED
+// the bounds words of every translation unit (registered at load time)
+static std::vector<int (*)()>& bounds_readers() {
+  static std::vector<int (*)()> v;
+  return v;
+}
+static std::mutex g_bounds_mu;
+void register_bounds_reader(int (*read_and_clear)()) {
+  std::lock_guard<std::mutex> lock(g_bounds_mu);
+  bounds_readers().push_back(read_and_clear);
+}
+static int read_all_bounds() {
+  std::lock_guard<std::mutex> lock(g_bounds_mu);
+  int v = 0;
+  for (auto fn : bounds_readers()) v |= fn();
+  return v;
+}
+#endif
 
 namespace {
 thread_local std::string g_err;
@@ -188,6 +211,16 @@ pl_status paillier_sync(void* stream, int* device_status) {
   if (device_status) *device_status = 0;
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+#ifdef PL_CHECKED
+  {
+    const int b = read_all_bounds();
+    if (b) {
+      char msg[96];
+      std::snprintf(msg, sizeof msg, "bounds check failed (sites 0x%x)", b);
+      return fail(PL_EDEVICE, msg);
+    }
+  }
+#endif
   int* sw = current_status();
   if (!sw) return fail(PL_ECUDA, "status word unavailable");
   int v = 0;

@@ -16,6 +16,7 @@
 // keys does not change any output bit.
 #include <cuda_runtime.h>
 
+#include "check.cuh"
 #include "internal.h"
 #include "mp.cuh"
 
@@ -61,7 +62,7 @@ __global__ void k_hist_scatter(const uint8_t* __restrict__ bins, size_t bstride,
     const int key = hist_key(node[i], bins[(size_t)f * bstride + i], K, num_nodes, only_node, status);
     if (key >= 0) {
       const int pos = off[(size_t)f * (NK + 1) + key] + atomicAdd(&cursor[(size_t)f * NK + key], 1);
-      idx[(size_t)f * M + pos] = (int)i;
+      if (PL_BOUNDS(pos >= 0 && (size_t)pos < M, kBoundsScatter)) idx[(size_t)f * M + pos] = (int)i;
     }
   }
 }
@@ -218,12 +219,14 @@ __global__ void __launch_bounds__(kBlock) k_seg_product(const __grid_constant__ 
       ids = idx + (size_t)f * M + j0;
     }
     const int maxlen = __reduce_max_sync(kFull, len);
-    if (len > 0) load_slice<S>(a, src + (size_t)ids[0] * NL, k);
+    // a sample id outside [0, M) (checked builds) reads sample 0 instead
+    auto sample = [&](int j) { const int id = ids[j]; return PL_BOUNDS(id >= 0 && (size_t)id < M, kBoundsSample) ? id : 0; };
+    if (len > 0) load_slice<S>(a, src + (size_t)sample(0) * NL, k);
     for (int j = 1; j < maxlen; ++j) {
       const bool act = j < len;
       const unsigned mask = __ballot_sync(kFull, act);
       if (act) {
-        load_slice<S>(t, src + (size_t)ids[j] * NL, k);
+        load_slice<S>(t, src + (size_t)sample(j) * NL, k);
         __syncwarp(mask);
         stage<S>(bs, st, t, k);
         __syncwarp(mask);
@@ -273,12 +276,15 @@ __global__ void __launch_bounds__(kBlock) k_combine(const __grid_constant__ N2Co
       first = featoff[f] + co[key];
     }
     const int maxn = __reduce_max_sync(kFull, nch);
-    if (nch > 0) load_slice_rw<S>(a, partial + ((size_t)first * ngh + gh) * NL, k);
+    const int nchunks = featoff[F];
+    // a chunk outside the work list (checked builds) reads chunk 0 instead
+    auto chunk = [&](int j) { return PL_BOUNDS(first + j < nchunks, kBoundsChunk) ? first + j : 0; };
+    if (nch > 0) load_slice_rw<S>(a, partial + ((size_t)chunk(0) * ngh + gh) * NL, k);
     for (int j = 1; j < maxn; ++j) {
       const bool act = j < nch;
       const unsigned mask = __ballot_sync(kFull, act);
       if (act) {
-        load_slice_rw<S>(t, partial + ((size_t)(first + j) * ngh + gh) * NL, k);
+        load_slice_rw<S>(t, partial + ((size_t)chunk(j) * ngh + gh) * NL, k);
         __syncwarp(mask);
         stage<S>(bs, st, t, k);
         __syncwarp(mask);

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/ckks.h"
+#include "check.cuh"
 #include "internal.h"
 
 namespace {
@@ -358,7 +359,8 @@ __global__ void __launch_bounds__(kThreads)
   const size_t p = blockIdx.x;
   for (int j = threadIdx.x; j < n / 2; j += blockDim.x) w[j] = fftw[j];
   for (int j = threadIdx.x; j < n; j += blockDim.x)
-    z[brev(pos[j], log_m)] = make_double2(re[p * n + j], im[p * n + j]);
+    if (PL_BOUNDS(pos[j] >= 0 && pos[j] < n, pl::kBoundsSlot))
+      z[brev(pos[j], log_m)] = make_double2(re[p * n + j], im[p * n + j]);
   __syncthreads();
   fft_stages(z, w, log_m, -1.0);
   const double f = scale / n;
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   fft_stages(z, w, log_m, 1.0);
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const double2 v = z[pos[j]];
+    const double2 v = z[PL_BOUNDS(pos[j] >= 0 && pos[j] < n, pl::kBoundsSlot) ? pos[j] : 0];
     // inv = 1 / scale when scale is a power of two (the product is then exact
     // and equals the quotient), else 0
     re[p * n + j] = inv != 0.0 ? v.x * inv : v.x / scale;
@@ -463,7 +465,9 @@ template <typename E>
 __device__ void gather_block(cg::cluster_group& cl, E* dst, E* cyc, int r, int logM) {
   for (int v = threadIdx.x; v < (1 << logM); v += blockDim.x) {
     const int idx = (r << logM) + v;
-    dst[v] = cl.map_shared_rank(cyc, idx & (kCl - 1))[idx >> kClLog];
+    const int src = idx & (kCl - 1), li = idx >> kClLog;
+    if (PL_BOUNDS(src < (int)cl.num_blocks() && li < (1 << logM), pl::kBoundsCluster))
+      dst[v] = cl.map_shared_rank(cyc, src)[li];
   }
 }
 
@@ -473,7 +477,9 @@ template <typename E>
 __device__ void gather_cyclic(cg::cluster_group& cl, E* dst, E* blk, int r, int logM) {
   for (int u = threadIdx.x; u < (1 << logM); u += blockDim.x) {
     const int idx = r + (u << kClLog);
-    dst[u] = cl.map_shared_rank(blk, idx >> logM)[idx & ((1 << logM) - 1)];
+    const int src = idx >> logM;
+    if (PL_BOUNDS(src < (int)cl.num_blocks(), pl::kBoundsCluster))
+      dst[u] = cl.map_shared_rank(blk, src)[idx & ((1 << logM) - 1)];
   }
 }
 
@@ -658,7 +664,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClFftThreads)
   double2 *blk = z, *cyc = z + M, *w = z + 2 * M;
   for (int j = threadIdx.x; j < n / 2; j += blockDim.x) w[j] = fftw[j];
   for (int v = threadIdx.x; v < M; v += blockDim.x) {  // bit-reversed load: Y[t] = z_j at t = pos_j
-    const int j = invpos[brev((r << logM) + v, log_m)];
+    int j = invpos[brev((r << logM) + v, log_m)];
+    if (!PL_BOUNDS(j >= 0 && j < n, pl::kBoundsSlot)) j = 0;
     blk[v] = make_double2(re[p * n + j], im[p * n + j]);
   }
   __syncthreads();
@@ -702,7 +709,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClFftThreads)
   cl.sync();
   fft_cyclic_stages(cyc, w, r, logM, log_m, 1.0);
   for (int u = threadIdx.x; u < M; u += blockDim.x) {
-    const int j = invpos[r + (u << kClLog)];
+    int j = invpos[r + (u << kClLog)];
+    if (!PL_BOUNDS(j >= 0 && j < n, pl::kBoundsSlot)) continue;
     const double2 v = cyc[u];
     re[p * n + j] = inv != 0.0 ? v.x * inv : v.x / scale;
     im[p * n + j] = inv != 0.0 ? v.y * inv : v.y / scale;

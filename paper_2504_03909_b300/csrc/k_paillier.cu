@@ -10,6 +10,7 @@
 
 #include <cstring>
 
+#include "check.cuh"
 #include "internal.h"
 #include "mp.cuh"
 
@@ -87,15 +88,17 @@ PL_DEV void window_exp(uint32_t (&acc)[S], const uint32_t (&n)[S], uint32_t np, 
 #pragma unroll
     for (int j = 0; j < S; ++j) a[j] = t[j];
   }
-  // most significant window first
-  load_slice_rw<S>(a, tbl + (size_t)(op[0] >> 1) * NL, k);
+  // most significant window first; an entry past the table (checked builds)
+  // reads entry 0 instead
+  auto entry = [&](int v) { return PL_BOUNDS((v >> 1) < nent, kBoundsTable) ? (v >> 1) : 0; };
+  load_slice_rw<S>(a, tbl + (size_t)entry(op[0]) * NL, k);
   for (int i = 1; i < nop; ++i) {
     const int v = op[i];
     __syncwarp();
     if (v == 0) {
       stage<S>(bs, st, a, k);
     } else {
-      load_slice_rw<S>(t, tbl + (size_t)(v >> 1) * NL, k);
+      load_slice_rw<S>(t, tbl + (size_t)entry(v) * NL, k);
       stage<S>(bs, st, t, k);
     }
     __syncwarp();

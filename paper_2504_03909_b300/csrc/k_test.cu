@@ -4,6 +4,7 @@
 #include <cstring>
 
 #include "../../include/paillier_testing.h"
+#include "check.cuh"
 #include "internal.h"
 #include "mp.cuh"
 
@@ -75,4 +76,24 @@ extern "C" int paillier_test_mont_mul(int limbs, int lanes, const uint32_t* h_N,
   PL_CASE(128, 4) PL_CASE(128, 8) PL_CASE(192, 8) PL_CASE(192, 16)
 #undef PL_CASE
   return fail(PL_EINVAL, "no compiled kernel for this (limbs, lanes) pair");
+}
+
+#ifdef PL_CHECKED
+namespace {
+__global__ void k_bounds_report(int site) { PL_BOUNDS(false, site); }
+}  // namespace
+#endif
+
+extern "C" int paillier_test_bounds_report(int site, void* stream) {
+  using namespace pl;
+  clear_error();
+  if (site < 0 || site > 30) return fail(PL_EINVAL, "site must be 0..30");
+#ifdef PL_CHECKED
+  k_bounds_report<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(site);
+  PL_CUDA_TRY(cudaGetLastError());
+  return PL_OK;
+#else
+  (void)stream;
+  return fail(PL_EINVAL, "not a checked build");
+#endif
 }

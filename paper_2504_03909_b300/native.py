@@ -11,7 +11,9 @@ import os
 import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpaillier_b300.so")
+# PAILLIER_B300_LIB=checked loads the bounds-checked build (build.py --checked)
+LIB_PATH = os.path.join(HERE, "libpaillier_b300_checked.so" if os.environ.get("PAILLIER_B300_LIB") == "checked"
+                        else "libpaillier_b300.so")
 HEADER_DIR = os.path.join(os.path.dirname(HERE), "include")
 
 PL_OK, PL_EINVAL, PL_ENOMEM, PL_ECUDA, PL_ERANGE, PL_ETIMEDOUT, PL_EBUSY, PL_EDEVICE = range(8)
@@ -44,6 +46,7 @@ SIGNATURES = {
     "paillier_sync": (_i, [_vp, C.POINTER(_i)]),
     "paillier_last_error": (C.c_char_p, []),
     "paillier_test_mont_mul": (_i, [_i, _i, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "paillier_test_bounds_report": (_i, [_i, _vp]),
     "paillier_imad_peak": (_i, [_i, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
     "paillier_fp64_peak": (_i, [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
     "paillier_launch_count": (C.c_ulonglong, []),

@@ -19,6 +19,17 @@ def test_library_exports_every_declared_function():
     assert set(native.SIGNATURES) <= set(names)
 
 
+def test_checked_library_exports_the_same_functions():
+    """The bounds-checked build (build.py --checked) has the same ABI."""
+    import os
+    path = os.path.join(native.HERE, "libpaillier_b300_checked.so")
+    if not os.path.exists(path):
+        pytest.skip("checked library not built")
+    lib = C.CDLL(path)
+    missing = [n for n in native.header_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
 @pytest.mark.parametrize("n_bits", [1024, 2048])
 def test_keygen_is_valid_and_deterministic(n_bits):
     k1 = P.Key.generate(n_bits, 11)
