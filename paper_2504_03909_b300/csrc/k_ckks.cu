@@ -148,21 +148,22 @@ __device__ void ntt_fwd(u64* a, const u64* tw, const NttConst& C, int L) {
   }
 }
 
-// inverse transform of one or two polynomials (b may be NULL)
+// inverse transform of one or two polynomials (b may be NULL); the work items
+// of both polynomials are spread over the threads together
 __device__ void ntt_inv(u64* a, u64* b, const u64* itw, const NttConst& C, int L) {
   const int N = 1 << L;
+  const int two = b ? 1 : 0;  // log2 of the number of polynomials
   int lt = 0;
   for (; lt < L % 3; ++lt) {  // leading radix-2 stages (never the last one: L >= 4)
     const int h = N >> (lt + 1);
-    for (int k = threadIdx.x; k < N / 2; k += blockDim.x) {
+    for (int task = threadIdx.x; task < (N / 2) << two; task += blockDim.x) {
+      u64* p = (task >= N / 2) ? b : a;
+      const int k = task & (N / 2 - 1);
       const int i = k >> lt, idx = (i << (lt + 1)) + (k & ((1 << lt) - 1));
-      const u64 w = itw[h + i];
-      for (u64* p = a; p; p = (p == a ? b : nullptr)) {
-        u64 x = p[idx], y = p[idx + (1 << lt)];
-        gs_bfly(x, y, w, C);
-        p[idx] = x;
-        p[idx + (1 << lt)] = y;
-      }
+      u64 x = p[idx], y = p[idx + (1 << lt)];
+      gs_bfly(x, y, itw[h + i], C);
+      p[idx] = x;
+      p[idx + (1 << lt)] = y;
     }
     __syncthreads();
   }
@@ -170,30 +171,30 @@ __device__ void ntt_inv(u64* a, u64* b, const u64* itw, const NttConst& C, int L
     // distances t, 2t, 4t on e_k = 8t I + j + k t (k < 8, j < t)
     const int h1 = N >> (lt + 1), h2 = N >> (lt + 2), h3 = N >> (lt + 3);
     const bool last = (lt + 3 == L);
-    for (int g = threadIdx.x; g < N / 8; g += blockDim.x) {
+    for (int task = threadIdx.x; task < (N / 8) << two; task += blockDim.x) {
+      u64* p = (task >= N / 8) ? b : a;
+      const int g = task & (N / 8 - 1);
       const int I = g >> lt, base = (I << (lt + 3)) + (g & ((1 << lt) - 1));
       const u64 w1[4] = {itw[h1 + 4 * I], itw[h1 + 4 * I + 1], itw[h1 + 4 * I + 2], itw[h1 + 4 * I + 3]};
       const u64 w2a = itw[h2 + 2 * I], w2b = itw[h2 + 2 * I + 1], w3 = itw[h3 + I];
-      for (u64* p = a; p; p = (p == a ? b : nullptr)) {
-        u64 x[8];
+      u64 x[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) x[k] = p[base + (k << lt)];
+      for (int k = 0; k < 8; ++k) x[k] = p[base + (k << lt)];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) gs_bfly(x[2 * k], x[2 * k + 1], w1[k], C);
-        gs_bfly(x[0], x[2], w2a, C);
-        gs_bfly(x[1], x[3], w2a, C);
-        gs_bfly(x[4], x[6], w2b, C);
-        gs_bfly(x[5], x[7], w2b, C);
-        if (last) {
+      for (int k = 0; k < 4; ++k) gs_bfly(x[2 * k], x[2 * k + 1], w1[k], C);
+      gs_bfly(x[0], x[2], w2a, C);
+      gs_bfly(x[1], x[3], w2a, C);
+      gs_bfly(x[4], x[6], w2b, C);
+      gs_bfly(x[5], x[7], w2b, C);
+      if (last) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) gs_last(x[k], x[k + 4], C);
-        } else {
+        for (int k = 0; k < 4; ++k) gs_last(x[k], x[k + 4], C);
+      } else {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) gs_bfly(x[k], x[k + 4], w3, C);
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) p[base + (k << lt)] = x[k];
+        for (int k = 0; k < 4; ++k) gs_bfly(x[k], x[k + 4], w3, C);
       }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) p[base + (k << lt)] = x[k];
     }
     __syncthreads();
   }
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(kThreads)
 namespace cg = cooperative_groups;
 
 constexpr int kCl = 8, kClLog = 3;
-constexpr int kClNttThreads = 128, kClFftThreads = 256;
+constexpr int kClNttThreads = 256, kClFftThreads = 256;
 
 // offset of the block-stage twiddles of distance 2^lt in a CTA's packed table
 // (t = 4, 2, 1 at 0, M/8, M/8 + M/4)
@@ -440,20 +441,20 @@ __device__ void ntt_fwd_tail(u64* a, const u64* tw, const NttConst& C, int logM)
   }
 }
 
-// inverse stages t = 1 .. kCl/2 on the block slice (one or two polynomials);
-// itw: packed like ntt_fwd_tail's
+// inverse stages t = 1 .. kCl/2 on the block slice (one or two polynomials,
+// spread over the threads together); itw: packed like ntt_fwd_tail's
 __device__ void ntt_inv_head(u64* a, u64* b, const u64* itw, const NttConst& C, int logM) {
   const int M = 1 << logM;
+  const int two = b ? 1 : 0;
   for (int lt = 0; lt < kClLog; ++lt) {
-    for (int k = threadIdx.x; k < M / 2; k += blockDim.x) {
+    for (int task = threadIdx.x; task < (M / 2) << two; task += blockDim.x) {
+      u64* p = (task >= M / 2) ? b : a;
+      const int k = task & (M / 2 - 1);
       const int i = k >> lt, idx = (i << (lt + 1)) + (k & ((1 << lt) - 1));
-      const u64 w = itw[tail_off(lt, M) + i];
-      for (u64* p = a; p; p = (p == a ? b : nullptr)) {
-        u64 x = p[idx], y = p[idx + (1 << lt)];
-        gs_bfly(x, y, w, C);
-        p[idx] = x;
-        p[idx + (1 << lt)] = y;
-      }
+      u64 x = p[idx], y = p[idx + (1 << lt)];
+      gs_bfly(x, y, itw[tail_off(lt, M) + i], C);
+      p[idx] = x;
+      p[idx + (1 << lt)] = y;
     }
     __syncthreads();
   }
