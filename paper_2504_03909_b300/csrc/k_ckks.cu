@@ -108,7 +108,7 @@ __device__ __forceinline__ void gs_last(u64& x, u64& y, const NttConst& C) {
 
 // L: log2 of the transformed length (C.log_n for a whole polynomial; less for
 // the slice of one CTA of a cluster, see below).
-__device__ void ntt_fwd(u64* a, const u64* tw, const NttConst& C, int L) {
+__device__ void ntt_fwd8(u64* a, const u64* tw, const NttConst& C, int L) {
   const int N = 1 << L;
   int lt = L - 1;  // log2 of the butterfly distance of the next stage
   for (; lt >= 2; lt -= 3) {
@@ -150,7 +150,7 @@ __device__ void ntt_fwd(u64* a, const u64* tw, const NttConst& C, int L) {
 
 // inverse transform of one or two polynomials (b may be NULL); the work items
 // of both polynomials are spread over the threads together
-__device__ void ntt_inv(u64* a, u64* b, const u64* itw, const NttConst& C, int L) {
+__device__ void ntt_inv8(u64* a, u64* b, const u64* itw, const NttConst& C, int L) {
   const int N = 1 << L;
   const int two = b ? 1 : 0;  // log2 of the number of polynomials
   int lt = 0;
@@ -198,6 +198,95 @@ __device__ void ntt_inv(u64* a, u64* b, const u64* itw, const NttConst& C, int L
     }
     __syncthreads();
   }
+}
+
+// Radix-4 forms (two stages per barrier, N/4 work items) for one polynomial
+// when the radix-8 forms would leave half of the CTA's threads idle; the one
+// stage left over (odd L) runs as a radix-2 stage: last for the forward
+// transform, first for the inverse (so that N^-1 folds into a radix-4 stage).
+__device__ void ntt_fwd4(u64* a, const u64* tw, const NttConst& C, int L) {
+  const int N = 1 << L;
+  int lt = L - 1;
+  for (; lt >= 1; lt -= 2) {
+    // distances t, t/2 on e_k = 2t i + j + k t/2 (k < 4, j < t/2)
+    const int m = N >> (lt + 1), q2 = lt - 1;
+    for (int g = threadIdx.x; g < N / 4; g += blockDim.x) {
+      const int i = g >> q2, base = (i << (lt + 1)) + (g & ((1 << q2) - 1));
+      u64 x0 = a[base], x1 = a[base + (1 << q2)], x2 = a[base + (2 << q2)], x3 = a[base + (3 << q2)];
+      const u64 w1 = tw[m + i];
+      ct_bfly(x0, x2, w1, C);
+      ct_bfly(x1, x3, w1, C);
+      ct_bfly(x0, x1, tw[2 * m + 2 * i], C);
+      ct_bfly(x2, x3, tw[2 * m + 2 * i + 1], C);
+      a[base] = x0;
+      a[base + (1 << q2)] = x1;
+      a[base + (2 << q2)] = x2;
+      a[base + (3 << q2)] = x3;
+    }
+    __syncthreads();
+  }
+  if (lt == 0) {
+    for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
+      u64 x = a[2 * b], y = a[2 * b + 1];
+      ct_bfly(x, y, tw[N / 2 + b], C);
+      a[2 * b] = x;
+      a[2 * b + 1] = y;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void ntt_inv4(u64* a, const u64* itw, const NttConst& C, int L) {
+  const int N = 1 << L;
+  int lt = 0;
+  if (L & 1) {
+    for (int k = threadIdx.x; k < N / 2; k += blockDim.x) {
+      u64 x = a[2 * k], y = a[2 * k + 1];
+      gs_bfly(x, y, itw[N / 2 + k], C);
+      a[2 * k] = x;
+      a[2 * k + 1] = y;
+    }
+    __syncthreads();
+    lt = 1;
+  }
+  for (; lt < L; lt += 2) {
+    // distances t, 2t on e_k = 4t I + j + k t (k < 4, j < t)
+    const int h1 = N >> (lt + 1), h2 = N >> (lt + 2);
+    const bool last = (lt + 2 == L);
+    for (int g = threadIdx.x; g < N / 4; g += blockDim.x) {
+      const int I = g >> lt, base = (I << (lt + 2)) + (g & ((1 << lt) - 1));
+      u64 x0 = a[base], x1 = a[base + (1 << lt)], x2 = a[base + (2 << lt)], x3 = a[base + (3 << lt)];
+      gs_bfly(x0, x1, itw[h1 + 2 * I], C);
+      gs_bfly(x2, x3, itw[h1 + 2 * I + 1], C);
+      if (last) {
+        gs_last(x0, x2, C);
+        gs_last(x1, x3, C);
+      } else {
+        const u64 w2 = itw[h2 + I];
+        gs_bfly(x0, x2, w2, C);
+        gs_bfly(x1, x3, w2, C);
+      }
+      a[base] = x0;
+      a[base + (1 << lt)] = x1;
+      a[base + (2 << lt)] = x2;
+      a[base + (3 << lt)] = x3;
+    }
+    __syncthreads();
+  }
+}
+
+// Dispatch: radix-8 unless it would leave half of the threads idle.
+__device__ __forceinline__ void ntt_fwd(u64* a, const u64* tw, const NttConst& C, int L) {
+  if ((int)blockDim.x >= (1 << L) / 4 && L >= 2)
+    ntt_fwd4(a, tw, C, L);
+  else
+    ntt_fwd8(a, tw, C, L);
+}
+__device__ __forceinline__ void ntt_inv(u64* a, u64* b, const u64* itw, const NttConst& C, int L) {
+  if (!b && (int)blockDim.x >= (1 << L) / 4 && L >= 2)
+    ntt_inv4(a, itw, C, L);
+  else
+    ntt_inv8(a, b, itw, C, L);
 }
 
 __device__ __forceinline__ u64 to_q(u64 x, u64) { return x; }  // already in [0, q)
