@@ -276,9 +276,8 @@ __global__ void __launch_bounds__(kBlock) k_combine(const __grid_constant__ N2Co
       first = featoff[f] + co[key];
     }
     const int maxn = __reduce_max_sync(kFull, nch);
-    const int nchunks = featoff[F];
     // a chunk outside the work list (checked builds) reads chunk 0 instead
-    auto chunk = [&](int j) { return PL_BOUNDS(first + j < nchunks, kBoundsChunk) ? first + j : 0; };
+    auto chunk = [&](int j) { return PL_BOUNDS(first + j < featoff[F], kBoundsChunk) ? first + j : 0; };
     if (nch > 0) load_slice_rw<S>(a, partial + ((size_t)chunk(0) * ngh + gh) * NL, k);
     for (int j = 1; j < maxn; ++j) {
       const bool act = j < nch;

@@ -52,9 +52,17 @@ PL_DEV uint32_t carry_out() { uint32_t c; asm volatile("addc.u32 %0, 0, 0;" : "=
 PL_DEV void sub_cc(uint32_t& d, uint32_t a) { asm volatile("sub.cc.u32 %0, %0, %1;" : "+r"(d) : "r"(a)); }
 PL_DEV void subc_cc(uint32_t& d, uint32_t a) { asm volatile("subc.cc.u32 %0, %0, %1;" : "+r"(d) : "r"(a)); }
 // sets the carry flag to c (0 or 1)
-PL_DEV void set_carry(uint32_t c) { uint32_t z; asm volatile("add.cc.u32 %0, %1, 0xffffffff;" : "=r"(z) : "r"(c)); }
+PL_DEV void set_carry(uint32_t c) {
+  uint32_t z;  // only the carry flag is wanted
+  asm volatile("add.cc.u32 %0, %1, 0xffffffff;" : "=r"(z) : "r"(c));
+  (void)z;
+}
 // sets the borrow flag to b (0 or 1)
-PL_DEV void set_borrow(uint32_t b) { uint32_t z; asm volatile("sub.cc.u32 %0, 0, %1;" : "=r"(z) : "r"(b)); }
+PL_DEV void set_borrow(uint32_t b) {
+  uint32_t z;  // only the borrow flag is wanted
+  asm volatile("sub.cc.u32 %0, 0, %1;" : "=r"(z) : "r"(b));
+  (void)z;
+}
 // borrow flag of the chain as 0/1
 PL_DEV uint32_t borrow_out() { uint32_t c; asm volatile("subc.u32 %0, 0, 0;" : "=r"(c)); return c & 1u; }
 
