@@ -81,7 +81,7 @@ def test_keygen_bit_exact(log_n):
     assert _u64(b) == ock.keygen(s, a, e, q)
 
 
-@pytest.mark.parametrize("log_n,batch", [(4, 3), (10, 3), (13, 2)])
+@pytest.mark.parametrize("log_n,batch", [(4, 3), (10, 3), (11, 2), (12, 2), (13, 2)])
 def test_encrypt_sum_decrypt_bit_exact(log_n, batch):
     N = 1 << log_n
     q = synth.ckks_prime(log_n)

@@ -66,12 +66,12 @@ def test_overflowing_slot_is_reported(cells):
 
 # ---- g/h packing: one plaintext per sample -----------------------------------
 
-@pytest.fixture(scope="module", params=[1024, 2048])
+@pytest.fixture(scope="module", params=[1024, 2048, 3072])
 def gh_case(request):
     n_bits = request.param
     p, q = synth.gen_primes(n_bits, 7)
     key = P.Key.from_primes(n_bits, p, q)
-    M, F, K, nodes = 3000, 5, 16, 3
+    M, F, K, nodes = (3000 if n_bits < 3072 else 800), 5, 16, 3
     gh = synth.gen_gh(M, 7)
     bins = synth.gen_bins_uniform(F, M, K, 7)
     node = synth.rng_misc(70).integers(-1, nodes, size=M).astype(np.int32)

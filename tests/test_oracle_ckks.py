@@ -75,3 +75,22 @@ def test_encrypt_decrypt_and_addition():
         tot = ckks.add(tot, c, q)
     got = ckks.decode(ckks.centre(ckks.decrypt(tot, s, q), q), N, scale)
     assert np.allclose(got, sum(zs), atol=3 * (N * 0.5 + 19 * (2 * N + 1)) * N / scale)
+
+
+def test_decoding_satisfies_parseval():
+    """For a real polynomial m, the slot values are half of the evaluations at
+    the primitive 2N-th roots (the other half are their conjugates), and the
+    twisted DFT preserves energy: sum_j |m(zeta_j)|^2 = (N / 2) sum_k m_k^2.
+    An identity of the mathematics, independent of the decoder's sums."""
+    for N in (16, 256):
+        rng = synth.rng_misc(44 + N)
+        m = rng.integers(-1000, 1000, size=N)
+        z = ckks.decode(m, N, 1.0)
+        assert len(z) == N // 2
+        lhs = float(np.sum(np.abs(z) ** 2))
+        rhs = N / 2 * float(np.sum(m.astype(np.float64) ** 2))
+        assert abs(lhs - rhs) <= 1e-9 * rhs
+        # the slot roots are distinct primitive 2N-th roots, no two conjugate
+        r = ckks.roots(N)
+        assert len(set(r)) == N // 2 and all(x % 2 == 1 for x in r)
+        assert not any((2 * N - x) in set(r) for x in r)
