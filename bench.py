@@ -975,10 +975,13 @@ def run_batched(args, cfg):
         else:
             P.decrypt_u64(key, cells, out=sums[:cells.shape[0]])
 
+    plan_gh = P.LevelPlan(key, M, F, K, maxn, gh=True) if B else None
+
     def level_hist(nn):
-        """This level's encrypted histograms of the nodes in node_buf."""
+        """This level's encrypted histograms of the nodes in node_buf (one
+        captured graph per plan, replayed for every level)."""
         if B:
-            P.hist_aggregate_gh(key, ctm1, bins_d, node_buf, nn, K, hist=hist_gh[:nn], count=cnt[:nn])
+            plan_gh.run(ctm1, bins_d, node_buf, nn, hist=hist_gh, count=cnt)
         else:
             plan.run(ctm.view(2, M, 2 * L), bins_d, node_buf, nn, hist=hist, count=cnt)
 
@@ -1095,7 +1098,7 @@ def run_batched(args, cfg):
         "pack_bits": pack_bits, "pack_slots": slots, "splits": args.splits, "subtract": bool(args.subtract),
         "gh_bits": B, "encryptions_per_tree": M if B else 2 * M,
         "cells_decoded_per_s": cells / ((prof["modexp_dec"] + prof["dec_crt"] + prof["unpack"] + prof["pack"]) * 1e-3),
-        "graph": plan.stats(),
+        "graph": (plan_gh if B else plan).stats(),
         "clocks": clk.summary(),
     }
     if rank == 0:

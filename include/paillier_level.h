@@ -32,6 +32,12 @@ typedef struct pl_level_plan pl_level_plan;
 pl_status paillier_level_plan_create(const pl_key* key, size_t M, int F, int K, int max_nodes,
                                      pl_level_plan** out);
 
+/* The same for ONE g/h-packed ciphertext array per sample (see paillier_pack.h):
+ * paillier_level_run then takes d_ctm [M][2L] and writes
+ * d_hist [num_nodes][F][K][2L], as paillier_hist_aggregate_gh. */
+pl_status paillier_level_plan_create_gh(const pl_key* key, size_t M, int F, int K, int max_nodes,
+                                        pl_level_plan** out);
+
 /* The encrypted histogram of one level, same layouts and results as
  * paillier_hist_aggregate:  d_ctm [2][M][2L], d_bins [F][M], d_node [M]
  * (values -1 .. num_nodes-1), d_hist [num_nodes][F][K][2][2L] out,

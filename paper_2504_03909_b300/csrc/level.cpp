@@ -11,6 +11,7 @@ struct pl_level_plan {
   const pl_key* key = nullptr;
   size_t M = 0;
   int F = 0, K = 0, max_nodes = 0, NK_max = 0;
+  int ngh = 2;  // ciphertext arrays per sample: 2 (g, h) or 1 (g/h packed)
   pl::AggCfg cfg;
   int device = 0;
   void* buf = nullptr;
@@ -41,7 +42,7 @@ struct pl_level_plan {
 
 extern "C" {
 
-pl_status paillier_level_plan_create(const pl_key* key, size_t M, int F, int K, int max_nodes, pl_level_plan** out) {
+static pl_status plan_create(const pl_key* key, size_t M, int F, int K, int max_nodes, int ngh, pl_level_plan** out) {
   using namespace pl;
   clear_error();
   if (!key || !out) return fail(PL_EINVAL, "NULL argument");
@@ -56,6 +57,7 @@ pl_status paillier_level_plan_create(const pl_key* key, size_t M, int F, int K, 
   p->K = K;
   p->max_nodes = max_nodes;
   p->NK_max = max_nodes * K;
+  p->ngh = ngh;
   p->cfg = key->agg_cfg;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaGetDevice"); }
@@ -67,6 +69,15 @@ pl_status paillier_level_plan_create(const pl_key* key, size_t M, int F, int K, 
   if (e != cudaSuccess) { p->cap = nullptr; delete p; return cuda_fail(e, "cudaStreamCreate"); }
   *out = p;
   return PL_OK;
+}
+
+pl_status paillier_level_plan_create(const pl_key* key, size_t M, int F, int K, int max_nodes, pl_level_plan** out) {
+  return plan_create(key, M, F, K, max_nodes, 2, out);
+}
+
+pl_status paillier_level_plan_create_gh(const pl_key* key, size_t M, int F, int K, int max_nodes,
+                                        pl_level_plan** out) {
+  return plan_create(key, M, F, K, max_nodes, 1, out);
 }
 
 pl_status paillier_level_run(pl_level_plan* plan, const uint32_t* d_ctm, const uint8_t* d_bins, const int32_t* d_node,
@@ -94,7 +105,7 @@ pl_status paillier_level_run(pl_level_plan* plan, const uint32_t* d_ctm, const u
     e = cudaStreamBeginCapture(plan->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     rc = hist_enqueue(plan->key, plan->cfg, plan->B, plan->NK_max, d_ctm, plan->M, plan->M, d_bins, plan->M,
-                      plan->F, plan->K, d_node, d_hist, d_count, st, plan->cap);
+                      plan->F, plan->K, d_node, d_hist, d_count, st, plan->cap, plan->ngh);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(plan->cap, &g);
     // kernels are counted when a replay launches them, not when they are captured

@@ -53,6 +53,7 @@ SIGNATURES = {
     "paillier_profile": (_i, [_i]),
     "paillier_profile_read": (_i, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "paillier_level_plan_create": (_i, [_vp, _sz, _i, _i, _i, C.POINTER(C.c_void_p)]),
+    "paillier_level_plan_create_gh": (_i, [_vp, _sz, _i, _i, _i, C.POINTER(C.c_void_p)]),
     "paillier_level_run": (_i, [_vp, _vp, _vp, _vp, _i, _vp, _vp, _vp]),
     "paillier_level_plan_stats": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)]),
     "paillier_level_plan_free": (None, [_vp]),

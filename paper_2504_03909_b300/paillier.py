@@ -173,20 +173,24 @@ def decrypt_u64(key: Key, ct: torch.Tensor, out: torch.Tensor | None = None, str
 
 class LevelPlan:
     """Batched tree-level path: one pass over all nodes of a level, captured
-    into a CUDA graph on the first run and replayed for later levels."""
+    into a CUDA graph on the first run and replayed for later levels.  gh=True:
+    one g/h-packed ciphertext array per sample ([M, 2L] in, [nodes, F, K, 2L] out)."""
 
-    def __init__(self, key: Key, M: int, F: int, K: int, max_nodes: int):
+    def __init__(self, key: Key, M: int, F: int, K: int, max_nodes: int, gh: bool = False):
         out = C.c_void_p()
-        call("paillier_level_plan_create", key.handle, M, F, K, max_nodes, C.byref(out))
+        fn = "paillier_level_plan_create_gh" if gh else "paillier_level_plan_create"
+        call(fn, key.handle, M, F, K, max_nodes, C.byref(out))
         self._h = out
-        self.key, self.M, self.F, self.K, self.max_nodes = key, M, F, K, max_nodes
+        self.key, self.M, self.F, self.K, self.max_nodes, self.gh = key, M, F, K, max_nodes, gh
 
     def run(self, ctm: torch.Tensor, bins: torch.Tensor, node: torch.Tensor, num_nodes: int,
             hist: torch.Tensor | None = None, count: torch.Tensor | None = None, stream=None):
         L = self.key.L
-        assert ctm.shape == (2, self.M, 2 * L) and bins.shape == (self.F, self.M) and node.numel() == self.M
+        want = (self.M, 2 * L) if self.gh else (2, self.M, 2 * L)
+        assert ctm.shape == want and bins.shape == (self.F, self.M) and node.numel() == self.M
         if hist is None:
-            hist = torch.empty((num_nodes, self.F, self.K, 2, 2 * L), dtype=torch.int32, device=ctm.device)
+            shape = (num_nodes, self.F, self.K, 2 * L) if self.gh else (num_nodes, self.F, self.K, 2, 2 * L)
+            hist = torch.empty(shape, dtype=torch.int32, device=ctm.device)
         if count is None:
             count = torch.empty((num_nodes, self.F, self.K), dtype=torch.int32, device=ctm.device)
         call("paillier_level_run", self._h, _ptr(ctm), _ptr(bins), _ptr(node), num_nodes, _ptr(hist), _ptr(count),

@@ -60,6 +60,38 @@ def test_level_graph_replay_matches_plain_per_node_and_oracle(tree):
     assert st["captures"] == 1 and st["replays"] == len(tree["levels"]) and st["kernels"] >= 6
 
 
+def test_gh_level_plan_matches_direct_and_oracle(tree):
+    """The plan over one g/h-packed array per sample: one capture, every level
+    equal to paillier_hist_aggregate_gh and, cell by cell, to the oracle's
+    product of the packed ciphertexts."""
+    key, M, F, K = tree["key"], tree["M"], tree["F"], tree["K"]
+    B = 37
+    gh = synth.gen_gh(M, 7)
+    r = synth.gen_r(tree["p"] * tree["q"], key.n_bits, M, 8, tree["p"], tree["q"])
+    g_d, h_d = torch.from_numpy(gh[0].copy()).cuda(), torch.from_numpy(gh[1].copy()).cuda()
+    ct1 = P.encrypt_gh(key, P.encode_gh(g_d, h_d, B), P.to_limb_tensor(r))
+    ctm1 = P.ct_prepare(key, ct1)
+    plan = P.LevelPlan(key, M, F, K, max_nodes=8, gh=True)
+    node_buf = torch.empty(M, dtype=torch.int32, device="cuda")
+    hist_buf = torch.empty((8, F, K, 2 * key.L), dtype=torch.int32, device="cuda")
+    cnt_buf = torch.empty((8, F, K), dtype=torch.int32, device="cuda")
+    pub = oracle.PublicKey(tree["p"] * tree["q"])
+    cts = synth.limbs_to_ints(P.from_limb_tensor(ct1))
+    for lvl, node_np in enumerate(tree["levels"]):
+        nn = 1 << lvl
+        node_buf.copy_(torch.from_numpy(node_np))
+        plan.run(ctm1, tree["bins"], node_buf, nn, hist=hist_buf, count=cnt_buf)
+        h_d, c_d = P.hist_aggregate_gh(key, ctm1, tree["bins"], node_buf, nn, K)
+        P.sync()
+        assert torch.equal(hist_buf[:nn], h_d) and torch.equal(cnt_buf[:nn], c_d), lvl
+        got = synth.limbs_to_ints(P.from_limb_tensor(hist_buf[:nn].reshape(-1, 2 * key.L)))
+        for v, f, b in [(0, 0, 0), (nn - 1, F - 1, K - 1), (nn // 2, 2, 5)]:
+            want = oracle.encrypted_histogram_cell(pub, cts, tree["bins_np"], node_np, v, f, b)
+            assert got[(v * F + f) * K + b] == want, (lvl, v, f, b)
+    st = plan.stats()
+    assert st["captures"] == 1 and st["replays"] == len(tree["levels"])
+
+
 def test_level_plan_recaptures_on_new_buffers(tree):
     key, M, F, K = tree["key"], tree["M"], tree["F"], tree["K"]
     plan = P.LevelPlan(key, M, F, K, max_nodes=2)
