@@ -62,6 +62,12 @@ void paillier_level_plan_free(pl_level_plan* plan);
 #define PL_OP_DECRYPT 1  /* exponentiation of decryption: lanes x window */
 #define PL_OP_HIST    2  /* histogram products mod n^2: lanes x tile */
 
+/* The configured lanes serve large calls.  A call on fewer items than the
+ * GPU holds at once (an exponentiation call on fewer than the resident
+ * instances; a packing call on fewer than two waves of packed ciphertexts)
+ * runs with twice the lanes per instance where that kernel exists: fewer,
+ * faster instances, shorter latency; the results are the same bits. */
+
 /* Current configuration of an op on this key: lanes per instance (limbs per
  * lane = limbs / lanes) and the window width (ops 0, 1) or tile (op 2). */
 pl_status paillier_get_config(const pl_key* key, int op, int* lanes, int* param);

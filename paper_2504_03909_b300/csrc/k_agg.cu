@@ -369,7 +369,7 @@ pl_status run_hist_products(const N2Const& P, const uint32_t* ctm, size_t M, siz
   return PL_OK;
 }
 
-#define PL_N2_CASES(X) X(64, 4) X(64, 8) X(128, 4) X(128, 8) X(192, 8) X(192, 16)
+#define PL_N2_CASES(X) X(64, 4) X(64, 8) X(64, 16) X(128, 4) X(128, 8) X(128, 16) X(192, 8) X(192, 16)
 
 pl_status dispatch_prepare(int NL, int T, const N2Const& P, const uint32_t* ct, size_t count, uint32_t* ctm,
                            cudaStream_t s) {
@@ -621,7 +621,12 @@ pl_status launch_pack(const pl_key* key, const uint32_t* ct, size_t count, int s
                       cudaStream_t s) {
   const size_t npacked = (count + slots - 1) / slots;
   if (!npacked) return PL_OK;
-  const int NL = 2 * key->L, T = key->agg_cfg.T;
+  const int NL = 2 * key->L;
+  // each packed ciphertext is one long chain of products: with few of them,
+  // twice the lanes per instance (where that kernel exists) shortens the chain
+  int T = key->agg_cfg.T;
+  const size_t resident = (size_t)sm_count() * 4 * (kBlock / T);
+  if (npacked < 2 * resident && agg_supported(NL, 2 * T)) T *= 2;
 #define PL_CASE(LL, TT) \
   if (NL == LL && T == TT) return run_pack<LL / TT, TT>(key->n2c, ct, count, slots, B, packed, npacked, s);
   PL_N2_CASES(PL_CASE)

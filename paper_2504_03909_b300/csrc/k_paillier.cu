@@ -440,9 +440,25 @@ pl_status launch_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t count,
 }
 
 // Shared by encrypt and decrypt: scratch = y [2][count][L] + window tables.
+// Lanes per instance for a call on `count` items: the configured lanes, or twice
+// as many when the call fills less than two waves of the GPU at the configured
+// lanes and that kernel exists (fewer, faster instances: shorter latency for
+// small calls; the results do not depend on it).
 template <bool DEC>
-static pl_status modexp_phase(pl_key* key, const ModexpCfg& cfg, const uint32_t* in, const uint64_t* msg,
+ModexpCfg lanes_for_count(int L, ModexpCfg cfg, size_t count) {
+  int grid = 0;
+  if (modexp_dispatch<DEC>(L, cfg.T, &grid, false, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr))
+    return cfg;
+  // 2 count instances (two CRT halves) against the resident instance slots
+  const size_t slots = (size_t)grid * (kBlock / cfg.T);
+  if (count < slots && modexp_supported(L, 2 * cfg.T)) cfg.T *= 2;
+  return cfg;
+}
+
+template <bool DEC>
+static pl_status modexp_phase(pl_key* key, ModexpCfg cfg, const uint32_t* in, const uint64_t* msg,
                               size_t count, uint32_t** y_out, cudaStream_t s, Scratch* scratch, int mw = 1) {
+  cfg = lanes_for_count<DEC>(key->L, cfg, count);
   const ModexpParams* P = key->modexp_params(DEC, cfg.w);
   if (!P) return fail(PL_EINVAL, "unsupported window width");
   const int L = key->L;
@@ -486,8 +502,8 @@ pl_status launch_encrypt(pl_key* key, const uint64_t* d_m, const uint32_t* d_r, 
 size_t decrypt_scratch_bytes(const pl_key* key, size_t count) {
   // the same carve as modexp_phase<true>: y [2][count][L] plus the window
   // tables of the grid that launch will use
-  const ModexpCfg cfg = key->dec_cfg;
   const int L = key->L;
+  const ModexpCfg cfg = lanes_for_count<true>(L, key->dec_cfg, count);
   int grid = 0;
   if (modexp_dispatch<true>(L, cfg.T, &grid, false, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr)) return 0;
   const size_t ipw = 32 / (size_t)cfg.T;
