@@ -369,7 +369,7 @@ pl_status run_hist_products(const N2Const& P, const uint32_t* ctm, size_t M, siz
   return PL_OK;
 }
 
-#define PL_N2_CASES(X) X(64, 4) X(64, 8) X(64, 16) X(128, 4) X(128, 8) X(128, 16) X(192, 8) X(192, 16)
+#define PL_N2_CASES(X) X(64, 4) X(64, 8) X(64, 16) X(128, 4) X(128, 8) X(128, 16) X(192, 8) X(192, 16) X(192, 32)
 
 pl_status dispatch_prepare(int NL, int T, const N2Const& P, const uint32_t* ct, size_t count, uint32_t* ctm,
                            cudaStream_t s) {

@@ -394,6 +394,9 @@ pl_status modexp_dispatch(int L, int T, int* grid_out, bool launch, const Modexp
   PL_CASE(64, 8)
   PL_CASE(96, 4)
   PL_CASE(96, 8)
+  if constexpr (DEC) {  // 6 limbs per lane: decryption only (encryption's first stage needs an even half)
+    PL_CASE(96, 16)
+  }
 #undef PL_CASE
   return fail(PL_EINVAL, "no exponentiation kernel for this (limbs, lanes) pair");
 }
@@ -451,7 +454,8 @@ ModexpCfg lanes_for_count(int L, ModexpCfg cfg, size_t count) {
     return cfg;
   // 2 count instances (two CRT halves) against the resident instance slots
   const size_t slots = (size_t)grid * (kBlock / cfg.T);
-  if (count < slots && modexp_supported(L, 2 * cfg.T)) cfg.T *= 2;
+  const bool have = modexp_supported(L, 2 * cfg.T) || (DEC && L == 96 && 2 * cfg.T == 16);
+  if (count < slots && have) cfg.T *= 2;
   return cfg;
 }
 
