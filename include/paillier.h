@@ -40,6 +40,8 @@
  *     message (thread-local, valid until the next call on the same thread).
  *   - Inputs must be canonical: 0 <= m < n, 1 <= r < n with gcd(r, n) = 1,
  *     ciphertexts in [1, n^2).  Outputs are canonical (fully reduced).
+ *     Encryption checks the randomness on the device: an r with
+ *     gcd(r, n) != 1 sets PL_EDEVICE in the status word.
  */
 #ifndef PAILLIER_B300_H
 #define PAILLIER_B300_H
@@ -110,7 +112,11 @@ pl_status paillier_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t coun
  * one single-number encryption).  d_m: [count] uint64 plaintexts (< n);
  * d_r: [count][L] randomness (uniform in Z_n^*, given by the caller);
  * d_ct: [count][2L] ciphertexts out.  Needs the private key: r^n is computed
- * mod p^2 and mod q^2 and recombined (the key holder's CRT split). */
+ * mod p^2 and mod q^2 and recombined (the key holder's CRT split).
+ * An r with r mod p = 0 or r mod q = 0 (gcd(r, n) != 1, r = 0 included) sets
+ * PL_EDEVICE in the status word; its row then holds a value that is not a
+ * unit mod n^2, the other rows are unaffected.  An r in [n, 2^(32L)) gives
+ * the encryption under r mod n, since r^n mod n^2 depends on r mod n only. */
 pl_status paillier_encrypt(const pl_key* key, const uint64_t* d_m, const uint32_t* d_r,
                            size_t count, uint32_t* d_ct, void* stream);
 

@@ -233,12 +233,13 @@ pl_status paillier_sync(void* stream, int* device_status) {
   if (device_status) *device_status = v;
   if (v & kStatusTimeout) return fail(PL_ETIMEDOUT, "a bounded device wait ran out");
   if (v & kStatusRange) return fail(PL_ERANGE, "a decrypted value does not fit 64 bits");
-  if (v & (kStatusBadBin | kStatusBadNode | kStatusEncode | kStatusCapacity)) {
+  if (v & (kStatusBadBin | kStatusBadNode | kStatusEncode | kStatusCapacity | kStatusNonUnit)) {
     std::string m = "device reported bad input:";
     if (v & kStatusBadBin) m += " bin >= K;";
     if (v & kStatusBadNode) m += " node >= num_nodes;";
     if (v & kStatusEncode) m += " value outside [-1, 2^15];";
     if (v & kStatusCapacity) m += " work list over capacity;";
+    if (v & kStatusNonUnit) m += " encryption randomness shares a factor with n;";
     return fail(PL_EDEVICE, m);
   }
   return PL_OK;
@@ -267,8 +268,9 @@ pl_status paillier_encrypt(const pl_key* key, const uint64_t* d_m, const uint32_
   if (!d_m || !d_r || !d_ct) return fail(PL_EINVAL, "NULL buffer");
   if (!aligned16(d_r) || !aligned16(d_ct)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
   if (count > (size_t)1 << 30) return fail(PL_EINVAL, "count too large");
-  if (!current_status()) return fail(PL_ECUDA, "no usable CUDA device");
-  return launch_encrypt(const_cast<pl_key*>(key), d_m, d_r, count, d_ct, static_cast<cudaStream_t>(stream));
+  int* st = current_status();
+  if (!st) return fail(PL_ECUDA, "no usable CUDA device");
+  return launch_encrypt(const_cast<pl_key*>(key), d_m, d_r, count, d_ct, st, static_cast<cudaStream_t>(stream));
 }
 
 pl_status paillier_ct_prepare(const pl_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_ctm,
@@ -395,9 +397,10 @@ pl_status paillier_encrypt_gh(const pl_key* key, const uint64_t* d_m, const uint
   if (!d_m || !d_r || !d_ct) return fail(PL_EINVAL, "NULL buffer");
   if (!aligned16(d_r) || !aligned16(d_ct)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
   if (count > (size_t)1 << 30) return fail(PL_EINVAL, "count too large");
-  if (!current_status()) return fail(PL_ECUDA, "no usable CUDA device");
-  return launch_encrypt(const_cast<pl_key*>(key), d_m, d_r, count, d_ct, static_cast<cudaStream_t>(stream), nullptr,
-                        2);
+  int* st = current_status();
+  if (!st) return fail(PL_ECUDA, "no usable CUDA device");
+  return launch_encrypt(const_cast<pl_key*>(key), d_m, d_r, count, d_ct, st, static_cast<cudaStream_t>(stream),
+                        nullptr, 2);
 }
 
 pl_status paillier_hist_aggregate_gh(const pl_key* key, const uint32_t* d_ctm, size_t M, const uint8_t* d_bins,

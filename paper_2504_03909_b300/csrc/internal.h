@@ -105,8 +105,9 @@ pl_status launch_encode(const float* d_v, size_t count, uint64_t* d_m, int* st, 
 pl_status launch_encode_gh(const float* d_g, const float* d_h, size_t count, int B, uint64_t* d_m, int* st,
                            cudaStream_t s);
 pl_status launch_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t count, double* d_out, cudaStream_t s);
+// st: device status word (kStatusNonUnit for randomness sharing a factor with n); may be null
 pl_status launch_encrypt(pl_key* key, const uint64_t* d_m, const uint32_t* d_r, size_t count, uint32_t* d_ct,
-                         cudaStream_t s, Scratch* scratch = nullptr, int mw = 1);
+                         int* st, cudaStream_t s, Scratch* scratch = nullptr, int mw = 1);
 pl_status launch_decrypt(pl_key* key, const uint32_t* d_ct, size_t count, void* d_out, bool u64, int* st,
                          cudaStream_t s, Scratch* scratch = nullptr);
 size_t decrypt_scratch_bytes(const pl_key* key, size_t count);

@@ -126,7 +126,7 @@ template <int S, int T, bool DEC>
 __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ ModexpParams P,
                                                    const uint32_t* __restrict__ in, const uint64_t* __restrict__ msg,
                                                    int mw, uint32_t* __restrict__ out, uint32_t* __restrict__ tbl,
-                                                   size_t count) {
+                                                   size_t count, int* status) {
   constexpr int NL = S * T;
   constexpr int IPW = 32 / T;
   extern __shared__ uint32_t smem[];
@@ -201,6 +201,15 @@ __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ Modex
         for (int j = 1; j < S2; ++j) addc_cc(tx[j], ax[j]);
         const uint32_t c = carry_out();
         normalize<S2, T>(tx, c, 0u, nx, k, kFull);
+        if (status != nullptr) {
+          // gcd(r, n) = 1 exactly when r mod p and r mod q are both non-zero
+          uint32_t any = 0;
+#pragma unroll
+          for (int j = 0; j < S2; ++j) any |= tx[j];
+          const unsigned nz = __ballot_sync(kFull, any != 0u);
+          const unsigned gm = (T == 32) ? kFull : ((1u << T) - 1u);
+          if (valid && k == 0 && ((nz >> (gw * T)) & gm) == 0u) atomicOr(status, kStatusNonUnit);
+        }
         window_exp<S2, T>(tx, nx, npx, P.op1[h], P.nop1[h], w, mytbl, bs, st, k);
         // leave Montgomery form mod x
         __syncwarp();
@@ -352,12 +361,12 @@ __global__ void __launch_bounds__(kBlock) k_dec_crt(const __grid_constant__ DecC
 
 template <int S, int T, bool DEC>
 pl_status run_modexp(const ModexpParams* P, const uint32_t* in, const uint64_t* msg, int mw, uint32_t* y,
-                     uint32_t* tbl, int grid, size_t count, cudaStream_t s) {
+                     uint32_t* tbl, int grid, size_t count, int* status, cudaStream_t s) {
   const int ipb = kBlock / T;
   const size_t smem = (size_t)S * T * ipb * sizeof(uint32_t);
   {
     ProfScope _ps((DEC ? "modexp_dec" : "modexp_enc"), s);
-    k_modexp<S, T, DEC><<<grid, kBlock, smem, s>>>(*P, in, msg, mw, y, tbl, count);
+    k_modexp<S, T, DEC><<<grid, kBlock, smem, s>>>(*P, in, msg, mw, y, tbl, count, status);
   }
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
@@ -381,11 +390,11 @@ int modexp_grid() {
 template <bool DEC>
 pl_status modexp_dispatch(int L, int T, int* grid_out, bool launch, const ModexpParams* P, const uint32_t* in,
                           const uint64_t* msg, uint32_t* y, uint32_t* tbl, size_t count, cudaStream_t s,
-                          int mw = 1) {
+                          int mw = 1, int* status = nullptr) {
 #define PL_CASE(LL, TT)                                                            \
   if (L == LL && T == TT) {                                                        \
     if (!launch) { *grid_out = modexp_grid<LL / TT, TT, DEC>(); return PL_OK; }     \
-    return run_modexp<LL / TT, TT, DEC>(P, in, msg, mw, y, tbl, *grid_out, count, s); \
+    return run_modexp<LL / TT, TT, DEC>(P, in, msg, mw, y, tbl, *grid_out, count, status, s); \
   }
   PL_CASE(32, 2)
   PL_CASE(32, 4)
@@ -461,7 +470,8 @@ ModexpCfg lanes_for_count(int L, ModexpCfg cfg, size_t count) {
 
 template <bool DEC>
 static pl_status modexp_phase(pl_key* key, ModexpCfg cfg, const uint32_t* in, const uint64_t* msg,
-                              size_t count, uint32_t** y_out, cudaStream_t s, Scratch* scratch, int mw = 1) {
+                              size_t count, uint32_t** y_out, cudaStream_t s, Scratch* scratch, int mw = 1,
+                              int* st = nullptr) {
   cfg = lanes_for_count<DEC>(key->L, cfg, count);
   const ModexpParams* P = key->modexp_params(DEC, cfg.w);
   if (!P) return fail(PL_EINVAL, "unsupported window width");
@@ -484,16 +494,16 @@ static pl_status modexp_phase(pl_key* key, ModexpCfg cfg, const uint32_t* in, co
   if (!base) return fail(PL_ENOMEM, "scratch allocation failed");
   uint32_t* y = reinterpret_cast<uint32_t*>(base + off_y);
   uint32_t* tbl = reinterpret_cast<uint32_t*>(base + off_t);
-  rc = modexp_dispatch<DEC>(L, cfg.T, &grid, true, P, in, msg, y, tbl, count, s, mw);
+  rc = modexp_dispatch<DEC>(L, cfg.T, &grid, true, P, in, msg, y, tbl, count, s, mw, st);
   *y_out = y;
   return rc;
 }
 
 pl_status launch_encrypt(pl_key* key, const uint64_t* d_m, const uint32_t* d_r, size_t count, uint32_t* d_ct,
-                         cudaStream_t s, Scratch* scratch, int mw) {
+                         int* st, cudaStream_t s, Scratch* scratch, int mw) {
   if (count == 0) return PL_OK;
   uint32_t* y = nullptr;
-  pl_status rc = modexp_phase<false>(key, key->enc_cfg, d_r, d_m, count, &y, s, scratch, mw);
+  pl_status rc = modexp_phase<false>(key, key->enc_cfg, d_r, d_m, count, &y, s, scratch, mw, st);
   if (rc) return rc;
   {
     ProfScope _ps("enc_crt", s);

@@ -148,7 +148,7 @@ pl_status paillier_autotune(pl_key* key, int op, const char* cache_path, void* s
     for (const Cand& c : cands) {
       (op == PL_OP_ENCRYPT ? key->enc_cfg : key->dec_cfg) = {c.lanes, c.param};
       auto run = [&] {
-        return op == PL_OP_ENCRYPT ? launch_encrypt(key, m, in, count, out, s)
+        return op == PL_OP_ENCRYPT ? launch_encrypt(key, m, in, count, out, st, s)
                                    : launch_decrypt(key, in, count, out, false, st, s);
       };
       rc = run();  // warm-up (also loads the kernel)

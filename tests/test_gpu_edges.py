@@ -1,6 +1,9 @@
 """Edge cases through the C ABI: a passive party holding only the public key,
-empty calls, values outside the encodable range, plaintexts >= 2^64, graph
-replays with fewer nodes, the largest bin count."""
+empty calls, values outside the encodable range, randomness that is not a unit
+of Z_n, plaintexts >= 2^64, graph replays with fewer nodes, the largest bin
+count."""
+
+from math import gcd
 
 import numpy as np
 import pytest
@@ -60,6 +63,30 @@ def test_encode_rejects_values_outside_range():
     got = m.cpu().numpy().view(np.uint64).tolist()
     assert got[:3] == [oracle.encode(0.5), oracle.encode(-1.0), oracle.encode(32768.0)]
     assert got[3:] == [0, 0, 0]
+
+
+def test_encrypt_flags_randomness_that_is_not_a_unit(env):
+    key, p, q = env["key"], env["p"], env["q"]
+    n = p * q
+    # r = 0, a multiple of p, a multiple of q; then units, one given as r + n
+    rs = [0, p, 3 * q, 5, 5 + n, 7]
+    ms = [11, 12, 13, 14, 15, 16]
+    assert 5 + n < 1 << 1024
+    ct = P.encrypt(key, torch.tensor(ms, dtype=torch.int64, device="cuda"),
+                   P.to_limb_tensor(synth.ints_to_limbs(rs, key.L)))
+    with pytest.raises(native.PaillierError) as e:
+        P.sync()
+    assert e.value.code == native.PL_EDEVICE and "factor with n" in str(e.value)
+    got = synth.limbs_to_ints(P.from_limb_tensor(ct))
+    pub = oracle.PublicKey(n)
+    # r^n mod n^2 depends on r mod n only, so r + n encrypts as r
+    assert got[3:] == [oracle.encrypt(pub, 14, 5), oracle.encrypt(pub, 15, 5), oracle.encrypt(pub, 16, 7)]
+    assert all(gcd(c, n) != 1 for c in got[:3])
+    P.sync()  # the word was cleared by the report
+    # units only: no report
+    P.encrypt(key, torch.tensor(ms[3:], dtype=torch.int64, device="cuda"),
+              P.to_limb_tensor(synth.ints_to_limbs(rs[3:], key.L)))
+    P.sync()
 
 
 def test_decrypt_u64_reports_wide_plaintexts(env):
