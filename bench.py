@@ -43,7 +43,7 @@ METRIC = "2048-bit Paillier enc/s & encrypted-hist ct-mults/s; p50/p99 request m
 
 # DRAM bytes (read + write) per encryption of the current k_modexp ENC kernel, from the ncu
 # capture summarised in profiles/k_modexp_enc_2048bit_small.md, keyed by (n_bits, window)
-TRAFFIC_PER_ENC = {(2048, 6): (328.43e6 + 329.61e6) / 16384}
+TRAFFIC_PER_ENC = {(2048, 6): (328.02e6 + 330.59e6) / 16384}
 
 
 # ----------------------------------------------------------------------------

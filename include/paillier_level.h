@@ -62,11 +62,12 @@ void paillier_level_plan_free(pl_level_plan* plan);
 #define PL_OP_DECRYPT 1  /* exponentiation of decryption: lanes x window */
 #define PL_OP_HIST    2  /* histogram products mod n^2: lanes x tile */
 
-/* The configured lanes serve large calls.  A call on fewer items than the
- * GPU holds at once (an exponentiation call on fewer than the resident
- * instances; a packing call on fewer than two waves of packed ciphertexts)
- * runs with twice the lanes per instance where that kernel exists: fewer,
- * faster instances, shorter latency; the results are the same bits. */
+/* The configured lanes serve large calls.  A call too small to keep the
+ * GPU's multiply-add pipes busy (at most about 1.5 warps per SM
+ * sub-partition at the configured lanes: about 3,000 encryptions or
+ * decryptions, or 2,000 packed ciphertexts, at 2048-bit) runs with twice
+ * the lanes per instance where that kernel exists: fewer, faster instances,
+ * shorter latency; the results are the same bits. */
 
 /* Current configuration of an op on this key: lanes per instance (limbs per
  * lane = limbs / lanes) and the window width (ops 0, 1) or tile (op 2). */

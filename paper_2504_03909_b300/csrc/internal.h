@@ -126,6 +126,16 @@ pl_status launch_hist(pl_key* key, const uint32_t* d_ctm, size_t M, size_t ghs, 
                       int32_t* d_count, bool per_node, int* st, cudaStream_t s, Scratch* scratch = nullptr,
                       int ngh = 2);
 int sm_count();
+// Whether a call of `instances` independent product chains at T lanes each
+// runs faster at 2T lanes.  Below about 1.5 warps per SM sub-partition the SMs
+// are latency-bound and an instance at 2T lanes finishes about 1.5-1.7x
+// sooner; above it the configured lanes have the higher throughput (measured
+// on B300 for encryption and decryption at 2048-bit and packing at 2048- and
+// 3072-bit: the crossover lies between 1.3 and 1.7 warps per sub-partition).
+inline bool double_lanes_pays(size_t instances, int T) {
+  const size_t warps = (instances * (size_t)T + 31) / 32;
+  return 2 * warps <= (size_t)12 * (size_t)sm_count();
+}
 pl_status launch_pack(const pl_key* key, const uint32_t* ct, size_t count, int slots, int B, uint32_t* packed,
                       cudaStream_t s);
 pl_status launch_unpack(const uint32_t* plain, int L, size_t count, int slots, int B, uint64_t* out, int* st,

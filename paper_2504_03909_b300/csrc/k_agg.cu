@@ -625,8 +625,7 @@ pl_status launch_pack(const pl_key* key, const uint32_t* ct, size_t count, int s
   // each packed ciphertext is one long chain of products: with few of them,
   // twice the lanes per instance (where that kernel exists) shortens the chain
   int T = key->agg_cfg.T;
-  const size_t resident = (size_t)sm_count() * 4 * (kBlock / T);
-  if (npacked < 2 * resident && agg_supported(NL, 2 * T)) T *= 2;
+  if (agg_supported(NL, 2 * T) && double_lanes_pays(npacked, T)) T *= 2;
 #define PL_CASE(LL, TT) \
   if (NL == LL && T == TT) return run_pack<LL / TT, TT>(key->n2c, ct, count, slots, B, packed, npacked, s);
   PL_N2_CASES(PL_CASE)

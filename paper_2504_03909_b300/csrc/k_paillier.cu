@@ -453,18 +453,14 @@ pl_status launch_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t count,
 
 // Shared by encrypt and decrypt: scratch = y [2][count][L] + window tables.
 // Lanes per instance for a call on `count` items: the configured lanes, or twice
-// as many when the call fills less than two waves of the GPU at the configured
-// lanes and that kernel exists (fewer, faster instances: shorter latency for
-// small calls; the results do not depend on it).
+// as many when the call is too small to keep the GPU's multiply-add pipes busy
+// and that kernel exists (fewer, faster instances: shorter latency for small
+// calls; the results do not depend on it).
 template <bool DEC>
 ModexpCfg lanes_for_count(int L, ModexpCfg cfg, size_t count) {
-  int grid = 0;
-  if (modexp_dispatch<DEC>(L, cfg.T, &grid, false, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr))
-    return cfg;
-  // 2 count instances (two CRT halves) against the resident instance slots
-  const size_t slots = (size_t)grid * (kBlock / cfg.T);
   const bool have = modexp_supported(L, 2 * cfg.T) || (DEC && L == 96 && 2 * cfg.T == 16);
-  if (count < slots && have) cfg.T *= 2;
+  // 2 count instances: the two CRT halves
+  if (have && double_lanes_pays(2 * count, cfg.T)) cfg.T *= 2;
   return cfg;
 }
 
