@@ -40,9 +40,12 @@ pl_status paillier_split_find(const uint64_t* d_sums, const int32_t* d_counts, i
  * with split (f, b) = (d_best_f[v], d_best_b[v]), f >= 0:
  * d_next[i] = 2 v + (d_bins[f * M + i] > b); d_next[i] = -1 if d_node[i] < 0 or
  * node v is a leaf.  (In the vertical setting the party owning feature f
- * applies its own split; here the parties are simulated on one device.) */
-pl_status paillier_split_apply(const uint8_t* d_bins, size_t M, const int32_t* d_node, const int32_t* d_best_f,
-                               const int32_t* d_best_b, int32_t* d_next, void* stream);
+ * applies its own split; here the parties are simulated on one device.)
+ *   d_bins [F][M]; d_node [M]; d_best_f, d_best_b [nodes]; d_next [M] out.
+ * A node id >= nodes or a split feature >= F writes -1 for that sample and
+ * sets PL_EDEVICE in the status word. */
+pl_status paillier_split_apply(const uint8_t* d_bins, size_t M, int F, const int32_t* d_node, int nodes,
+                               const int32_t* d_best_f, const int32_t* d_best_b, int32_t* d_next, void* stream);
 
 /* Histogram subtraction (XGBoost's trick; the paper does not use it): at a
  * level below the root only the smaller child of every split node needs an
@@ -55,7 +58,9 @@ pl_status paillier_split_apply(const uint8_t* d_bins, size_t M, const int32_t* d
  * writes d_small_node [M] = v for the samples of that child, -1 for all
  * others: a node array of parents.  nodes = number of parents.  d_small_right
  * [nodes] (out) = 1 if the smaller child is the right one.  The parent's split
- * (d_best_f, d_best_b) gives the child sizes from d_counts [nodes][F][K]. */
+ * (d_best_f, d_best_b) gives the child sizes from d_counts [nodes][F][K].
+ * A child id >= 2 nodes or a split feature >= F is skipped (-1, left) and
+ * sets PL_EDEVICE in the status word. */
 pl_status paillier_child_select(const int32_t* d_next, size_t M, const int32_t* d_counts, int nodes, int F, int K,
                                 const int32_t* d_best_f, const int32_t* d_best_b, int32_t* d_small_right,
                                 int32_t* d_small_node, void* stream);
@@ -65,7 +70,7 @@ pl_status paillier_child_select(const int32_t* d_next, size_t M, const int32_t* 
  * d_small_sums[v] and the other child gets d_parent_sums[v] - d_small_sums[v]
  * (and the same for counts).  Layouts [nodes][F][K][2] (sums, uint64) and
  * [nodes][F][K] (counts) for parents and small children; [2 nodes][F][K][2]
- * and [2 nodes][F][K] out. */
+ * and [2 nodes][F][K] out.  Any non-zero d_small_right[v] means "right". */
 pl_status paillier_child_subtract(const uint64_t* d_parent_sums, const int32_t* d_parent_counts,
                                   const uint64_t* d_small_sums, const int32_t* d_small_counts,
                                   const int32_t* d_small_right, int nodes, int F, int K, uint64_t* d_child_sums,
@@ -89,7 +94,9 @@ pl_status paillier_tree_decide(const uint8_t* d_bins_party, int F_party, int f_l
 
 /* Routing with the combined decisions: from the root, follow d_go_right of
  * each split node until a leaf (d_tree_f < 0) or `depth` levels; d_leaf[i] is
- * the level-order index of the node reached. */
+ * the level-order index of the node reached.  d_tree_f holds at least
+ * 2^depth - 1 nodes and d_go_right [2^depth - 1][M] (only the entries of
+ * split nodes are read; any non-zero byte means "right"). */
 pl_status paillier_tree_route(const uint8_t* d_go_right, size_t M, const int32_t* d_tree_f, int depth,
                               int32_t* d_leaf, void* stream);
 

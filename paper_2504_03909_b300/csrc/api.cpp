@@ -233,13 +233,14 @@ pl_status paillier_sync(void* stream, int* device_status) {
   if (device_status) *device_status = v;
   if (v & kStatusTimeout) return fail(PL_ETIMEDOUT, "a bounded device wait ran out");
   if (v & kStatusRange) return fail(PL_ERANGE, "a decrypted value does not fit 64 bits");
-  if (v & (kStatusBadBin | kStatusBadNode | kStatusEncode | kStatusCapacity | kStatusNonUnit)) {
+  if (v & (kStatusBadBin | kStatusBadNode | kStatusEncode | kStatusCapacity | kStatusNonUnit | kStatusBadSplit)) {
     std::string m = "device reported bad input:";
     if (v & kStatusBadBin) m += " bin >= K;";
     if (v & kStatusBadNode) m += " node >= num_nodes;";
     if (v & kStatusEncode) m += " value outside [-1, 2^15];";
     if (v & kStatusCapacity) m += " work list over capacity;";
     if (v & kStatusNonUnit) m += " encryption randomness shares a factor with n;";
+    if (v & kStatusBadSplit) m += " split feature >= F;";
     return fail(PL_EDEVICE, m);
   }
   return PL_OK;

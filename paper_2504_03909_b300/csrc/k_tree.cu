@@ -71,14 +71,20 @@ __global__ void __launch_bounds__(kSplitBlock) k_split_find(const uint64_t* __re
 }
 
 __global__ void k_split_apply(const uint8_t* __restrict__ bins, size_t M, const int32_t* __restrict__ node,
-                              const int32_t* __restrict__ best_f, const int32_t* __restrict__ best_b,
-                              int32_t* __restrict__ next) {
+                              int nodes, int F, const int32_t* __restrict__ best_f,
+                              const int32_t* __restrict__ best_b, int32_t* __restrict__ next, int* status) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
     const int v = node[i];
     int out = -1;
-    if (v >= 0) {
+    if (v >= nodes) {
+      atomicOr(status, kStatusBadNode);
+    } else if (v >= 0) {
       const int f = best_f[v];
-      if (f >= 0) out = 2 * v + (bins[(size_t)f * M + i] > (uint8_t)best_b[v] ? 1 : 0);
+      if (f >= F) {
+        atomicOr(status, kStatusBadSplit);
+      } else if (f >= 0) {
+        out = 2 * v + (bins[(size_t)f * M + i] > (uint8_t)best_b[v] ? 1 : 0);
+      }
     }
     next[i] = out;
   }
@@ -87,11 +93,12 @@ __global__ void k_split_apply(const uint8_t* __restrict__ bins, size_t M, const 
 // per parent: which child is smaller (counts of the split feature's bins)
 __global__ void k_child_sizes(const int32_t* __restrict__ counts, int nodes, int F, int K,
                               const int32_t* __restrict__ best_f, const int32_t* __restrict__ best_b,
-                              int32_t* __restrict__ small_right) {
+                              int32_t* __restrict__ small_right, int* status) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nodes) return;
   const int f = best_f[v];
-  if (f < 0) { small_right[v] = 0; return; }
+  if (f >= F) atomicOr(status, kStatusBadSplit);
+  if (f < 0 || f >= F) { small_right[v] = 0; return; }
   const int32_t* c = counts + ((size_t)v * F + f) * K;
   long long left = 0, right = 0;
   for (int b = 0; b < K; ++b) (b <= best_b[v] ? left : right) += c[b];
@@ -99,10 +106,12 @@ __global__ void k_child_sizes(const int32_t* __restrict__ counts, int nodes, int
 }
 
 __global__ void k_child_select(const int32_t* __restrict__ next, size_t M, const int32_t* __restrict__ small_right,
-                               int32_t* __restrict__ small_node) {
+                               int nodes, int32_t* __restrict__ small_node, int* status) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
     const int c = next[i];
-    small_node[i] = (c >= 0 && (c & 1) == small_right[c >> 1]) ? (c >> 1) : -1;
+    if (c >= 2 * nodes) atomicOr(status, kStatusBadNode);
+    const bool in = c >= 0 && c < 2 * nodes;
+    small_node[i] = (in && (c & 1) == small_right[c >> 1]) ? (c >> 1) : -1;
   }
 }
 
@@ -114,7 +123,7 @@ __global__ void k_child_subtract(const uint64_t* __restrict__ ps, const int32_t*
   const size_t total = (size_t)nodes * per_node;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
     const size_t v = i / per_node, cell = i % per_node;
-    const int sr = small_right[v];
+    const int sr = small_right[v] != 0 ? 1 : 0;
     const size_t small_child = 2 * v + sr, big_child = 2 * v + (1 - sr);
     for (int k = 0; k < 2; ++k) {
       const uint64_t s = ss[i * 2 + k];
@@ -145,7 +154,7 @@ __global__ void k_tree_route(const uint8_t* __restrict__ go_right, size_t M, con
     for (int l = 0; l < depth; ++l) {
       const int t = first + v;
       if (tf[t] < 0 || l == depth - 1) break;
-      v = 2 * v + go_right[(size_t)t * M + i];
+      v = 2 * v + (go_right[(size_t)t * M + i] != 0 ? 1 : 0);
       first = 2 * first + 1;
     }
     leaf[i] = first + v;
@@ -163,6 +172,13 @@ __global__ void k_leaf_weights(const uint64_t* __restrict__ sums, const int32_t*
   for (int b = 0; b < K; ++b) { Sg += s[2 * b]; Sh += s[2 * b + 1]; C += c[b]; }
   const double G = fx(Sg, C), H = fx(Sh, C);
   w[v] = -__ddiv_rn(G, __dadd_rn(H, lambda));
+}
+
+// the current device's status word (null without a usable device)
+int* tree_status() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  return status_word(dev);
 }
 
 }  // namespace
@@ -220,13 +236,15 @@ pl_status paillier_child_select(const int32_t* d_next, size_t M, const int32_t* 
   if (nodes < 1 || F < 1 || K < 1 || K > 256) return fail(PL_EINVAL, "bad sizes");
   if (!d_next || !d_counts || !d_best_f || !d_best_b || !d_small_right || !d_small_node)
     return fail(PL_EINVAL, "NULL buffer");
+  int* st = tree_status();
+  if (!st) return fail(PL_ECUDA, "no usable CUDA device");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_child_sizes<<<(nodes + 127) / 128, 128, 0, s>>>(d_counts, nodes, F, K, d_best_f, d_best_b, d_small_right);
+  k_child_sizes<<<(nodes + 127) / 128, 128, 0, s>>>(d_counts, nodes, F, K, d_best_f, d_best_b, d_small_right, st);
   note_launch();
   PL_CUDA_TRY(cudaGetLastError());
   if (M) {
     const int grid = (int)std::min<size_t>((M + 255) / 256, (size_t)sm_count() * 8);
-    k_child_select<<<grid, 256, 0, s>>>(d_next, M, d_small_right, d_small_node);
+    k_child_select<<<grid, 256, 0, s>>>(d_next, M, d_small_right, nodes, d_small_node, st);
     note_launch();
     PL_CUDA_TRY(cudaGetLastError());
   }
@@ -269,14 +287,18 @@ pl_status paillier_split_find(const uint64_t* d_sums, const int32_t* d_counts, i
   return PL_OK;
 }
 
-pl_status paillier_split_apply(const uint8_t* d_bins, size_t M, const int32_t* d_node, const int32_t* d_best_f,
-                               const int32_t* d_best_b, int32_t* d_next, void* stream) {
+pl_status paillier_split_apply(const uint8_t* d_bins, size_t M, int F, const int32_t* d_node, int nodes,
+                               const int32_t* d_best_f, const int32_t* d_best_b, int32_t* d_next, void* stream) {
   using namespace pl;
   clear_error();
+  if (F < 1 || nodes < 1) return fail(PL_EINVAL, "need F >= 1 and nodes >= 1");
   if (M == 0) return PL_OK;
   if (!d_bins || !d_node || !d_best_f || !d_best_b || !d_next) return fail(PL_EINVAL, "NULL buffer");
+  int* st = tree_status();
+  if (!st) return fail(PL_ECUDA, "no usable CUDA device");
   const int grid = (int)std::min<size_t>((M + 255) / 256, (size_t)sm_count() * 8);
-  k_split_apply<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_bins, M, d_node, d_best_f, d_best_b, d_next);
+  k_split_apply<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_bins, M, d_node, nodes, F, d_best_f, d_best_b,
+                                                                      d_next, st);
   note_launch();
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;

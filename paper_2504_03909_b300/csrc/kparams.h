@@ -22,6 +22,7 @@ constexpr int kStatusEncode = 8;       // value outside the encodable range
 constexpr int kStatusTimeout = 16;     // a bounded wait ran out
 constexpr int kStatusCapacity = 32;    // a work list was larger than its buffer
 constexpr int kStatusNonUnit = 64;     // encryption randomness r with gcd(r, n) != 1
+constexpr int kStatusBadSplit = 128;   // a split feature >= F
 
 // One half of the key holder's CRT split: arithmetic mod N = x^2 for the
 // prime x = p (or q), L limbs, R = 2^(32 L); and mod x itself, L/2 limbs,

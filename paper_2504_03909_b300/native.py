@@ -82,7 +82,7 @@ SIGNATURES.update({
     "paillier_decrypt_gh": (_i, [_vp, _vp, _sz, _i, _vp, _vp]),
     "paillier_decrypt_packed_gh": (_i, [_vp, _vp, _sz, _i, _vp, _vp]),
     "paillier_split_find": (_i, [_vp, _vp, _i, _i, _i, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp, _vp]),
-    "paillier_split_apply": (_i, [_vp, _sz, _vp, _vp, _vp, _vp, _vp]),
+    "paillier_split_apply": (_i, [_vp, _sz, _i, _vp, _i, _vp, _vp, _vp, _vp]),
     "paillier_tree_decide": (_i, [_vp, _i, _i, _sz, _vp, _vp, _i, _vp, _vp]),
     "paillier_tree_route": (_i, [_vp, _sz, _vp, _i, _vp, _vp]),
     "paillier_leaf_weights": (_i, [_vp, _vp, _i, _i, _i, C.c_double, _vp, _vp]),

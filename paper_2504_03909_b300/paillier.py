@@ -1,10 +1,12 @@
 """Python face of the C ABI, over torch device tensors.
 
-Every function here only checks shapes, takes ``data_ptr()`` and the current
+Every function here only checks its tensor arguments (device, contiguity,
+dtype, shape: the kernels trust them), takes ``data_ptr()`` and the current
 CUDA stream, and calls the native library; all arithmetic runs in the CUDA
-kernels.  Multi-precision arrays are held in int32 tensors whose bits are the
-uint32 limbs (little-endian limbs, one row per value); uint64 values are held
-in int64 tensors.
+kernels.  A bad argument raises ValueError before anything is launched.
+Multi-precision arrays are held in int32 tensors whose bits are the uint32
+limbs (little-endian limbs, one row per value); uint64 values are held in
+int64 tensors.
 """
 
 from __future__ import annotations
@@ -24,9 +26,32 @@ def _stream(stream=None) -> int:
     return stream.cuda_stream
 
 
-def _ptr(t: torch.Tensor) -> int:
-    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+def _ptr(t: torch.Tensor, name: str = "tensor", dtype=None, shape=None, numel=None, min_numel=None) -> int:
+    """data_ptr() of a tensor argument after the checks the kernels rely on: a
+    contiguous tensor on the current CUDA device, of the given dtype and shape
+    (or element count).  Raises ValueError (TypeError for a non-tensor)."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor, got {type(t).__name__}")
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: expected a tensor on the current CUDA device, got {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()}")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{name}: expected at least {min_numel} elements, got {t.numel()}")
     return t.data_ptr()
+
+
+def _rows(t: torch.Tensor, name: str, width: int) -> int:
+    """Rows of an int32 limb array [..., width]."""
+    if not isinstance(t, torch.Tensor) or t.dim() < 1 or t.shape[-1] != width:
+        raise ValueError(f"{name}: expected an array [..., {width}]")
+    return t.numel() // width
 
 
 def _limbs_from_int(x: int, limbs: int) -> np.ndarray:
@@ -96,18 +121,18 @@ class Key:
 
 def encode(v: torch.Tensor, stream=None) -> torch.Tensor:
     """Fixed-point plaintexts of float32 values (int64 tensor of uint64 bits)."""
-    assert v.dtype == torch.float32
+    pv = _ptr(v, "v", torch.float32)
     out = torch.empty(v.shape, dtype=torch.int64, device=v.device)
-    call("paillier_encode", _ptr(v), v.numel(), _ptr(out), _stream(stream))
+    call("paillier_encode", pv, v.numel(), _ptr(out, "out"), _stream(stream))
     return out
 
 
 def decode(s: torch.Tensor, cnt: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """Float64 values of fixed-point sums s (int64 bits) of cnt encoded values each."""
-    assert s.dtype == torch.int64 and cnt.dtype == torch.int32 and s.numel() == cnt.numel()
+    ps, pc = _ptr(s, "s", torch.int64), _ptr(cnt, "cnt", torch.int32, numel=s.numel())
     if out is None:
         out = torch.empty(s.shape, dtype=torch.float64, device=s.device)
-    call("paillier_decode", _ptr(s), _ptr(cnt), s.numel(), _ptr(out), _stream(stream))
+    call("paillier_decode", ps, pc, s.numel(), _ptr(out, "out", torch.float64, min_numel=s.numel()), _stream(stream))
     return out
 
 
@@ -115,20 +140,22 @@ def encrypt(key: Key, m: torch.Tensor, r: torch.Tensor, out: torch.Tensor | None
     """Ciphertexts [count, 2L] (int32 bits) of plaintexts m [count] (int64 bits)
     under randomness r [count, L] (int32 bits)."""
     count = m.numel()
-    assert m.dtype == torch.int64 and r.dtype == torch.int32 and r.shape == (count, key.L)
+    pm, pr = _ptr(m, "m", torch.int64), _ptr(r, "r", torch.int32, shape=(count, key.L))
     if out is None:
         out = torch.empty((count, 2 * key.L), dtype=torch.int32, device=m.device)
-    call("paillier_encrypt", key.handle, _ptr(m), _ptr(r), count, _ptr(out), _stream(stream))
+    po = _ptr(out, "out", torch.int32, min_numel=count * 2 * key.L)
+    call("paillier_encrypt", key.handle, pm, pr, count, po, _stream(stream))
     return out
 
 
 def ct_prepare(key: Key, ct: torch.Tensor, out: torch.Tensor | None = None, stream=None):
     """Montgomery form (mod n^2) of ciphertexts [..., 2L]."""
-    assert ct.dtype == torch.int32 and ct.shape[-1] == 2 * key.L
-    count = ct.numel() // (2 * key.L)
+    count = _rows(ct, "ct", 2 * key.L)
+    pc = _ptr(ct, "ct", torch.int32)
     if out is None:
         out = torch.empty_like(ct)
-    call("paillier_ct_prepare", key.handle, _ptr(ct), count, _ptr(out), _stream(stream))
+    call("paillier_ct_prepare", key.handle, pc, count, _ptr(out, "out", torch.int32, min_numel=ct.numel()),
+         _stream(stream))
     return out
 
 
@@ -138,36 +165,37 @@ def hist_aggregate(key: Key, ctm: torch.Tensor, bins: torch.Tensor, node: torch.
     """Encrypted histogram [num_nodes, F, K, 2, 2L] and counts [num_nodes, F, K]
     from Montgomery-form ciphertexts ctm [2, M, 2L], bins [F, M] uint8, node [M] int32."""
     M = node.numel()
-    F = bins.shape[0]
-    assert ctm.dtype == torch.int32 and ctm.shape == (2, M, 2 * key.L)
-    assert bins.dtype == torch.uint8 and bins.shape == (F, M) and node.dtype == torch.int32
+    F = bins.shape[0] if bins.dim() == 2 else -1
+    args = (_ptr(ctm, "ctm", torch.int32, shape=(2, M, 2 * key.L)), M, _ptr(bins, "bins", torch.uint8, shape=(F, M)),
+            F, K, _ptr(node, "node", torch.int32), num_nodes)
     if hist is None:
         hist = torch.empty((num_nodes, F, K, 2, 2 * key.L), dtype=torch.int32, device=ctm.device)
     if count is None:
         count = torch.empty((num_nodes, F, K), dtype=torch.int32, device=ctm.device)
     fn = "paillier_hist_aggregate_per_node" if per_node else "paillier_hist_aggregate"
-    call(fn, key.handle, _ptr(ctm), M, _ptr(bins), F, K, _ptr(node), num_nodes, _ptr(hist), _ptr(count),
-         _stream(stream))
+    call(fn, key.handle, *args, _ptr(hist, "hist", torch.int32, min_numel=num_nodes * F * K * 2 * 2 * key.L),
+         _ptr(count, "count", torch.int32, min_numel=num_nodes * F * K), _stream(stream))
     return hist, count
 
 
 def decrypt(key: Key, ct: torch.Tensor, out: torch.Tensor | None = None, stream=None):
     """Plaintexts [count, L] (int32 bits) of ciphertexts [..., 2L]."""
-    assert ct.dtype == torch.int32 and ct.shape[-1] == 2 * key.L
-    count = ct.numel() // (2 * key.L)
+    count = _rows(ct, "ct", 2 * key.L)
+    pc = _ptr(ct, "ct", torch.int32)
     if out is None:
         out = torch.empty((count, key.L), dtype=torch.int32, device=ct.device)
-    call("paillier_decrypt", key.handle, _ptr(ct), count, _ptr(out), _stream(stream))
+    call("paillier_decrypt", key.handle, pc, count, _ptr(out, "out", torch.int32, min_numel=count * key.L),
+         _stream(stream))
     return out
 
 
 def decrypt_u64(key: Key, ct: torch.Tensor, out: torch.Tensor | None = None, stream=None):
     """Plaintexts as uint64 (int64 tensor) of ciphertexts [..., 2L]."""
-    assert ct.dtype == torch.int32 and ct.shape[-1] == 2 * key.L
-    count = ct.numel() // (2 * key.L)
+    count = _rows(ct, "ct", 2 * key.L)
+    pc = _ptr(ct, "ct", torch.int32)
     if out is None:
         out = torch.empty(ct.shape[:-1], dtype=torch.int64, device=ct.device)
-    call("paillier_decrypt_u64", key.handle, _ptr(ct), count, _ptr(out), _stream(stream))
+    call("paillier_decrypt_u64", key.handle, pc, count, _ptr(out, "out", torch.int64, min_numel=count), _stream(stream))
     return out
 
 
@@ -187,14 +215,17 @@ class LevelPlan:
             hist: torch.Tensor | None = None, count: torch.Tensor | None = None, stream=None):
         L = self.key.L
         want = (self.M, 2 * L) if self.gh else (2, self.M, 2 * L)
-        assert ctm.shape == want and bins.shape == (self.F, self.M) and node.numel() == self.M
+        args = (_ptr(ctm, "ctm", torch.int32, shape=want), _ptr(bins, "bins", torch.uint8, shape=(self.F, self.M)),
+                _ptr(node, "node", torch.int32, numel=self.M), num_nodes)
+        shape = (num_nodes, self.F, self.K, 2 * L) if self.gh else (num_nodes, self.F, self.K, 2, 2 * L)
         if hist is None:
-            shape = (num_nodes, self.F, self.K, 2 * L) if self.gh else (num_nodes, self.F, self.K, 2, 2 * L)
             hist = torch.empty(shape, dtype=torch.int32, device=ctm.device)
         if count is None:
             count = torch.empty((num_nodes, self.F, self.K), dtype=torch.int32, device=ctm.device)
-        call("paillier_level_run", self._h, _ptr(ctm), _ptr(bins), _ptr(node), num_nodes, _ptr(hist), _ptr(count),
-             _stream(stream))
+        cells = num_nodes * self.F * self.K
+        words = cells * (1 if self.gh else 2) * 2 * L
+        call("paillier_level_run", self._h, *args, _ptr(hist, "hist", torch.int32, min_numel=words),
+             _ptr(count, "count", torch.int32, min_numel=cells), _stream(stream))
         return hist, count
 
     def stats(self):
@@ -214,6 +245,19 @@ class LevelPlan:
             pass
 
 
+def _request_ptrs(key: Key, ctm, M: int, F: int, bins, node, ghs: int, bst: int, gh_bits: int):
+    """Checked pointers of a serving request over the first M samples / F
+    features of resident arrays (g and h rows ghs apart unless g/h-packed,
+    feature rows bst apart)."""
+    if M < 0 or F < 0 or ghs < M or bst < M:
+        raise ValueError("need M, F >= 0 and strides >= M")
+    rows = M if gh_bits else ghs + M
+    pc = _ptr(ctm, "ctm", torch.int32, min_numel=rows * 2 * key.L)
+    pb = _ptr(bins, "bins", torch.uint8, min_numel=(F - 1) * bst + M if F else 0)
+    pn = _ptr(node, "node", torch.int32, min_numel=M) if node is not None else None
+    return pc, pb, pn
+
+
 class Server:
     """Continuous-batching request loop (histogram + decryption jobs)."""
 
@@ -230,12 +274,13 @@ class Server:
         arrays (ctm: g and h arrays gh_stride rows apart, or with gh_bits one
         g/h-packed array); returns (ticket, host sums [num_nodes, F, K, 2]
         uint64 (pinned), host counts [num_nodes, F, K] int32 (pinned))."""
+        ghs = gh_stride if gh_stride is not None else M
+        bst = bins_stride if bins_stride is not None else M
+        pc, pb, pn = _request_ptrs(key, ctm, M, F, bins, node, ghs, bst, gh_bits)
         sums = torch.empty((num_nodes, F, K, 2), dtype=torch.int64).pin_memory()
         counts = torch.empty((num_nodes, F, K), dtype=torch.int32).pin_memory()
-        req = native.Request(key.handle.value, _ptr(ctm), gh_stride if gh_stride is not None else M, M, F, K,
-                             _ptr(bins), bins_stride if bins_stride is not None else M,
-                             _ptr(node) if node is not None else None, num_nodes, sums.data_ptr(), counts.data_ptr(),
-                             pack_bits, gh_bits)
+        req = native.Request(key.handle.value, pc, ghs, M, F, K, pb, bst, pn, num_nodes, sums.data_ptr(),
+                             counts.data_ptr(), pack_bits, gh_bits)
         t = C.c_uint64()
         call("pl_server_submit", self._h, C.byref(req), C.byref(t))
         self._keep[t.value] = (sums, counts, ctm, bins, node, key)
@@ -245,8 +290,8 @@ class Server:
     def request_bytes(key: Key, ctm: torch.Tensor, M: int, F: int, K: int, bins: torch.Tensor,
                       node: torch.Tensor | None = None, num_nodes: int = 1, pack_bits: int = 0,
                       gh_bits: int = 0) -> int:
-        req = native.Request(key.handle.value, _ptr(ctm), M, M, F, K, _ptr(bins), M,
-                             _ptr(node) if node is not None else None, num_nodes, 0, 0, pack_bits, gh_bits)
+        pc, pb, pn = _request_ptrs(key, ctm, M, F, bins, node, M, M, gh_bits)
+        req = native.Request(key.handle.value, pc, M, M, F, K, pb, M, pn, num_nodes, 0, 0, pack_bits, gh_bits)
         b = C.c_size_t()
         call("pl_server_request_bytes", C.byref(req), C.byref(b))
         return b.value
@@ -293,21 +338,34 @@ def pack_slots(key: Key, slot_bits: int) -> int:
 
 def pack(key: Key, ct: torch.Tensor, slot_bits: int, out: torch.Tensor | None = None, stream=None):
     """Packed ciphertexts [ceil(count / slots), 2L] of cells ct [..., 2L]."""
-    assert ct.dtype == torch.int32 and ct.shape[-1] == 2 * key.L
-    count = ct.numel() // (2 * key.L)
+    count = _rows(ct, "ct", 2 * key.L)
+    pc = _ptr(ct, "ct", torch.int32)
     slots = pack_slots(key, slot_bits)
+    if slots < 1:
+        raise ValueError(f"no packing at {slot_bits}-bit slots for this key")
+    npk = (count + slots - 1) // slots
     if out is None:
-        out = torch.empty(((count + slots - 1) // slots, 2 * key.L), dtype=torch.int32, device=ct.device)
-    call("paillier_pack", key.handle, _ptr(ct), count, slot_bits, _ptr(out), _stream(stream))
+        out = torch.empty((npk, 2 * key.L), dtype=torch.int32, device=ct.device)
+    call("paillier_pack", key.handle, pc, count, slot_bits, _ptr(out, "out", torch.int32, min_numel=npk * 2 * key.L),
+         _stream(stream))
     return out
+
+
+def _packed_count(key: Key, cells: int, slot_bits: int) -> int:
+    slots = pack_slots(key, slot_bits)
+    if slots < 1 or cells < 0:
+        raise ValueError(f"no packing of {cells} cells at {slot_bits}-bit slots for this key")
+    return (cells + slots - 1) // slots
 
 
 def decrypt_packed_u64(key: Key, packed: torch.Tensor, count: int, slot_bits: int,
                        out: torch.Tensor | None = None, stream=None):
     """The `count` cell plaintexts (int64 bits of uint64) of packed ciphertexts."""
+    pp = _ptr(packed, "packed", torch.int32, min_numel=_packed_count(key, count, slot_bits) * 2 * key.L)
     if out is None:
         out = torch.empty(count, dtype=torch.int64, device=packed.device)
-    call("paillier_decrypt_packed_u64", key.handle, _ptr(packed), count, slot_bits, _ptr(out), _stream(stream))
+    po = _ptr(out, "out", torch.int64, min_numel=count)
+    call("paillier_decrypt_packed_u64", key.handle, pp, count, slot_bits, po, _stream(stream))
     return out
 
 
@@ -315,22 +373,22 @@ def decrypt_packed_u64(key: Key, packed: torch.Tensor, count: int, slot_bits: in
 
 def encode_gh(g: torch.Tensor, h: torch.Tensor, B: int, out: torch.Tensor | None = None, stream=None):
     """m = enc(g) + 2^B enc(h): [count, 2] int64 (bits of the two uint64 words)."""
-    assert g.dtype == torch.float32 and h.dtype == torch.float32 and g.shape == h.shape
     count = g.numel()
+    pg, ph = _ptr(g, "g", torch.float32), _ptr(h, "h", torch.float32, shape=g.shape)
     if out is None:
         out = torch.empty((count, 2), dtype=torch.int64, device=g.device)
-    call("paillier_encode_gh", _ptr(g), _ptr(h), count, B, _ptr(out), _stream(stream))
+    call("paillier_encode_gh", pg, ph, count, B, _ptr(out, "out", torch.int64, min_numel=2 * count), _stream(stream))
     return out
 
 
 def encrypt_gh(key: Key, m: torch.Tensor, r: torch.Tensor, out: torch.Tensor | None = None, stream=None):
     """Ciphertexts [count, 2L] of two-word plaintexts m [count, 2]."""
-    assert m.dtype == torch.int64 and m.shape[-1] == 2
-    count = m.numel() // 2
-    assert r.dtype == torch.int32 and r.numel() == count * key.L
+    count = _rows(m, "m", 2)
+    pm, pr = _ptr(m, "m", torch.int64), _ptr(r, "r", torch.int32, numel=count * key.L)
     if out is None:
         out = torch.empty((count, 2 * key.L), dtype=torch.int32, device=m.device)
-    call("paillier_encrypt_gh", key.handle, _ptr(m), _ptr(r), count, _ptr(out), _stream(stream))
+    po = _ptr(out, "out", torch.int32, min_numel=count * 2 * key.L)
+    call("paillier_encrypt_gh", key.handle, pm, pr, count, po, _stream(stream))
     return out
 
 
@@ -339,58 +397,76 @@ def hist_aggregate_gh(key: Key, ctm: torch.Tensor, bins: torch.Tensor, node: tor
     """Encrypted histogram [num_nodes, F, K, 2L] and counts of ONE g/h-packed
     Montgomery-form array ctm [M, 2L]."""
     M = node.numel()
-    F = bins.shape[0]
-    assert ctm.dtype == torch.int32 and ctm.shape == (M, 2 * key.L)
-    assert bins.dtype == torch.uint8 and bins.shape == (F, M) and node.dtype == torch.int32
+    F = bins.shape[0] if bins.dim() == 2 else -1
+    args = (_ptr(ctm, "ctm", torch.int32, shape=(M, 2 * key.L)), M, _ptr(bins, "bins", torch.uint8, shape=(F, M)),
+            F, K, _ptr(node, "node", torch.int32), num_nodes)
     if hist is None:
         hist = torch.empty((num_nodes, F, K, 2 * key.L), dtype=torch.int32, device=ctm.device)
     if count is None:
         count = torch.empty((num_nodes, F, K), dtype=torch.int32, device=ctm.device)
-    call("paillier_hist_aggregate_gh", key.handle, _ptr(ctm), M, _ptr(bins), F, K, _ptr(node), num_nodes,
-         _ptr(hist), _ptr(count), _stream(stream))
+    call("paillier_hist_aggregate_gh", key.handle, *args,
+         _ptr(hist, "hist", torch.int32, min_numel=num_nodes * F * K * 2 * key.L),
+         _ptr(count, "count", torch.int32, min_numel=num_nodes * F * K), _stream(stream))
     return hist, count
 
 
 def decrypt_gh(key: Key, ct: torch.Tensor, B: int, out: torch.Tensor | None = None, stream=None):
     """(S_g, S_h) [count, 2] (int64 bits of uint64) of g/h-packed cells ct [..., 2L]."""
-    assert ct.dtype == torch.int32 and ct.shape[-1] == 2 * key.L
-    count = ct.numel() // (2 * key.L)
+    count = _rows(ct, "ct", 2 * key.L)
+    pc = _ptr(ct, "ct", torch.int32)
     if out is None:
         out = torch.empty((count, 2), dtype=torch.int64, device=ct.device)
-    call("paillier_decrypt_gh", key.handle, _ptr(ct), count, B, _ptr(out), _stream(stream))
+    call("paillier_decrypt_gh", key.handle, pc, count, B, _ptr(out, "out", torch.int64, min_numel=2 * count),
+         _stream(stream))
     return out
 
 
 def decrypt_packed_gh(key: Key, packed: torch.Tensor, cells: int, B: int, out: torch.Tensor | None = None,
                       stream=None):
     """(S_g, S_h) [cells, 2] of g/h-packed cells packed with pack(slot_bits = 2B)."""
+    pp = _ptr(packed, "packed", torch.int32, min_numel=_packed_count(key, cells, 2 * B) * 2 * key.L)
     if out is None:
         out = torch.empty((cells, 2), dtype=torch.int64, device=packed.device)
-    call("paillier_decrypt_packed_gh", key.handle, _ptr(packed), cells, B, _ptr(out), _stream(stream))
+    call("paillier_decrypt_packed_gh", key.handle, pp, cells, B, _ptr(out, "out", torch.int64, min_numel=2 * cells),
+         _stream(stream))
     return out
+
+
+def _sums_shape(sums: torch.Tensor, counts: torch.Tensor):
+    """(nodes, F, K) of decrypted sums [nodes, F, K, 2] (int64) and counts [nodes, F, K] (int32)."""
+    if not isinstance(sums, torch.Tensor) or sums.dim() != 4 or sums.shape[-1] != 2:
+        raise ValueError("sums: expected an array [nodes, F, K, 2]")
+    nodes, F, K, _ = sums.shape
+    return nodes, F, K, _ptr(sums, "sums", torch.int64), _ptr(counts, "counts", torch.int32, shape=(nodes, F, K))
 
 
 def split_find(sums: torch.Tensor, counts: torch.Tensor, lam: float = 1.0, gamma: float = 0.0,
                min_child_weight: float = 0.0, stream=None):
     """Best split per node from decrypted sums [nodes, F, K, 2] (int64 bits of
     uint64) and counts [nodes, F, K]: (feature, bin, gain) tensors [nodes]."""
-    nodes, F, K, _ = sums.shape
-    assert sums.dtype == torch.int64 and counts.dtype == torch.int32 and counts.shape == (nodes, F, K)
+    nodes, F, K, ps, pc = _sums_shape(sums, counts)
     bf = torch.empty(nodes, dtype=torch.int32, device=sums.device)
     bb = torch.empty_like(bf)
     bg = torch.empty(nodes, dtype=torch.float64, device=sums.device)
-    call("paillier_split_find", _ptr(sums), _ptr(counts), nodes, F, K, lam, gamma, min_child_weight, _ptr(bf),
-         _ptr(bb), _ptr(bg), _stream(stream))
+    call("paillier_split_find", ps, pc, nodes, F, K, lam, gamma, min_child_weight, _ptr(bf), _ptr(bb), _ptr(bg),
+         _stream(stream))
     return bf, bb, bg
 
 
 def split_apply(bins: torch.Tensor, node: torch.Tensor, best_f: torch.Tensor, best_b: torch.Tensor,
                 out: torch.Tensor | None = None, stream=None):
-    """Next-level node ids of every sample under the chosen splits."""
+    """Next-level node ids of every sample under the chosen splits: bins
+    [F, M] uint8, node [M], best_f / best_b [nodes] int32.  A node id >= nodes
+    or a split feature >= F is reported at sync()."""
     M = node.numel()
+    if bins.dim() != 2 or bins.shape[1] != M:
+        raise ValueError(f"bins: expected [F, {M}]")
+    F, nodes = bins.shape[0], best_f.numel()
+    args = (_ptr(bins, "bins", torch.uint8), M, F, _ptr(node, "node", torch.int32), nodes,
+            _ptr(best_f, "best_f", torch.int32), _ptr(best_b, "best_b", torch.int32, numel=nodes))
     if out is None:
         out = torch.empty_like(node)
-    call("paillier_split_apply", _ptr(bins), M, _ptr(node), _ptr(best_f), _ptr(best_b), _ptr(out), _stream(stream))
+    call("paillier_split_apply", *args, _ptr(out, "out", torch.int32, min_numel=M), _stream(stream))
     return out
 
 
@@ -398,46 +474,60 @@ def child_select(next_node: torch.Tensor, counts: torch.Tensor, best_f: torch.Te
                  stream=None):
     """(small_right [parents], small_node [M]): which child of every parent is
     smaller, and the node array of parents restricted to those children."""
+    if counts.dim() != 3:
+        raise ValueError("counts: expected [nodes, F, K]")
     nodes, F, K = counts.shape
     M = next_node.numel()
+    args = (_ptr(next_node, "next_node", torch.int32), M, _ptr(counts, "counts", torch.int32), nodes, F, K,
+            _ptr(best_f, "best_f", torch.int32, numel=nodes), _ptr(best_b, "best_b", torch.int32, numel=nodes))
     sr = torch.empty(nodes, dtype=torch.int32, device=counts.device)
     sn = torch.empty_like(next_node)
-    call("paillier_child_select", _ptr(next_node), M, _ptr(counts), nodes, F, K, _ptr(best_f), _ptr(best_b),
-         _ptr(sr), _ptr(sn), _stream(stream))
+    call("paillier_child_select", *args, _ptr(sr), _ptr(sn), _stream(stream))
     return sr, sn
 
 
 def child_subtract(parent_sums, parent_counts, small_sums, small_counts, small_right, stream=None):
     """Child-level sums [2 nodes, F, K, 2] and counts [2 nodes, F, K]."""
-    nodes, F, K, _ = parent_sums.shape
+    nodes, F, K, pps, ppc = _sums_shape(parent_sums, parent_counts)
+    args = (pps, ppc, _ptr(small_sums, "small_sums", torch.int64, numel=nodes * F * K * 2),
+            _ptr(small_counts, "small_counts", torch.int32, numel=nodes * F * K),
+            _ptr(small_right, "small_right", torch.int32, numel=nodes))
     cs = torch.empty((2 * nodes, F, K, 2), dtype=torch.int64, device=parent_sums.device)
     cc = torch.empty((2 * nodes, F, K), dtype=torch.int32, device=parent_sums.device)
-    call("paillier_child_subtract", _ptr(parent_sums), _ptr(parent_counts), _ptr(small_sums), _ptr(small_counts),
-         _ptr(small_right), nodes, F, K, _ptr(cs), _ptr(cc), _stream(stream))
+    call("paillier_child_subtract", *args, nodes, F, K, _ptr(cs), _ptr(cc), _stream(stream))
     return cs, cc
 
 
 def tree_decide(bins_party: torch.Tensor, f_lo: int, tree_f: torch.Tensor, tree_b: torch.Tensor,
                 go_right: torch.Tensor, stream=None):
     """One party fills go_right [nodes, M] (uint8) for the tree nodes on its features."""
+    if bins_party.dim() != 2:
+        raise ValueError("bins_party: expected [F_party, M]")
     F_party, M = bins_party.shape
-    call("paillier_tree_decide", _ptr(bins_party), F_party, f_lo, M, _ptr(tree_f), _ptr(tree_b), tree_f.numel(),
-         _ptr(go_right), _stream(stream))
+    nodes = tree_f.numel()
+    call("paillier_tree_decide", _ptr(bins_party, "bins_party", torch.uint8), F_party, f_lo, M,
+         _ptr(tree_f, "tree_f", torch.int32), _ptr(tree_b, "tree_b", torch.int32, numel=nodes), nodes,
+         _ptr(go_right, "go_right", torch.uint8, min_numel=nodes * M), _stream(stream))
     return go_right
 
 
 def tree_route(go_right: torch.Tensor, tree_f: torch.Tensor, depth: int, stream=None):
     """Level-order index of the node every sample reaches."""
+    if go_right.dim() != 2 or not 1 <= depth <= 30:
+        raise ValueError("go_right: expected [nodes, M]; depth 1..30")
     M = go_right.shape[1]
+    nodes = (1 << depth) - 1
+    args = (_ptr(go_right, "go_right", torch.uint8, min_numel=nodes * M), M,
+            _ptr(tree_f, "tree_f", torch.int32, min_numel=nodes), depth)
     leaf = torch.empty(M, dtype=torch.int32, device=go_right.device)
-    call("paillier_tree_route", _ptr(go_right), M, _ptr(tree_f), depth, _ptr(leaf), _stream(stream))
+    call("paillier_tree_route", *args, _ptr(leaf), _stream(stream))
     return leaf
 
 
 def leaf_weights(sums: torch.Tensor, counts: torch.Tensor, lam: float = 1.0, stream=None):
-    nodes, F, K, _ = sums.shape
+    nodes, F, K, ps, pc = _sums_shape(sums, counts)
     w = torch.empty(nodes, dtype=torch.float64, device=sums.device)
-    call("paillier_leaf_weights", _ptr(sums), _ptr(counts), nodes, F, K, lam, _ptr(w), _stream(stream))
+    call("paillier_leaf_weights", ps, pc, nodes, F, K, lam, _ptr(w), _stream(stream))
     return w
 
 

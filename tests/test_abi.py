@@ -30,6 +30,28 @@ def test_checked_library_exports_the_same_functions():
     assert not missing, missing
 
 
+def test_binding_refuses_host_tensors_before_any_call():
+    """The Python layer checks every tensor before its pointer crosses the ABI
+    (the kernels trust them): a host tensor never reaches the library."""
+    import torch
+    from paper_2504_03909_b300 import ckks
+    key = P.Key.generate(1024, 3)
+    m = torch.zeros(4, dtype=torch.int64)
+    r = torch.zeros((4, key.L), dtype=torch.int32)
+    with pytest.raises(ValueError, match="CUDA"):
+        P.encrypt(key, m, r)
+    with pytest.raises(ValueError, match="CUDA"):
+        P.decrypt_u64(key, torch.zeros((2, 2 * key.L), dtype=torch.int32))
+    with pytest.raises(ValueError, match="CUDA"):
+        P.split_find(torch.zeros((1, 2, 4, 2), dtype=torch.int64), torch.zeros((1, 2, 4), dtype=torch.int32))
+    with pytest.raises(ValueError):
+        P.decrypt(key, torch.zeros((2, 2 * key.L + 1), dtype=torch.int32))
+    with pytest.raises(TypeError):
+        P._ptr(np.zeros(3), "x")
+    with pytest.raises(ValueError, match="CUDA"):
+        ckks.Context._poly(type("C", (), {"N": 8})(), torch.zeros(8, dtype=torch.int8), "s", torch.int8)
+
+
 @pytest.mark.parametrize("n_bits", [1024, 2048])
 def test_keygen_is_valid_and_deterministic(n_bits):
     k1 = P.Key.generate(n_bits, 11)

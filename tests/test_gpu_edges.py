@@ -1,7 +1,8 @@
 """Edge cases through the C ABI: a passive party holding only the public key,
 empty calls, values outside the encodable range, randomness that is not a unit
 of Z_n, plaintexts >= 2^64, graph replays with fewer nodes, the largest bin
-count."""
+count, bad tensor arguments (refused before any launch) and out-of-range ids
+in the tree kernels (bounded on the device and reported)."""
 
 from math import gcd
 
@@ -121,3 +122,81 @@ def test_graph_replay_with_fewer_nodes_after_more(env):
         P.sync()
         assert torch.equal(hist[:nn], h) and torch.equal(cnt[:nn], c)
     assert plan.stats()["captures"] == 1
+
+
+def test_binding_checks_arguments_before_any_launch(env):
+    key, M = env["key"], env["M"]
+    m = env["m"][:8]
+    r = P.to_limb_tensor(synth.ints_to_limbs([5] * 8, key.L))
+    ctm = P.ct_prepare(key, env["ct"].view(2, M, -1))
+    bins = torch.from_numpy(synth.gen_bins_uniform(2, M, 16, 8)).cuda()
+    node = torch.zeros(M, dtype=torch.int32, device="cuda")
+    P.sync()
+    bad = [
+        lambda: P.encrypt(key, m.to(torch.int32), r),  # dtype
+        lambda: P.encrypt(key, m, r[:, :-1]),  # shape
+        lambda: P.encrypt(key, m, r.t().contiguous().t()),  # not contiguous
+        lambda: P.encrypt(key, m, r, out=torch.empty((7, 2 * key.L), dtype=torch.int32, device="cuda")),  # short out
+        lambda: P.decrypt(key, env["ct"][:, :-1].contiguous()),  # row width
+        lambda: P.decrypt_u64(key, env["ct"][:4], out=torch.empty(3, dtype=torch.int64, device="cuda")),
+        lambda: P.hist_aggregate(key, ctm, bins.to(torch.int32), node, 1, 16),
+        lambda: P.hist_aggregate(key, ctm[:, :-1].contiguous(), bins, node, 1, 16),
+        lambda: P.hist_aggregate(key, ctm, bins, node, 1, 16,
+                                 hist=torch.empty((1, 2, 16, 2, key.L), dtype=torch.int32, device="cuda")),
+        lambda: P.decrypt_packed_u64(key, env["ct"][:1], 10_000, 40),  # fewer packed rows than cells need
+        lambda: P.split_apply(bins, node, torch.zeros(2, dtype=torch.int32, device="cuda"),
+                              torch.zeros(1, dtype=torch.int32, device="cuda")),
+    ]
+    for i, f in enumerate(bad):
+        with pytest.raises(ValueError):
+            f()
+    assert P.sync() == 0  # nothing reached the device
+
+
+def test_tree_kernels_bound_device_read_ids():
+    M, F, K = 64, 3, 8
+    bins = torch.from_numpy(synth.gen_bins_uniform(F, M, K, 7)).cuda()
+    b_np = bins.cpu().numpy()
+    node = torch.zeros(M, dtype=torch.int32, device="cuda")
+    node[5], node[6], node[7] = 2, 1, -1  # two nodes exist: id 2 is out of range; node 1 splits on feature 7 >= F
+    bf = torch.tensor([1, 7], dtype=torch.int32, device="cuda")
+    bb = torch.tensor([3, 3], dtype=torch.int32, device="cuda")
+    nxt = P.split_apply(bins, node, bf, bb)
+    with pytest.raises(native.PaillierError) as e:
+        P.sync()
+    assert e.value.code == native.PL_EDEVICE
+    assert "node >= num_nodes" in str(e.value) and "split feature >= F" in str(e.value)
+    got = nxt.cpu().tolist()
+    assert got[5] == got[6] == got[7] == -1
+    assert all(got[i] == (1 if b_np[1, i] > 3 else 0) for i in range(M) if i not in (5, 6, 7))
+
+    # child ids beyond 2 nodes are skipped and reported
+    counts = torch.ones((2, F, K), dtype=torch.int32, device="cuda")
+    zero2 = torch.zeros(2, dtype=torch.int32, device="cuda")
+    ids = torch.tensor([0, 1, 2, 3, 9, -1], dtype=torch.int32, device="cuda")
+    sr, sn = P.child_select(ids, counts, zero2, torch.full((2,), 3, dtype=torch.int32, device="cuda"))
+    with pytest.raises(native.PaillierError) as e:
+        P.sync()
+    assert "node >= num_nodes" in str(e.value)
+    assert sr.cpu().tolist() == [0, 0] and sn.cpu().tolist() == [0, -1, 1, -1, -1, -1]
+
+    # any non-zero "small is right" flag means right
+    rng = synth.rng_misc(12)
+    ps = torch.from_numpy(rng.integers(1 << 40, 1 << 41, size=(2, F, K, 2)).astype(np.int64)).cuda()
+    pc = torch.from_numpy(rng.integers(100, 200, size=(2, F, K)).astype(np.int32)).cuda()
+    ss = torch.from_numpy(rng.integers(0, 1 << 40, size=(2, F, K, 2)).astype(np.int64)).cuda()
+    sc = torch.from_numpy(rng.integers(0, 100, size=(2, F, K)).astype(np.int32)).cuda()
+    a = P.child_subtract(ps, pc, ss, sc, torch.tensor([1, 0], dtype=torch.int32, device="cuda"))
+    b = P.child_subtract(ps, pc, ss, sc, torch.tensor([7, 0], dtype=torch.int32, device="cuda"))
+    P.sync()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert torch.equal(a[0][1], ss[0]) and torch.equal(a[0][0], ps[0] - ss[0])
+
+    # any non-zero decision byte means right
+    depth = 3
+    tf = torch.tensor([0, 1, 2, -1, -1, -1, -1], dtype=torch.int32, device="cuda")
+    ones = torch.ones((7, M), dtype=torch.uint8, device="cuda")
+    leaf1 = P.tree_route(ones, tf, depth)
+    leaf255 = P.tree_route(torch.full((7, M), 255, dtype=torch.uint8, device="cuda"), tf, depth)
+    P.sync()
+    assert leaf1.cpu().tolist() == leaf255.cpu().tolist() == [6] * M
