@@ -874,11 +874,12 @@ def run_ours(args, cfg):
             "unit": "TIMAD/s",
             "frac": achieved / peak,
             # DRAM bytes per encryption of this kernel version from the ncu capture summarised in
-            # profiles/k_modexp_enc_2048bit_small.md (16,384 encryptions, w = 5), scaled to this launch
+            # profiles/k_modexp_enc_2048bit_small.md (16,384 encryptions, w = 6), scaled to this launch
             "traffic": units * TRAFFIC_PER_ENC.get((n_bits, w)) if (n_bits, w) in TRAFFIC_PER_ENC else None,
             "traffic_note": "ncu dram__bytes_read+write of a 16,384-encryption capture of this kernel version "
                             "(profiles/k_modexp_enc_2048bit_small.md), scaled by encryptions",
             "peak_source": "derived: SMs x 64 IMAD lanes/clk/SM (4 sub-partitions x 16) x 2032 MHz max SM clock",
+            "sms": sm_count_of(dev),
             "peaks_measured_TIMAD_s": {k: v_ / 1e12 for k, v_ in peaks.items()},
             "frac_of_measured_best_mix": achieved / best_mix,
             "frac_of_carry_chain_mix": achieved / peaks["carry_rows"],
