@@ -5,12 +5,14 @@ one, plus properties that hold at any size:
 * level workload (250,000 samples x 30 features x 256 bins, 2048-bit n):
   a seeded sample of 4,096 ciphertexts bit-exact vs the oracle; EVERY decrypted
   histogram cell equal to the plaintext fixed-point histogram (so every
-  ciphertext is consistent through the homomorphism); 512 sampled cells
-  bit-exact vs the oracle's product; 8 sampled decryptions vs the lambda form.
+  ciphertext is consistent through the homomorphism); 4,096 distinct sampled
+  cells bit-exact vs the oracle's product; 8 sampled decryptions vs the lambda
+  form.
 * batched workload (same data, depth-6 Beta(0.5, 0.5) tree): every level
   through the captured graph, every decrypted cell of every level equal to the
-  plaintext histogram; 256 sampled cells of the deepest level bit-exact vs the
-  oracle's product; batched == plain per-node at the deepest level.
+  plaintext histogram; 4,096 distinct sampled cells of every level below the
+  root (the root is the level workload's) bit-exact vs the oracle's product;
+  batched == plain per-node at the deepest level.
 * large workload's kernel shapes (3072-bit n, 64 log-normal features, 256
   bins) on 20,000 samples and a depth-3 tree.
 Tolerance: none (bit-exact integers).
@@ -23,7 +25,7 @@ import torch
 import oracle
 from paper_2504_03909_b300 import paillier as P, synth
 
-from helpers import oracle_decrypt_many, oracle_encrypt_many, oracle_products_many
+from helpers import oracle_cells_many, oracle_decrypt_many, oracle_encrypt_many, sample_cells
 
 pytestmark = pytest.mark.gpu
 
@@ -65,7 +67,7 @@ def test_level_sampled_ciphertexts_bit_exact(level):
     assert got == want
 
 
-def test_level_root_histogram_every_cell_and_sampled_products(level):
+def test_level_root_histogram_every_cell_and_sampled_products(level, tmp_path):
     cfg, key = level["cfg"], level["key"]
     M, F, K = cfg["M"], cfg["F"], cfg["K"]
     node = torch.zeros(M, dtype=torch.int32, device="cuda")
@@ -75,14 +77,13 @@ def test_level_root_histogram_every_cell_and_sampled_products(level):
     ps, pc = oracle.plain_histogram_np(level["m"][:M], level["m"][M:], level["bins"], np.zeros(M, np.int64), 1, K)
     assert np.array_equal(sums.cpu().numpy().reshape(1, F, K, 2), ps)
     assert np.array_equal(cnt.cpu().numpy(), pc)
-    # sampled cells (g and h): the oracle's product of the cell's ciphertexts
-    cts = synth.limbs_to_ints(P.from_limb_tensor(level["ct"]))
+    # 4,096 distinct cells (g and h): the oracle's product of the cell's ciphertexts
     rng = synth.rng_misc(22)
-    cells = [(int(rng.integers(F)), int(rng.integers(K)), int(rng.integers(2))) for _ in range(512)]
-    groups = [[cts[k * M + i] for i in np.flatnonzero(level["bins"][f] == b)] for f, b, k in cells]
-    want = oracle_products_many(level["n"], groups)
+    cells = sample_cells(rng, [0], F, K, 4096)
+    want = oracle_cells_many(str(tmp_path), level["n"], P.from_limb_tensor(level["ct"]), level["bins"],
+                             np.zeros((1, M), np.int32), cells)
     got = P.from_limb_tensor(hist[0])
-    assert [synth.limbs_to_ints(got[f, b, k][None])[0] for f, b, k in cells] == want
+    assert [synth.limbs_to_ints(got[f, b, k][None])[0] for _, _, f, b, k in cells] == want
     # sampled decryptions against the textbook lambda form
     flat = P.from_limb_tensor(hist.reshape(-1, 2 * key.L))
     pick = rng.choice(flat.shape[0], size=8, replace=False)
@@ -90,7 +91,7 @@ def test_level_root_histogram_every_cell_and_sampled_products(level):
     assert sums.reshape(-1).cpu().numpy()[pick].tolist() == want
 
 
-def test_batched_depth6_every_level_every_cell(level):
+def test_batched_depth6_every_level_every_cell(level, tmp_path):
     cfg, key = level["cfg"], level["key"]
     M, F, K = cfg["M"], cfg["F"], cfg["K"]
     bcfg = synth.CONFIGS["batched"]
@@ -100,6 +101,9 @@ def test_batched_depth6_every_level_every_cell(level):
     node_buf = torch.empty(M, dtype=torch.int32, device="cuda")
     hist = torch.empty((maxn, F, K, 2, 2 * key.L), dtype=torch.int32, device="cuda")
     cnt = torch.empty((maxn, F, K), dtype=torch.int32, device="cuda")
+    rng = synth.rng_misc(23)
+    cells = sample_cells(rng, range(1, len(levels)), F, K, 4096)
+    got_cells = {}
     for lvl, node_np in enumerate(levels):
         nn = 1 << lvl
         node_buf.copy_(torch.from_numpy(node_np))
@@ -109,21 +113,19 @@ def test_batched_depth6_every_level_every_cell(level):
         ps, pc = oracle.plain_histogram_np(level["m"][:M], level["m"][M:], level["bins"], node_np, nn, K)
         assert np.array_equal(sums.cpu().numpy().reshape(nn, F, K, 2), ps), lvl
         assert np.array_equal(cnt[:nn].cpu().numpy(), pc), lvl
+        got = P.from_limb_tensor(hist[:nn])
+        for c in cells:
+            if c[0] == lvl:
+                got_cells[c] = synth.limbs_to_ints(got[c[1], c[2], c[3], c[4]][None])[0]
         if lvl == len(levels) - 1:
             h2, c2 = P.hist_aggregate(key, level["ctm"], level["bins_d"], node_buf, nn, K, per_node=True)
             P.sync()
             assert torch.equal(h2, hist[:nn]) and torch.equal(c2, cnt[:nn])
-            # sampled cells of the deepest level vs the oracle's product
-            cts = synth.limbs_to_ints(P.from_limb_tensor(level["ct"]))
-            rng = synth.rng_misc(23)
-            cells = [(int(rng.integers(nn)), int(rng.integers(F)), int(rng.integers(K)), int(rng.integers(2)))
-                     for _ in range(256)]
-            groups = [[cts[k * M + i] for i in np.flatnonzero((level["bins"][f] == b) & (node_np == v))]
-                      for v, f, b, k in cells]
-            want = oracle_products_many(level["n"], groups)
-            got = P.from_limb_tensor(hist[:nn])
-            assert [synth.limbs_to_ints(got[v, f, b, k][None])[0] for v, f, b, k in cells] == want
     assert plan.stats()["captures"] == 1
+    # 4,096 sampled cells of every level below the root vs the oracle's product
+    want = oracle_cells_many(str(tmp_path), level["n"], P.from_limb_tensor(level["ct"]), level["bins"],
+                             np.stack(levels).astype(np.int32), cells)
+    assert [got_cells[c] for c in cells] == want
 
 
 def test_large_shapes_3072bit():
