@@ -174,6 +174,20 @@ def imad_peak_derived(sms: int) -> float:
     return sms * IMAD_LANES_PER_SM * MAX_SM_MHZ * 1e6
 
 
+def plaintext_root_sums(P, torch, v, bins_d, M: int, F: int, K: int):
+    """Untimed check data: per (feature, bin) of the root, the plain sums of the
+    encoded g and h values and the sample counts (torch index_add / bincount on
+    the device).  Every ciphertext enters F cells of the root histogram, so a
+    decrypted root equal to these sums checks every ciphertext of the step
+    through the homomorphism."""
+    m = P.encode(v)
+    idx = (torch.arange(F, device=v.device)[:, None] * K + bins_d.long()).reshape(-1)
+    want = torch.zeros((F * K, 2), dtype=torch.int64, device=v.device)
+    for k in range(2):
+        want[:, k].index_add_(0, idx, m[k * M:(k + 1) * M].repeat(F))
+    return want, torch.bincount(idx, minlength=F * K)
+
+
 def sm_count_of(dev) -> int:
     import torch
     return torch.cuda.get_device_properties(dev).multi_processor_count
@@ -789,6 +803,9 @@ def run_ours(args, cfg):
     e2e_s = e2.elapsed_time(e3) / 1e3
     e2e_s = max_over_ranks(e2e_s, dist, dev)
     P.sync()
+    want, want_cnt = plaintext_root_sums(P, torch, v, bins_d, M, F, K)
+    if not (torch.equal(sums.view(F * K, 2), want) and torch.equal(cnt.view(-1).long(), want_cnt)):
+        raise RuntimeError("decrypted root histogram differs from the plaintext sums")
 
     # the same step with g/h packing (one plaintext enc(g) + 2^B enc(h) per
     # sample, a decrypt-count reduction the paper does not use): reported
@@ -897,6 +914,8 @@ def run_ours(args, cfg):
         "e2e": {"value": whole_job_rate(units, e2e_steps, world, e2e_s), "unit": "enc/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
+        "verified": f"decrypted root histogram == plaintext sums of the encoded values, all {F * K * 2} cells "
+                    "and counts (untimed)",
     }
     if gh_line is not None:
         line["gh_packed"] = gh_line
@@ -1076,6 +1095,19 @@ def run_batched(args, cfg):
                 hist_levels(True)
                 t_per_node = timed(lambda: hist_levels(True), args.steps)
         P.sync(stream)
+        # untimed: the root histogram of this step's ciphertexts, decrypted, equals the plaintext sums
+        node0 = torch.zeros(M, dtype=torch.int32, device=dev)
+        if B:
+            h0, c0 = P.hist_aggregate_gh(key, ctm1, bins_d, node0, 1, K)
+            got = P.decrypt_gh(key, h0.reshape(-1, 2 * L), B)
+        else:
+            h0, c0 = P.hist_aggregate(key, ctm.view(2, M, 2 * L), bins_d, node0, 1, K)
+            got = P.decrypt_u64(key, h0.reshape(-1, 2 * L))
+        want, want_cnt = plaintext_root_sums(P, torch, v, bins_d, M, F, K)
+        P.sync(stream)
+        if not (torch.equal(got.view(F * K, 2), want) and torch.equal(c0.view(-1).long(), want_cnt)):
+            raise RuntimeError("decrypted root histogram differs from the plaintext sums")
+        del h0, c0, got, want, want_cnt
     ct_mults = 0
     strict = 0
     for lv in levels:
@@ -1106,6 +1138,8 @@ def run_batched(args, cfg):
         "cells_decoded_per_s": cells / ((prof["modexp_dec"] + prof["dec_crt"] + prof["unpack"] + prof["pack"]) * 1e-3),
         "graph": (plan_gh if B else plan).stats(),
         "clocks": clk.summary(),
+        "verified": f"root histogram of the step's ciphertexts, decrypted, == plaintext sums of the encoded "
+                    f"values, all {F * K * 2} cells and counts (untimed)",
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
