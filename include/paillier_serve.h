@@ -66,7 +66,12 @@ typedef struct pl_request {
 #define PL_REQ_CANCELLED 4
 
 /* Creates a server on the current device: `slots` >= 1 concurrent requests,
- * at most hbm_budget bytes of request memory in flight. */
+ * at most hbm_budget bytes of request memory in flight.  Request memory is
+ * stream-ordered (cudaMallocAsync from the device's default memory pool); the
+ * server sets that pool's release threshold to its maximum, so freed request
+ * memory stays cached in the pool for the next request.  The setting belongs
+ * to the process's default pool of this device and outlives the server;
+ * memory cached there is returned by cudaMemPoolTrimTo or at process exit. */
 pl_status pl_server_create(int slots, size_t hbm_budget, pl_server** out);
 
 /* Queues a request (arguments are checked here; PL_EBUSY if it can never fit
