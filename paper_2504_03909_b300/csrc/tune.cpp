@@ -125,15 +125,20 @@ pl_status paillier_autotune(pl_key* key, int op, const char* cache_path, void* s
     bufs.push_back(p);
     return p;
   };
-  auto cleanup = [&] {
-    cudaStreamSynchronize(s);
-    for (void* p : bufs) cudaFree(p);
-  };
   std::vector<Cand> cands = candidates(key, op);
   if (cands.empty()) return fail(PL_EINVAL, "no candidates for this key size");
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&] {  // every path out after this point
+    cudaStreamSynchronize(s);
+    for (void* p : bufs) cudaFree(p);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(PL_ECUDA, "autotune events");
+  }
   double best_ms = 1e30;
   pl_status rc = PL_OK;
   const ModexpCfg enc0 = key->enc_cfg, dec0 = key->dec_cfg;
@@ -192,8 +197,6 @@ pl_status paillier_autotune(pl_key* key, int op, const char* cache_path, void* s
       if (ms < best_ms) { best_ms = ms; best = c; }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   cleanup();
   key->enc_cfg = enc0;
   key->dec_cfg = dec0;
