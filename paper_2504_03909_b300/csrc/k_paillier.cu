@@ -110,6 +110,56 @@ PL_DEV void window_exp(uint32_t (&acc)[S], const uint32_t (&n)[S], uint32_t np, 
   for (int j = 0; j < S; ++j) acc[j] = a[j];
 }
 
+// The first encryption stage of one instance on a group of T lanes holding S
+// limbs each of the prime x (S T = L/2 limbs): z = (r mod x)^(x' mod (x - 1))
+// mod x, canonical, returned in z; r is the L-limb row rrow.  A zero residue r
+// mod x (gcd(r, n) != 1) sets kStatusNonUnit when status is given.
+template <int S, int T>
+PL_DEV void enc_stage1(uint32_t (&z)[S], const HalfConst& H, const uint8_t* op1, int nop1, int w,
+                       const uint32_t* rrow, uint32_t* mytbl, uint32_t* bs, int st, int k, bool valid, int gw,
+                       int* status) {
+  constexpr int NLh = S * T;
+  uint32_t nx[S], tx[S];
+  const_slice<S>(nx, H.Nx, k);
+  const uint32_t npx = H.npx;
+  // r = r_lo + r_hi Rx: Montgomery form (r mod x) Rx = mont(r_lo, Rx^2) + mont(r_hi, Rx^3)
+  load_slice<S>(z, rrow, k);
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < S; ++j) bs[(k * S + j) * st] = H.R2x[k * S + j];
+  __syncwarp();
+  mont_mul<S, T>(tx, z, bs, st, nx, npx, k);
+  store_slice<S>(mytbl, tx, k);
+  load_slice<S>(z, rrow + NLh, k);
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < S; ++j) bs[(k * S + j) * st] = H.R3x[k * S + j];
+  __syncwarp();
+  mont_mul<S, T>(tx, z, bs, st, nx, npx, k);
+  load_slice_rw<S>(z, mytbl, k);
+  add_cc(tx[0], z[0]);
+#pragma unroll
+  for (int j = 1; j < S; ++j) addc_cc(tx[j], z[j]);
+  const uint32_t c = carry_out();
+  normalize<S, T>(tx, c, 0u, nx, k, kFull);
+  if (status != nullptr) {
+    // gcd(r, n) = 1 exactly when r mod p and r mod q are both non-zero
+    uint32_t any = 0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) any |= tx[j];
+    const unsigned nz = __ballot_sync(kFull, any != 0u);
+    const unsigned gm = (T == 32) ? kFull : ((1u << T) - 1u);
+    if (valid && k == 0 && ((nz >> (gw * T)) & gm) == 0u) atomicOr(status, kStatusNonUnit);
+  }
+  window_exp<S, T>(tx, nx, npx, op1, nop1, w, mytbl, bs, st, k);
+  // leave Montgomery form mod x
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < S; ++j) bs[(k * S + j) * st] = (k * S + j == 0) ? 1u : 0u;
+  __syncwarp();
+  mont_mul<S, T>(z, tx, bs, st, nx, npx, k);
+}
+
 // Batched exponentiation in the CRT halves.  Instance (h, i): half h (prime
 // x = p or q), item i.  A warp takes 32/T consecutive items of one half, so the
 // exponent schedules are warp-uniform.
@@ -122,7 +172,11 @@ PL_DEV void window_exp(uint32_t (&acc)[S], const uint32_t (&n)[S], uint32_t np, 
 //   DEC: y[h][i] = c_i^(x - 1) mod x^2                (in = c [count][2L])
 // Every value is canonical.  tbl: per-group window table, 2^(w-1) entries of
 // L limbs for each group of the grid.
-template <int S, int T, bool DEC>
+// STAGE (encryption only) splits the two exponentiations over two launches so
+// that each runs at its own lanes per instance: STAGE 1 computes z = (r mod
+// x)^(x' mod (x - 1)) mod x alone (S T = L/2 limbs; out = z [2][count][L/2]),
+// STAGE 2 the rest from z (in = z; S T = L limbs); STAGE 0 does both.
+template <int S, int T, bool DEC, int STAGE = 0>
 __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ ModexpParams P,
                                                    const uint32_t* __restrict__ in, const uint64_t* __restrict__ msg,
                                                    int mw, uint32_t* __restrict__ out, uint32_t* __restrict__ tbl,
@@ -150,6 +204,12 @@ __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ Modex
     const bool valid = i < count;
     const size_t ii = valid ? i : count - 1;
     const HalfConst& H = P.half[h];
+    if constexpr (STAGE == 1) {
+      uint32_t z[S];
+      enc_stage1<S, T>(z, H, P.op1[h], P.nop1[h], w, in + ii * 2 * NL, mytbl, bs, st, k, valid, gw, status);
+      if (valid) store_slice<S>(out + ((size_t)h * count + ii) * NL, z, k);
+      continue;
+    }
     uint32_t n[S], a[S], t[S];
     const_slice<S>(n, H.N, k);
     const uint32_t np = H.np;
@@ -173,58 +233,28 @@ __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ Modex
       normalize<S, T>(t, 0u, 1u, n, k, kFull);
       if (valid) store_slice<S>(yrow, t, k);
 
-      // stage 1, mod x on L/2 limbs: z = (r mod x)^(x' mod (x - 1)) mod x
-      {
+      if constexpr (STAGE == 0) {
+        // stage 1, mod x on L/2 limbs; z (< x) into the L-limb layout of stage 2, zero-extended
         constexpr int S2 = S / 2;
         constexpr int NLh = S2 * T;
-        uint32_t nx[S2], ax[S2], tx[S2];
-        const_slice<S2>(nx, H.Nx, k);
-        const uint32_t npx = H.npx;
-        const uint32_t* rrow = in + ii * NL;
-        // r = r_lo + r_hi Rx: Montgomery form (r mod x) Rx = mont(r_lo, Rx^2) + mont(r_hi, Rx^3)
-        load_slice<S2>(ax, rrow, k);
+        uint32_t z[S2];
+        enc_stage1<S2, T>(z, H, P.op1[h], P.nop1[h], w, in + ii * NL, mytbl, bs, st, k, valid, gw, status);
         __syncwarp();
-#pragma unroll
-        for (int j = 0; j < S2; ++j) bs[(k * S2 + j) * st] = H.R2x[k * S2 + j];
-        __syncwarp();
-        mont_mul<S2, T>(tx, ax, bs, st, nx, npx, k);
-        store_slice<S2>(mytbl, tx, k);
-        load_slice<S2>(ax, rrow + NLh, k);
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < S2; ++j) bs[(k * S2 + j) * st] = H.R3x[k * S2 + j];
-        __syncwarp();
-        mont_mul<S2, T>(tx, ax, bs, st, nx, npx, k);
-        load_slice_rw<S2>(ax, mytbl, k);
-        add_cc(tx[0], ax[0]);
-#pragma unroll
-        for (int j = 1; j < S2; ++j) addc_cc(tx[j], ax[j]);
-        const uint32_t c = carry_out();
-        normalize<S2, T>(tx, c, 0u, nx, k, kFull);
-        if (status != nullptr) {
-          // gcd(r, n) = 1 exactly when r mod p and r mod q are both non-zero
-          uint32_t any = 0;
-#pragma unroll
-          for (int j = 0; j < S2; ++j) any |= tx[j];
-          const unsigned nz = __ballot_sync(kFull, any != 0u);
-          const unsigned gm = (T == 32) ? kFull : ((1u << T) - 1u);
-          if (valid && k == 0 && ((nz >> (gw * T)) & gm) == 0u) atomicOr(status, kStatusNonUnit);
-        }
-        window_exp<S2, T>(tx, nx, npx, P.op1[h], P.nop1[h], w, mytbl, bs, st, k);
-        // leave Montgomery form mod x
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < S2; ++j) bs[(k * S2 + j) * st] = (k * S2 + j == 0) ? 1u : 0u;
-        __syncwarp();
-        mont_mul<S2, T>(ax, tx, bs, st, nx, npx, k);
-        // z (< x, L/2 limbs) into the L-limb layout of stage 2, zero-extended
-        __syncwarp();
-        stage<S2>(bs, st, ax, k);
+        stage<S2>(bs, st, z, k);
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < S; ++j) {
           const int idx = k * S + j;
           a[j] = idx < NLh ? bs[idx * st] : 0u;
+        }
+      } else {
+        // z from the first-stage launch: lanes below T/2 hold its L/2 limbs, the rest zero
+        static_assert(T % 2 == 0, "the second stage needs an even number of lanes");
+        if (k < T / 2) {
+          load_slice<S>(a, in + ((size_t)h * count + ii) * (NL / 2), k);
+        } else {
+#pragma unroll
+          for (int j = 0; j < S; ++j) a[j] = 0u;
         }
       }
       // stage 2 base: z R mod x^2
@@ -359,27 +389,29 @@ __global__ void __launch_bounds__(kBlock) k_dec_crt(const __grid_constant__ DecC
 // ---------------------------------------------------------------------------
 // launch helpers
 
-template <int S, int T, bool DEC>
+template <int S, int T, bool DEC, int STAGE = 0>
 pl_status run_modexp(const ModexpParams* P, const uint32_t* in, const uint64_t* msg, int mw, uint32_t* y,
                      uint32_t* tbl, int grid, size_t count, int* status, cudaStream_t s) {
   const int ipb = kBlock / T;
   const size_t smem = (size_t)S * T * ipb * sizeof(uint32_t);
   {
-    ProfScope _ps((DEC ? "modexp_dec" : "modexp_enc"), s);
-    k_modexp<S, T, DEC><<<grid, kBlock, smem, s>>>(*P, in, msg, mw, y, tbl, count, status);
+    ProfScope _ps(DEC ? "modexp_dec" : (STAGE == 1 ? "modexp_enc1" : "modexp_enc"), s);
+    k_modexp<S, T, DEC, STAGE><<<grid, kBlock, smem, s>>>(*P, in, msg, mw, y, tbl, count, status);
   }
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
 }
 
-template <int S, int T, bool DEC>
+template <int S, int T, bool DEC, int STAGE = 0>
 int modexp_grid() {
   static int blocks_per_sm = -1;
   if (blocks_per_sm < 0) {
     const int ipb = kBlock / T;
     const size_t smem = (size_t)S * T * ipb * sizeof(uint32_t);
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_modexp<S, T, DEC>, kBlock, smem) != cudaSuccess || b < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_modexp<S, T, DEC, STAGE>, kBlock, smem) !=
+            cudaSuccess ||
+        b < 1)
       b = 1;
     blocks_per_sm = b;
   }
@@ -408,6 +440,32 @@ pl_status modexp_dispatch(int L, int T, int* grid_out, bool launch, const Modexp
   }
 #undef PL_CASE
   return fail(PL_EINVAL, "no exponentiation kernel for this (limbs, lanes) pair");
+}
+
+// Encryption split over two launches (STAGE 1, then 2) where both kernels
+// exist: the first stage at half the lanes of the second (2048-bit: 2 lanes of
+// 16 limbs mod x, then 4 of 16 mod x^2; 3072-bit: 4 of 12, then 8 of 12).
+bool enc_split(int L, int T) { return (L == 64 && T == 4) || (L == 96 && T == 8); }
+
+// STAGE 1 dispatch on (limbs of x, lanes) and STAGE 2 on (limbs of x^2, lanes)
+template <int STAGE>
+pl_status enc_stage_dispatch(int L, int T, int* grid_out, bool launch, const ModexpParams* P, const uint32_t* in,
+                             const uint64_t* msg, uint32_t* y, uint32_t* tbl, size_t count, cudaStream_t s, int mw,
+                             int* status) {
+#define PL_CASE(LL, TT)                                                                            \
+  if (L == LL && T == TT) {                                                                        \
+    if (!launch) { *grid_out = modexp_grid<LL / TT, TT, false, STAGE>(); return PL_OK; }            \
+    return run_modexp<LL / TT, TT, false, STAGE>(P, in, msg, mw, y, tbl, *grid_out, count, status, s); \
+  }
+  if constexpr (STAGE == 1) {
+    PL_CASE(32, 2)
+    PL_CASE(48, 4)
+  } else {
+    PL_CASE(64, 4)
+    PL_CASE(96, 8)
+  }
+#undef PL_CASE
+  return fail(PL_EINVAL, "no split encryption kernel for this (limbs, lanes) pair");
 }
 
 }  // namespace
@@ -464,6 +522,47 @@ ModexpCfg lanes_for_count(int L, ModexpCfg cfg, size_t count) {
   return cfg;
 }
 
+// grid of a launch on `count` items at T lanes: no more blocks than items need
+static int trim_grid(int grid, size_t count, int T) {
+  const size_t ipw = 32 / (size_t)T;
+  const size_t warps_needed = 2 * ((count + ipw - 1) / ipw);
+  const size_t blocks_needed = (warps_needed + (kBlock / 32) - 1) / (kBlock / 32);
+  return (size_t)grid > blocks_needed ? (int)blocks_needed : grid;
+}
+
+// Encryption as two launches (enc_split): z [2][count][L/2], then y.
+static pl_status enc_phase_split(pl_key* key, ModexpCfg cfg, const ModexpParams* P, const uint32_t* d_r,
+                                 const uint64_t* msg, size_t count, uint32_t** y_out, cudaStream_t s,
+                                 Scratch* scratch, int mw, int* st) {
+  const int L = key->L, T1 = cfg.T / 2;
+  int g1 = 0, g2 = 0;
+  pl_status rc = enc_stage_dispatch<1>(L / 2, T1, &g1, false, P, nullptr, nullptr, nullptr, nullptr, 0, s, mw, st);
+  if (rc) return rc;
+  rc = enc_stage_dispatch<2>(L, cfg.T, &g2, false, P, nullptr, nullptr, nullptr, nullptr, 0, s, mw, st);
+  if (rc) return rc;
+  g1 = trim_grid(g1, count, T1);
+  g2 = trim_grid(g2, count, cfg.T);
+  // the window tables of the two launches share one region
+  const size_t tb1 = (size_t)g1 * (kBlock / T1) * table_entries(cfg.w) * (L / 2);
+  const size_t tb2 = (size_t)g2 * (kBlock / cfg.T) * table_entries(cfg.w) * L;
+  Carve cv;
+  const size_t off_y = cv.take((size_t)2 * count * L * sizeof(uint32_t));
+  const size_t off_z = cv.take((size_t)count * L * sizeof(uint32_t));
+  const size_t off_t = cv.take(std::max(tb1, tb2) * sizeof(uint32_t));
+  Scratch* sc = scratch ? scratch : key->scratch_for_current_device();
+  if (!sc) return fail(PL_ECUDA, "no current device");
+  char* base = static_cast<char*>(sc->get(cv.off, s));
+  if (!base) return fail(PL_ENOMEM, "scratch allocation failed");
+  uint32_t* y = reinterpret_cast<uint32_t*>(base + off_y);
+  uint32_t* z = reinterpret_cast<uint32_t*>(base + off_z);
+  uint32_t* tbl = reinterpret_cast<uint32_t*>(base + off_t);
+  rc = enc_stage_dispatch<1>(L / 2, T1, &g1, true, P, d_r, msg, z, tbl, count, s, mw, st);
+  if (rc) return rc;
+  rc = enc_stage_dispatch<2>(L, cfg.T, &g2, true, P, z, msg, y, tbl, count, s, mw, st);
+  *y_out = y;
+  return rc;
+}
+
 template <bool DEC>
 static pl_status modexp_phase(pl_key* key, ModexpCfg cfg, const uint32_t* in, const uint64_t* msg,
                               size_t count, uint32_t** y_out, cudaStream_t s, Scratch* scratch, int mw = 1,
@@ -472,6 +571,9 @@ static pl_status modexp_phase(pl_key* key, ModexpCfg cfg, const uint32_t* in, co
   const ModexpParams* P = key->modexp_params(DEC, cfg.w);
   if (!P) return fail(PL_EINVAL, "unsupported window width");
   const int L = key->L;
+  if constexpr (!DEC) {
+    if (enc_split(L, cfg.T)) return enc_phase_split(key, cfg, P, in, msg, count, y_out, s, scratch, mw, st);
+  }
   int grid = 0;
   pl_status rc = modexp_dispatch<DEC>(L, cfg.T, &grid, false, P, nullptr, nullptr, nullptr, nullptr, 0, s);
   if (rc) return rc;
