@@ -70,7 +70,11 @@ void paillier_level_plan_free(pl_level_plan* plan);
  * shorter latency; the results are the same bits. */
 
 /* Current configuration of an op on this key: lanes per instance (limbs per
- * lane = limbs / lanes) and the window width (ops 0, 1) or tile (op 2). */
+ * lane = limbs / lanes) and the window width (ops 0, 1) or tile (op 2).
+ * Encryption with 4 lanes at 2048-bit or 8 at 3072-bit runs as two launches:
+ * the first exponentiation (mod p and mod q, half the limbs) at half the
+ * lanes, then the second (mod p^2 and mod q^2) at the configured lanes, so
+ * that both keep the same limbs per lane; other settings run one launch. */
 pl_status paillier_get_config(const pl_key* key, int op, int* lanes, int* param);
 
 /* Sets a configuration (checked against the compiled kernel shapes:
