@@ -1,0 +1,79 @@
+"""The benchmark's work accounting (the numerator of every roofline it
+reports): a left-to-right sliding-window exponentiation over the odd powers,
+carried out on Python integers step by step as the schedule prescribes,
+computes pow(b, e, m) in exactly bench.sliding_ops(e, w) steps, and the
+per-encryption totals add up over the two stages and CRT halves."""
+
+import random
+
+import pytest
+
+import bench
+
+
+def sliding_schedule(e: int, w: int):
+    """Ops of the schedule: ("load", v) for the leading window value v, then
+    ("sq",) per squaring and ("mul", v) per product by the table entry b^v."""
+    ops, i = [], e.bit_length() - 1
+    while i >= 0:
+        if not (e >> i) & 1:
+            ops.append(("sq",))
+            i -= 1
+            continue
+        j = max(i - w + 1, 0)
+        while not (e >> j) & 1:
+            j += 1
+        v = (e >> j) & ((1 << (i - j + 1)) - 1)  # odd window value
+        if not ops:
+            ops.append(("load", v))
+        else:
+            ops += [("sq",)] * (i - j + 1) + [("mul", v)]
+        i = j - 1
+    return ops
+
+
+def run(ops, b: int, m: int, w: int) -> int:
+    table = {v: pow(b, v, m) for v in range(1, 1 << w, 2)}  # the odd powers
+    acc = None
+    for op in ops:
+        if op[0] == "load":
+            acc = table[op[1]]
+        elif op[0] == "sq":
+            acc = acc * acc % m
+        else:
+            acc = acc * table[op[1]] % m
+    return acc
+
+
+@pytest.mark.parametrize("w", [2, 4, 5, 6, 7])
+def test_sliding_window_schedule_computes_the_power_in_the_counted_steps(w):
+    rng = random.Random(w)
+    m = rng.getrandbits(256) | (1 << 255) | 1
+    for bits in (1, 2, 7, 64, 511, 1024):
+        for _ in range(5):
+            e = rng.getrandbits(bits) | (1 << (bits - 1))
+            b = rng.randrange(2, m)
+            ops = sliding_schedule(e, w)
+            assert run(ops, b, m, w) == pow(b, e, m)
+            assert len(ops) == bench.sliding_ops(e, w)
+    # worked case: e = 0b1011 with w = 2: the leading window is the top bit (b),
+    # a zero bit (b^2), then the window 0b11 (b^4, b^8, times b^3 = b^11)
+    assert sliding_schedule(0b1011, 2) == [("load", 1), ("sq",), ("sq",), ("sq",), ("mul", 3)]
+    assert bench.sliding_ops(0b1011, 2) == 5
+
+
+def test_montgomery_and_exponentiation_counts():
+    assert bench.mont_imad(32) == 4 * 32 * 32 + 32
+    # pre + table (b^2 and 2^(w-1) - 1 products) + schedule after its leading window + post
+    e, w = 0b1011, 2
+    assert bench.exp_montmuls(e, w) == 2 + 2 + 4 + 1
+
+
+def test_encryption_totals_add_over_stages_and_halves():
+    p, q = 0xF7E3_5A1B_C2D4_E6F9, 0xE1C3_A5B7_99DB_FD13  # odd numbers standing in for the primes
+    n_bits, w = 128, 5
+    first, second = bench.enc_imad_stages(n_bits, w, p, q)
+    L = n_bits // 32
+    assert first == sum(bench.exp_montmuls(xo % (x - 1), w) for x, xo in ((p, q), (q, p))) * bench.mont_imad(L // 2)
+    assert second == sum(bench.exp_montmuls(x, w) for x in (p, q)) * bench.mont_imad(L)
+    assert bench.enc_imad(n_bits, w, p, q) == first + second
