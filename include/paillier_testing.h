@@ -9,6 +9,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "paillier.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -22,6 +24,16 @@ extern "C" {
  * (64,4) (64,8) (96,4) (96,8) (128,4) (128,8) (192,8) (192,16). */
 int paillier_test_mont_mul(int limbs, int lanes, const uint32_t* h_N, const uint32_t* d_a,
                            const uint32_t* d_b, size_t count, uint32_t* d_out, void* stream);
+
+/* Lengths of the key's key-fixed exponentiation schedules (host only, no
+ * device work), for the CRT halves h = 0 (prime p) and 1 (prime q): nop[h] is
+ * the number of ops of the exponentiation mod x^2 (exponent x for encryption,
+ * x - 1 for decryption; x the half's prime), nop1[h] (encryption only, may be
+ * NULL; 0 for decryption) that of the first encryption stage mod x (exponent
+ * x' mod (x - 1), x' the other prime).  The first op loads the leading window
+ * from the table of odd powers, every other op is one Montgomery product (a
+ * squaring or a product by a table entry).  key must be private; w in 2..7. */
+int paillier_test_schedule_ops(const pl_key* key, int dec, int w, int* nop, int* nop1);
 
 /* Checked builds only (build.py --checked): launches one thread that reports
  * a failed bounds check at `site` (0..30) without touching any memory, so

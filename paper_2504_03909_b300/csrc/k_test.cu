@@ -97,3 +97,17 @@ extern "C" int paillier_test_bounds_report(int site, void* stream) {
   return fail(PL_EINVAL, "not a checked build");
 #endif
 }
+
+extern "C" int paillier_test_schedule_ops(const pl_key* key, int dec, int w, int* nop, int* nop1) {
+  using namespace pl;
+  clear_error();
+  if (!key || !nop) return fail(PL_EINVAL, "NULL argument");
+  if (!key->priv) return fail(PL_EINVAL, "a public key has no exponentiation schedules");
+  const ModexpParams* P = const_cast<pl_key*>(key)->modexp_params(dec != 0, w);
+  if (!P) return fail(PL_EINVAL, "unsupported window width");
+  for (int h = 0; h < 2; ++h) {
+    nop[h] = P->nop[h];
+    if (nop1) nop1[h] = dec ? 0 : P->nop1[h];
+  }
+  return PL_OK;
+}

@@ -47,6 +47,7 @@ SIGNATURES = {
     "paillier_last_error": (C.c_char_p, []),
     "paillier_test_mont_mul": (_i, [_i, _i, _vp, _vp, _vp, _sz, _vp, _vp]),
     "paillier_test_bounds_report": (_i, [_i, _vp]),
+    "paillier_test_schedule_ops": (_i, [_vp, _i, _i, _vp, _vp]),
     "paillier_imad_peak": (_i, [_i, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
     "paillier_fp64_peak": (_i, [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
     "paillier_launch_count": (C.c_ulonglong, []),

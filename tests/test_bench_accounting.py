@@ -77,3 +77,22 @@ def test_encryption_totals_add_over_stages_and_halves():
     assert first == sum(bench.exp_montmuls(xo % (x - 1), w) for x, xo in ((p, q), (q, p))) * bench.mont_imad(L // 2)
     assert second == sum(bench.exp_montmuls(x, w) for x in (p, q)) * bench.mont_imad(L)
     assert bench.enc_imad(n_bits, w, p, q) == first + second
+
+
+@pytest.mark.parametrize("w", [4, 5, 6, 7])
+def test_bench_counts_the_schedules_the_kernels_run(w):
+    """The library's key-fixed schedules (what the kernels execute) have the
+    lengths the bench's accounting gives them, for every exponent of both CRT
+    halves (host-side entry point; no GPU)."""
+    import ctypes as C
+
+    from paper_2504_03909_b300 import native, paillier as P, synth
+    for n_bits, seed in ((1024, 3), (2048, 4)):
+        p, q = synth.gen_primes(n_bits, seed)
+        key = P.Key.from_primes(n_bits, p, q)
+        nop, nop1 = (C.c_int * 2)(), (C.c_int * 2)()
+        native.call("paillier_test_schedule_ops", key.handle, 0, w, nop, nop1)
+        assert list(nop) == [bench.sliding_ops(x, w) for x in (p, q)]
+        assert list(nop1) == [bench.sliding_ops(xo % (x - 1), w) for x, xo in ((p, q), (q, p))]
+        native.call("paillier_test_schedule_ops", key.handle, 1, w, nop, None)
+        assert list(nop) == [bench.sliding_ops(x - 1, w) for x in (p, q)]
