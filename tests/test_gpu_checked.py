@@ -1,7 +1,8 @@
 """The bounds-checked library (build.py --checked: device-side checks on every
 gathered sample id, chunk partial, sorted position, window-table entry, CKKS
-cluster exchange and slot permutation) runs the main paths without a single
-failed check, and gives the same integers as the normal library.  It stands
+cluster exchange and slot permutation) runs the main paths (encryption as one
+launch at 1024-bit and as two at 2048-bit) without a single failed check, and
+gives the same integers as the normal library.  It stands
 in for compute-sanitizer, which this pool does not offer."""
 
 import os
@@ -45,6 +46,14 @@ def _workload() -> dict:
     ct1 = P.encrypt_gh(key, P.encode_gh(g_d, h_d, B), P.to_limb_tensor(r[:M]))
     h1, _ = P.hist_aggregate_gh(key, P.ct_prepare(key, ct1), bins, node, nodes, K)
     out.update(ct_gh=ct1, sums_gh=P.decrypt_gh(key, h1.reshape(-1, 2 * key.L), B))
+
+    # 2048-bit encryption large enough to take the two-launch path (first stage
+    # at 2 lanes, second at 4)
+    p2, q2 = synth.gen_primes(2048, 22)
+    key2 = P.Key.from_primes(2048, p2, q2)
+    M2 = 4000
+    m2 = P.encode(torch.from_numpy(synth.gen_gh(M2 // 2, 22).reshape(-1)).cuda())
+    out.update(ct2048=P.encrypt(key2, m2, P.to_limb_tensor(synth.gen_r(p2 * q2, 2048, M2, 22, p2, q2))))
 
     log_n = 10
     N, qc = 1 << log_n, synth.ckks_prime(log_n)
