@@ -700,11 +700,41 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
   }
 }
 
+// One DIT butterfly: u + t x, u - t x (t = W^j, conjugated for sign -1), the
+// same operations in the same order as the radix-2 stages.
+__device__ __forceinline__ void dit_bfly(double2& u, double2& x, double2 t, double sign) {
+  const double wr = t.x, wi = sign * t.y;
+  const double vr = x.x * wr - x.y * wi, vi = x.x * wi + x.y * wr;
+  x = make_double2(u.x - vr, u.y - vi);
+  u = make_double2(u.x + vr, u.y + vi);
+}
+
 // FFT stages in the block layout: lg = 1 .. logM (half size h = 2^(lg-1) < M);
-// w[j] = W^j of the length-n transform (log_n2 = log2 n)
+// w[j] = W^j of the length-n transform (log_n2 = log2 n).  Two consecutive
+// stages run in registers on four elements per work item (one barrier per
+// pair), the last one alone when logM is odd.
 __device__ void fft_block_stages(double2* a, const double2* w, int logM, int log_n2, double sign) {
   const int M = 1 << logM;
-  for (int lg = 1; lg <= logM; ++lg) {
+  int lg0 = 1;
+  for (; lg0 + 1 <= logM; lg0 += 2) {
+    const int half = 1 << (lg0 - 1);
+    for (int b = threadIdx.x; b < M / 4; b += blockDim.x) {
+      const int j = b & (half - 1);
+      const int i0 = ((b >> (lg0 - 1)) << (lg0 + 1)) + j;
+      double2 x0 = a[i0], x1 = a[i0 + half], x2 = a[i0 + 2 * half], x3 = a[i0 + 3 * half];
+      const double2 t1 = w[j << (log_n2 - lg0)];
+      dit_bfly(x0, x1, t1, sign);
+      dit_bfly(x2, x3, t1, sign);
+      dit_bfly(x0, x2, w[j << (log_n2 - lg0 - 1)], sign);
+      dit_bfly(x1, x3, w[(j + half) << (log_n2 - lg0 - 1)], sign);
+      a[i0] = x0;
+      a[i0 + half] = x1;
+      a[i0 + 2 * half] = x2;
+      a[i0 + 3 * half] = x3;
+    }
+    __syncthreads();
+  }
+  for (int lg = lg0; lg <= logM; ++lg) {
     const int half = 1 << (lg - 1);
     for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
       const int g = b >> (lg - 1), j = b & (half - 1);
@@ -722,10 +752,30 @@ __device__ void fft_block_stages(double2* a, const double2* w, int logM, int log
 
 // FFT stages in the cyclic layout of CTA r: lg = logM + 1 .. log_n2 (global half
 // size h >= M, local half size h / kCl; the pair's global offset in its group
-// is r + kCl j')
+// is r + kCl j'), two stages per barrier as in the block layout
 __device__ void fft_cyclic_stages(double2* a, const double2* w, int r, int logM, int log_n2, double sign) {
   const int M = 1 << logM;
-  for (int lg = logM + 1; lg <= log_n2; ++lg) {
+  int lg0 = logM + 1;
+  for (; lg0 + 1 <= log_n2; lg0 += 2) {
+    const int lh = lg0 - 1 - kClLog;  // log2 of the local half size of stage lg0
+    for (int b = threadIdx.x; b < M / 4; b += blockDim.x) {
+      const int jl = b & ((1 << lh) - 1);
+      const int i0 = ((b >> lh) << (lh + 2)) + jl;
+      const int hl = 1 << lh;
+      double2 x0 = a[i0], x1 = a[i0 + hl], x2 = a[i0 + 2 * hl], x3 = a[i0 + 3 * hl];
+      const double2 t1 = w[(r + (jl << kClLog)) << (log_n2 - lg0)];
+      dit_bfly(x0, x1, t1, sign);
+      dit_bfly(x2, x3, t1, sign);
+      dit_bfly(x0, x2, w[(r + (jl << kClLog)) << (log_n2 - lg0 - 1)], sign);
+      dit_bfly(x1, x3, w[(r + ((jl + hl) << kClLog)) << (log_n2 - lg0 - 1)], sign);
+      a[i0] = x0;
+      a[i0 + hl] = x1;
+      a[i0 + 2 * hl] = x2;
+      a[i0 + 3 * hl] = x3;
+    }
+    __syncthreads();
+  }
+  for (int lg = lg0; lg <= log_n2; ++lg) {
     const int lh = lg - 1 - kClLog;  // log2 of the local half size
     for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
       const int g = b >> lh, jl = b & ((1 << lh) - 1);
