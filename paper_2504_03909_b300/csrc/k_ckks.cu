@@ -514,39 +514,60 @@ constexpr int kClNttThreads = 256, kClFftThreads = 256;
 __device__ __forceinline__ int tail_off(int lt, int M) { return lt == 2 ? 0 : (lt == 1 ? M / 8 : M / 8 + M / 4); }
 
 // forward stages t = kCl/2 .. 1 on the block slice of CTA r; tw: this CTA's
-// packed block-stage twiddles (global entry N/2t + r M/2t + i at tail_off + i)
+// packed block-stage twiddles (global entry N/2t + r M/2t + i at tail_off + i).
+// The three stages stay inside groups of 8 consecutive entries: one work item
+// per group, in registers, one barrier.
+static_assert(kCl == 8, "the block-layout stages are written for clusters of 8");
 __device__ void ntt_fwd_tail(u64* a, const u64* tw, const NttConst& C, int logM) {
   const int M = 1 << logM;
-  for (int lt = kClLog - 1; lt >= 0; --lt) {
-    const u64* w = tw + tail_off(lt, M);
-    for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
-      const int i = b >> lt, idx = (i << (lt + 1)) + (b & ((1 << lt) - 1));
-      u64 x = a[idx], y = a[idx + (1 << lt)];
-      ct_bfly(x, y, w[i], C);
-      a[idx] = x;
-      a[idx + (1 << lt)] = y;
-    }
-    __syncthreads();
+  const u64 *w4 = tw + tail_off(2, M), *w2 = tw + tail_off(1, M), *w1 = tw + tail_off(0, M);
+  for (int g = threadIdx.x; g < M / 8; g += blockDim.x) {
+    u64 x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = a[8 * g + k];
+    const u64 t4 = w4[g];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ct_bfly(x[k], x[k + 4], t4, C);
+    const u64 t2a = w2[2 * g], t2b = w2[2 * g + 1];
+    ct_bfly(x[0], x[2], t2a, C);
+    ct_bfly(x[1], x[3], t2a, C);
+    ct_bfly(x[4], x[6], t2b, C);
+    ct_bfly(x[5], x[7], t2b, C);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) ct_bfly(x[2 * m], x[2 * m + 1], w1[4 * g + m], C);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[8 * g + k] = x[k];
   }
+  __syncthreads();
 }
 
 // inverse stages t = 1 .. kCl/2 on the block slice (one or two polynomials,
-// spread over the threads together); itw: packed like ntt_fwd_tail's
+// spread over the threads together); itw: packed like ntt_fwd_tail's; the
+// mirror image of ntt_fwd_tail (groups of 8, one barrier)
 __device__ void ntt_inv_head(u64* a, u64* b, const u64* itw, const NttConst& C, int logM) {
   const int M = 1 << logM;
   const int two = b ? 1 : 0;
-  for (int lt = 0; lt < kClLog; ++lt) {
-    for (int task = threadIdx.x; task < (M / 2) << two; task += blockDim.x) {
-      u64* p = (task >= M / 2) ? b : a;
-      const int k = task & (M / 2 - 1);
-      const int i = k >> lt, idx = (i << (lt + 1)) + (k & ((1 << lt) - 1));
-      u64 x = p[idx], y = p[idx + (1 << lt)];
-      gs_bfly(x, y, itw[tail_off(lt, M) + i], C);
-      p[idx] = x;
-      p[idx + (1 << lt)] = y;
-    }
-    __syncthreads();
+  const u64 *w1 = itw + tail_off(0, M), *w2 = itw + tail_off(1, M), *w4 = itw + tail_off(2, M);
+  for (int task = threadIdx.x; task < (M / 8) << two; task += blockDim.x) {
+    u64* p = (task >= M / 8) ? b : a;
+    const int g = task & (M / 8 - 1);
+    u64 x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = p[8 * g + k];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) gs_bfly(x[2 * m], x[2 * m + 1], w1[4 * g + m], C);
+    const u64 t2a = w2[2 * g], t2b = w2[2 * g + 1];
+    gs_bfly(x[0], x[2], t2a, C);
+    gs_bfly(x[1], x[3], t2a, C);
+    gs_bfly(x[4], x[6], t2b, C);
+    gs_bfly(x[5], x[7], t2b, C);
+    const u64 t4 = w4[g];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gs_bfly(x[k], x[k + 4], t4, C);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) p[8 * g + k] = x[k];
   }
+  __syncthreads();
 }
 
 // block slice of CTA r <- the cluster's cyclic slices (global index r M + v
