@@ -66,6 +66,12 @@ __device__ __forceinline__ u64 smod(long long x, u64 q) {  // signed small or la
   const long long r = x % (long long)q;
   return r < 0 ? (u64)(r + (long long)q) : (u64)r;
 }
+// the same for a 32-bit value: one conditional add when |x| < q is certain
+// (q > 2^31; q is the same for every thread, so the branch is uniform)
+__device__ __forceinline__ u64 smod32(int32_t x, u64 q) {
+  if (q > 0x80000000ull) return x < 0 ? q - (u64)(-(long long)x) : (u64)x;
+  return smod(x, q);
+}
 
 struct NttConst {
   u64 q, qn, r2;
@@ -290,7 +296,7 @@ __device__ __forceinline__ void ntt_inv(u64* a, u64* b, const u64* itw, const Nt
 }
 
 __device__ __forceinline__ u64 to_q(u64 x, u64) { return x; }  // already in [0, q)
-__device__ __forceinline__ u64 to_q(int8_t x, u64 q) { return smod(x, q); }
+__device__ __forceinline__ u64 to_q(int8_t x, u64 q) { return smod32(x, q); }
 
 // Every kernel below keeps its twiddle table in shared memory (copied once at
 // entry with 16-byte loads): one DRAM/L2 round trip instead of one per stage.
@@ -333,7 +339,7 @@ __global__ void __launch_bounds__(kThreads)
   const size_t p = blockIdx.x;
   u64 *x = sm, *y = sm + N, *t = sm + 2 * N;
   stage_table(t, tw, N);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = smod(v[p * N + i], C.q);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = smod32(v[p * N + i], C.q);
   __syncthreads();
   ntt_fwd(x, t, C, C.log_n);
   stage_table(t, itw, N);
@@ -347,8 +353,8 @@ __global__ void __launch_bounds__(kThreads)
   u64* c0 = c + p * 2 * N;
   u64* c1 = c0 + N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    c0[i] = addm(addm(x[i], smod(e0[p * N + i], C.q), C.q), smod(m[p * N + i], C.q), C.q);
-    c1[i] = addm(y[i], smod(e1[p * N + i], C.q), C.q);
+    c0[i] = addm(addm(x[i], smod32(e0[p * N + i], C.q), C.q), smod(m[p * N + i], C.q), C.q);
+    c1[i] = addm(y[i], smod32(e1[p * N + i], C.q), C.q);
   }
 }
 
@@ -388,7 +394,7 @@ __global__ void __launch_bounds__(kThreads)
     sm[i] = mmul(ahat[i], shat[i], C.q, C.qn);
   __syncthreads();
   ntt_inv(sm, nullptr, t, C, C.log_n);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) b[i] = addm(subm(0, sm[i], C.q), smod(e[i], C.q), C.q);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) b[i] = addm(subm(0, sm[i], C.q), smod32(e[i], C.q), C.q);
 }
 
 constexpr int kMaxSum = 256;  // operands of one ckks_sum (kernel parameter space)
@@ -650,7 +656,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
   }
   cp_async_commit();
   stage_table(t, tw, M);
-  for (int u = threadIdx.x; u < M; u += blockDim.x) x0[u] = smod(v[p * N + r + (u << kClLog)], C.q);
+  for (int u = threadIdx.x; u < M; u += blockDim.x) x0[u] = smod32(v[p * N + r + (u << kClLog)], C.q);
   __syncthreads();
   ntt_fwd(x0, t, C, logM);  // stages t >= kCl
   cl.sync();
@@ -675,8 +681,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
   u64* c1 = c0 + N;
   for (int u = threadIdx.x; u < M; u += blockDim.x) {
     const size_t g = (size_t)r + ((size_t)u << kClLog);
-    c0[g] = addm(addm(x0[u], smod(ee[u], C.q), C.q), smod((long long)em[u], C.q), C.q);
-    c1[g] = addm(x1[u], smod(ee[M + u], C.q), C.q);
+    c0[g] = addm(addm(x0[u], smod32(ee[u], C.q), C.q), smod((long long)em[u], C.q), C.q);
+    c1[g] = addm(x1[u], smod32(ee[M + u], C.q), C.q);
   }
 }
 
