@@ -66,6 +66,13 @@ __device__ __forceinline__ u64 smod(long long x, u64 q) {  // signed small or la
   const long long r = x % (long long)q;
   return r < 0 ? (u64)(r + (long long)q) : (u64)r;
 }
+// the same for a 64-bit value that is usually smaller than q in magnitude
+// (encoded plaintext coefficients): one conditional add then, else the remainder
+__device__ __forceinline__ u64 smod64(long long x, u64 q) {
+  const u64 ax = x < 0 ? (u64)(-(x + 1)) + 1u : (u64)x;  // |x|, also for INT64_MIN
+  if (ax < q) return x < 0 ? q - ax : ax;
+  return smod(x, q);
+}
 // the same for a 32-bit value: one conditional add when |x| < q is certain
 // (q > 2^31; q is the same for every thread, so the branch is uniform)
 __device__ __forceinline__ u64 smod32(int32_t x, u64 q) {
@@ -353,7 +360,7 @@ __global__ void __launch_bounds__(kThreads)
   u64* c0 = c + p * 2 * N;
   u64* c1 = c0 + N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    c0[i] = addm(addm(x[i], smod32(e0[p * N + i], C.q), C.q), smod(m[p * N + i], C.q), C.q);
+    c0[i] = addm(addm(x[i], smod32(e0[p * N + i], C.q), C.q), smod64(m[p * N + i], C.q), C.q);
     c1[i] = addm(y[i], smod32(e1[p * N + i], C.q), C.q);
   }
 }
@@ -681,7 +688,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
   u64* c1 = c0 + N;
   for (int u = threadIdx.x; u < M; u += blockDim.x) {
     const size_t g = (size_t)r + ((size_t)u << kClLog);
-    c0[g] = addm(addm(x0[u], smod32(ee[u], C.q), C.q), smod((long long)em[u], C.q), C.q);
+    c0[g] = addm(addm(x0[u], smod32(ee[u], C.q), C.q), smod64((long long)em[u], C.q), C.q);
     c1[g] = addm(x1[u], smod32(ee[M + u], C.q), C.q);
   }
 }
