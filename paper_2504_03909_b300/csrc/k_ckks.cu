@@ -620,6 +620,9 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// waits until at most P of this thread's committed groups are still in flight
+template <int P>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(P) : "memory"); }
 
 // 16-byte copies of n words (n even, both ends 16-byte aligned)
 __device__ __forceinline__ void cp_async_words(u64* dst, const u64* src, int n) {
@@ -650,7 +653,11 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
   u64 *x0 = sm, *x1 = sm + M, *y0 = sm + 2 * M, *y1 = sm + 3 * M, *t = sm + 4 * M;
   u64 *pk0 = sm + 5 * M, *pk1 = sm + 6 * M, *twf = sm + 7 * M, *twi = sm + 8 * M, *em = sm + 9 * M;
   int32_t* ee = reinterpret_cast<int32_t*>(sm + 10 * M);
-  // everything needed after the first phase, in flight while it runs
+  // asynchronous copies in three groups: the forward length-M twiddles (needed
+  // first), everything needed after the first transform, and (issued once the
+  // forward transform is done with t) the inverse length-M twiddles
+  cp_async_words(t, tw, M);
+  cp_async_commit();
   cp_async_words(pk0, pk + (r << logM), M);
   cp_async_words(pk1, pk + N + (r << logM), M);
   cp_async_tail(twf, tw, N, r, logM);
@@ -662,16 +669,17 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
     cp_async4(ee + M + u, e1 + g);
   }
   cp_async_commit();
-  stage_table(t, tw, M);
   for (int u = threadIdx.x; u < M; u += blockDim.x) x0[u] = smod32(v[p * N + r + (u << kClLog)], C.q);
+  cp_async_wait_group<1>();
   __syncthreads();
   ntt_fwd(x0, t, C, logM);  // stages t >= kCl
   cl.sync();
+  cp_async_words(t, itw, M);
+  cp_async_commit();
   gather_block(cl, y0, x0, r, logM);
-  cp_async_wait();
+  cp_async_wait_group<1>();
   __syncthreads();
   ntt_fwd_tail(y0, twf, C, logM);  // stages t < kCl
-  stage_table(t, itw, M);
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     const u64 xv = y0[i];
     y0[i] = mmul(xv, pk0[i], C.q, C.qn);
@@ -683,6 +691,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
   gather_cyclic(cl, x0, y0, r, logM);
   gather_cyclic(cl, x1, y1, r, logM);
   cl.sync();  // no CTA reads another's block slice after this
+  cp_async_wait();  // the inverse twiddles
+  __syncthreads();
   ntt_inv(x0, x1, t, C, logM);
   u64* c0 = c + p * 2 * N;
   u64* c1 = c0 + N;
@@ -706,27 +716,33 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClNttThreads)
   u64 *x = sm, *y = sm + M, *t = sm + 2 * M, *sh = sm + 3 * M, *ec0 = sm + 4 * M, *twf = sm + 5 * M,
       *twi = sm + 6 * M;
   const u64* c0 = c + p * 2 * N;
+  // copy groups as in k_encrypt_cl
+  cp_async_words(t, tw, M);
+  cp_async_commit();
   cp_async_words(sh, shat + (r << logM), M);
   cp_async_tail(twf, tw, N, r, logM);
   cp_async_tail(twi, itw, N, r, logM);
   for (int u = threadIdx.x; u < M; u += blockDim.x) cp_async8(ec0 + u, c0 + r + ((size_t)u << kClLog));
   cp_async_commit();
-  stage_table(t, tw, M);
   for (int u = threadIdx.x; u < M; u += blockDim.x) x[u] = c0[N + r + (u << kClLog)];
+  cp_async_wait_group<1>();
   __syncthreads();
   ntt_fwd(x, t, C, logM);
   cl.sync();
+  cp_async_words(t, itw, M);
+  cp_async_commit();
   gather_block(cl, y, x, r, logM);
-  cp_async_wait();
+  cp_async_wait_group<1>();
   __syncthreads();
   ntt_fwd_tail(y, twf, C, logM);
-  stage_table(t, itw, M);
   for (int i = threadIdx.x; i < M; i += blockDim.x) y[i] = mmul(y[i], sh[i], C.q, C.qn);
   __syncthreads();
   ntt_inv_head(y, nullptr, twi, C, logM);
   cl.sync();
   gather_cyclic(cl, x, y, r, logM);
   cl.sync();
+  cp_async_wait();  // the inverse twiddles
+  __syncthreads();
   ntt_inv(x, nullptr, t, C, logM);
   for (int u = threadIdx.x; u < M; u += blockDim.x) {
     const size_t g = (size_t)r + ((size_t)u << kClLog);
@@ -836,12 +852,14 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClFftThreads)
   const size_t p = blockIdx.x / kCl;
   const int log_m = log_n - 1, n = 1 << log_m, N = 2 * n, logM = log_m - kClLog, M = 1 << logM;
   double2 *blk = z, *cyc = z + M, *w = z + 2 * M;
-  for (int j = threadIdx.x; j < n / 2; j += blockDim.x) w[j] = fftw[j];
+  for (int j = threadIdx.x; j < n / 2; j += blockDim.x) cp_async16(w + j, fftw + j);  // in flight during the load
+  cp_async_commit();
   for (int v = threadIdx.x; v < M; v += blockDim.x) {  // bit-reversed load: Y[t] = z_j at t = pos_j
     int j = invpos[brev((r << logM) + v, log_m)];
     if (!PL_BOUNDS(j >= 0 && j < n, pl::kBoundsSlot)) j = 0;
     blk[v] = make_double2(re[p * n + j], im[p * n + j]);
   }
+  cp_async_wait();
   __syncthreads();
   fft_block_stages(blk, w, logM, log_m, -1.0);
   cl.sync();
@@ -867,7 +885,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClFftThreads)
   const size_t p = blockIdx.x / kCl;
   const int log_m = log_n - 1, n = 1 << log_m, N = 2 * n, logM = log_m - kClLog, M = 1 << logM;
   double2 *blk = z, *cyc = z + M, *w = z + 2 * M;
-  for (int j = threadIdx.x; j < n / 2; j += blockDim.x) w[j] = fftw[j];
+  for (int j = threadIdx.x; j < n / 2; j += blockDim.x) cp_async16(w + j, fftw + j);  // in flight during the load
+  cp_async_commit();
   for (int v = threadIdx.x; v < M; v += blockDim.x) {  // bit-reversed load of the twisted w_k
     const int k = brev((r << logM) + v, log_m);
     const u64 a = mq[p * N + k], b = mq[p * N + k + n];
@@ -876,6 +895,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kClFftThreads)
     const double2 t = twist[k];
     blk[v] = make_double2(x * t.x - y * t.y, x * t.y + y * t.x);
   }
+  cp_async_wait();
   __syncthreads();
   fft_block_stages(blk, w, logM, log_m, 1.0);
   cl.sync();
