@@ -14,7 +14,8 @@ one, plus properties that hold at any size:
   root (the root is the level workload's) bit-exact vs the oracle's product;
   batched == plain per-node at the deepest level.
 * large workload's kernel shapes (3072-bit n, 64 log-normal features, 256
-  bins) on 20,000 samples and a depth-3 tree.
+  bins) on 20,000 samples and a depth-3 tree; 257 sampled ciphertexts (the
+  last one included) bit-exact vs the oracle.
 Tolerance: none (bit-exact integers).
 """
 
@@ -132,7 +133,7 @@ def test_large_shapes_3072bit():
     d = _setup(synth.CONFIGS["large"], M=20_000)
     cfg, key = d["cfg"], d["key"]
     M, F, K = cfg["M"], cfg["F"], cfg["K"]
-    idx = sorted(synth.rng_misc(23).choice(2 * M, size=16, replace=False).tolist())
+    idx = sorted(set(synth.rng_misc(23).choice(2 * M, size=256, replace=False).tolist()) | {2 * M - 1})
     want = oracle_encrypt_many(d["n"], [int(d["m"][i]) for i in idx], synth.limbs_to_ints(d["r"][idx]))
     assert synth.limbs_to_ints(P.from_limb_tensor(d["ct"][idx])) == want
     levels = synth.gen_tree_levels(M, 3, cfg["seed"])
