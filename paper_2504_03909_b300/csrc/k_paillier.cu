@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kBlock) k_modexp(const __grid_constant__ Modex
         }
       } else {
         // z from the first-stage launch: lanes below T/2 hold its L/2 limbs, the rest zero
-        static_assert(T % 2 == 0, "the second stage needs an even number of lanes");
+        static_assert(STAGE != 2 || T % 2 == 0, "the second stage needs an even number of lanes");
         if (k < T / 2) {
           load_slice<S>(a, in + ((size_t)h * count + ii) * (NL / 2), k);
         } else {
