@@ -577,11 +577,7 @@ static pl_status modexp_phase(pl_key* key, ModexpCfg cfg, const uint32_t* in, co
   int grid = 0;
   pl_status rc = modexp_dispatch<DEC>(L, cfg.T, &grid, false, P, nullptr, nullptr, nullptr, nullptr, 0, s);
   if (rc) return rc;
-  // no more blocks than items need
-  const size_t ipw = 32 / (size_t)cfg.T;
-  const size_t warps_needed = 2 * ((count + ipw - 1) / ipw);
-  const size_t blocks_needed = (warps_needed + (kBlock / 32) - 1) / (kBlock / 32);
-  if ((size_t)grid > blocks_needed) grid = (int)blocks_needed;
+  grid = trim_grid(grid, count, cfg.T);
   const size_t ipb = kBlock / cfg.T;
   Carve cv;
   const size_t off_y = cv.take((size_t)2 * count * L * sizeof(uint32_t));
@@ -618,10 +614,7 @@ size_t decrypt_scratch_bytes(const pl_key* key, size_t count) {
   const ModexpCfg cfg = lanes_for_count<true>(L, key->dec_cfg, count);
   int grid = 0;
   if (modexp_dispatch<true>(L, cfg.T, &grid, false, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr)) return 0;
-  const size_t ipw = 32 / (size_t)cfg.T;
-  const size_t warps_needed = 2 * ((count + ipw - 1) / ipw);
-  const size_t blocks_needed = (warps_needed + (kBlock / 32) - 1) / (kBlock / 32);
-  if ((size_t)grid > blocks_needed) grid = (int)blocks_needed;
+  grid = trim_grid(grid, count, cfg.T);
   const size_t ipb = kBlock / cfg.T;
   Carve cv;
   cv.take((size_t)2 * count * L * sizeof(uint32_t));
