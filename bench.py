@@ -904,6 +904,18 @@ def run_ours(args, cfg):
         first_stage = {"kernel": "k_modexp (encryption, first stage: (r mod x)^(x' mod (x - 1)) mod x)",
                        "achieved": units * imad1 / (t1 * 1e-3) / 1e12, "frac": units * imad1 / (t1 * 1e-3) / peak,
                        "launch_ms": t1, "imad_per_launch": units * imad1}
+    # the encrypted histogram's segmented product: one product mod n^2 (2L limbs) per contribution
+    t_seg = prof["seg_product"][0] / max(1, prof["seg_product"][1])
+    agg_imad = M * F * 2 * mont_imad(2 * L)
+    agg_rate = agg_imad / (t_seg * 1e-3)
+    aggregate_roofline = {
+        "bound": "alu", "kernel": "k_seg_product (one product mod n^2 per (sample, feature, g/h) contribution)",
+        "achieved": agg_rate / 1e12, "peak": peak / 1e12, "unit": "TIMAD/s", "frac": agg_rate / peak,
+        "frac_of_measured_best_mix": agg_rate / best_mix, "frac_of_carry_chain_mix": agg_rate / peaks["carry_rows"],
+        "launch_ms": t_seg, "imad_per_launch": agg_imad,
+        "dram_note": "ncu: DRAM reads about one pass over the ciphertexts, 3.6 GB/s, 0.05 % of peak "
+                     "(profiles/k_seg_product_2048bit_small.md): the pass is ALU-bound",
+    }
     line = {
         "metric": METRIC,
         "value": value,
@@ -946,6 +958,7 @@ def run_ours(args, cfg):
             "launch_ms": enc_launch_ms,
             "first_stage": first_stage,
         },
+        "aggregate_roofline": aggregate_roofline,
         "clocks": clk.summary(),
         "e2e": {"value": whole_job_rate(units, e2e_steps, world, e2e_s), "unit": "enc/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
