@@ -42,8 +42,8 @@ from paper_2504_03909_b300 import synth  # noqa: E402
 METRIC = "2048-bit Paillier enc/s & encrypted-hist ct-mults/s; p50/p99 request ms"
 
 # DRAM bytes (read + write) per encryption of the current encryption kernel that dominates the
-# step (the second stage when encryption runs as two launches), from the ncu capture
-# summarised in profiles/k_modexp_enc2_2048bit_small.md, keyed by (n_bits, window)
+# step (the second stage when encryption runs as two launches), from an ncu capture of
+# 16,384 encryptions of this kernel version, keyed by (n_bits, window)
 TRAFFIC_PER_ENC = {(2048, 6): (311.65e6 + 248.54e6) / 16384}
 
 
@@ -913,8 +913,8 @@ def run_ours(args, cfg):
         "achieved": agg_rate / 1e12, "peak": peak / 1e12, "unit": "TIMAD/s", "frac": agg_rate / peak,
         "frac_of_measured_best_mix": agg_rate / best_mix, "frac_of_carry_chain_mix": agg_rate / peaks["carry_rows"],
         "launch_ms": t_seg, "imad_per_launch": agg_imad,
-        "dram_note": "ncu: DRAM reads about one pass over the ciphertexts, 3.6 GB/s, 0.05 % of peak "
-                     "(profiles/k_seg_product_2048bit_small.md): the pass is ALU-bound",
+        "dram_note": "ncu capture of the segmented product on 2 x 65,536 x 16 contributions: DRAM reads "
+                     "about one pass over the ciphertexts, 3.6 GB/s, 0.05 % of peak: the pass is ALU-bound",
     }
     line = {
         "metric": METRIC,
@@ -942,11 +942,11 @@ def run_ours(args, cfg):
             "peak": peak / 1e12,
             "unit": "TIMAD/s",
             "frac": achieved / peak,
-            # DRAM bytes per encryption of this kernel version from the ncu capture summarised in
-            # profiles/k_modexp_enc2_2048bit_small.md (16,384 encryptions, w = 6), scaled to this launch
+            # DRAM bytes per encryption of this kernel version from an ncu capture of 16,384
+            # encryptions (w = 6), scaled to this launch
             "traffic": units * TRAFFIC_PER_ENC.get((n_bits, w)) if (n_bits, w) in TRAFFIC_PER_ENC else None,
-            "traffic_note": "ncu dram__bytes_read+write of a 16,384-encryption capture of this kernel version "
-                            "(profiles/k_modexp_enc2_2048bit_small.md), scaled by encryptions",
+            "traffic_note": "ncu dram__bytes_read+write of a 16,384-encryption capture of this kernel "
+                            "version, scaled by encryptions",
             "peak_source": "derived: SMs x 64 IMAD lanes/clk/SM (4 sub-partitions x 16) x 2032 MHz max SM clock",
             "sms": sm_count_of(dev),
             "peaks_measured_TIMAD_s": {k: v_ / 1e12 for k, v_ in peaks.items()},

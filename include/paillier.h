@@ -101,8 +101,13 @@ void paillier_key_free(pl_key* key);
  * [0, 1/4]); other values write 0 and set PL_EDEVICE in the status word. */
 pl_status paillier_encode(const float* d_v, size_t count, uint64_t* d_m, void* stream);
 
-/* Decoding of histogram sums: d_out[i] = (d_s[i] - d_cnt[i] * 2^24) / 2^24
- * in float64, for sums of d_cnt[i] encoded values. */
+/* Decoding of histogram sums (Sec. III.B: the decrypted G/H go on to tree
+ * building): d_out[i] = (d_s[i] - d_cnt[i] * 2^24) / 2^24 in float64, for
+ * sums of d_cnt[i] >= 0 encoded values.  The difference is formed exactly in
+ * 64-bit integers (valid while |d_s[i] - d_cnt[i] 2^24| < 2^63, which every
+ * sum of at most 2^31 encoded values meets) and rounded once to float64,
+ * nearest, ties to even; the scaling by 2^-24 is exact.  d_s, d_cnt, d_out:
+ * [count] device arrays owned by the caller.  count = 0 does nothing. */
 pl_status paillier_decode(const uint64_t* d_s, const int32_t* d_cnt, size_t count,
                           double* d_out, void* stream);
 

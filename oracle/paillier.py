@@ -23,7 +23,7 @@ with the generator g = n + 1:
     decrypt_crt   = the Chinese-remainder decryption of the same paper (its
                     Sec. 7), used here only as a cross-check of ``decrypt``.
 
-Readings where the paper is silent (each is listed in the design doc):
+Readings where the paper is silent (the same readings as the GPU path):
   * g = n + 1; the homomorphic "addition" is the product mod n^2;
   * fixed point: m = round_half_even(v * 2^24) + 2^24 (additive offset);
   * an empty histogram cell is the ciphertext 1 (the empty product);

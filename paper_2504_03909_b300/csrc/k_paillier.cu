@@ -652,14 +652,18 @@ pl_status launch_decrypt(pl_key* key, const uint32_t* d_ct, size_t count, void* 
 // needs (the two CRT half results and the per-instance window tables) lives in
 // one file-scope device array instead of the key's scratch buffer.  The array
 // is part of the library's device image: every GPU that loads the library
-// holds it (about 35 MB) until the process exits.
+// holds it (about 21 MB) until the process exits.
 namespace pl {
 namespace {
 
 constexpr size_t kNaMaxCount = 8192;  // ciphertexts per call
 constexpr int kNaWindow = 4;          // window bits
-constexpr size_t kNaYWords = 2 * kNaMaxCount * kMaxL;                       // y[2][count][L]
-constexpr size_t kNaTblWords = (size_t)148 * 32 * 16 * kMaxL;  // 16 table entries for 4736 instances at L = 96
+constexpr size_t kNaYWords = 2 * kNaMaxCount * kMaxL;  // y[2][count][L]
+// Window tables for this many instances running at once (each instance owns
+// table_entries(kNaWindow) = 8 entries of up to kMaxL limbs); the launch grid
+// is cut so that no more instances than this are resident, whatever the GPU.
+constexpr size_t kNaTableSlots = 4736;
+constexpr size_t kNaTblWords = kNaTableSlots * table_entries(kNaWindow) * kMaxL;
 constexpr int kNaMaxDevices = 64;
 
 static __device__ __align__(256) uint32_t g_na_scratch[kNaYWords + kNaTblWords];

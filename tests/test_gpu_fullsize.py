@@ -7,7 +7,8 @@ one, plus properties that hold at any size:
   histogram cell equal to the plaintext fixed-point histogram (so every
   ciphertext is consistent through the homomorphism); EVERY root cell (15,360
   products of about 1,000 ciphertexts each) bit-exact vs the oracle's product;
-  8 sampled decryptions vs the lambda form.
+  8 sampled decryptions vs the lambda form; every decoded float64 cell equal
+  to the oracle's exact decode.
 * batched workload (same data, depth-6 Beta(0.5, 0.5) tree): every level
   through the captured graph, every decrypted cell of every level equal to the
   plaintext histogram; 4,096 distinct sampled cells of every level below the
@@ -78,6 +79,13 @@ def test_level_root_histogram_every_cell_and_sampled_products(level, tmp_path):
     ps, pc = oracle.plain_histogram_np(level["m"][:M], level["m"][M:], level["bins"], np.zeros(M, np.int64), 1, K)
     assert np.array_equal(sums.cpu().numpy().reshape(1, F, K, 2), ps)
     assert np.array_equal(cnt.cpu().numpy(), pc)
+    # A9: every decoded cell (g and h) equals the oracle's exact decode, rounded once to float64
+    cnt2 = cnt.reshape(1, F, K, 1).expand(1, F, K, 2).contiguous()
+    dec = P.decode(sums.reshape(-1), cnt2.reshape(-1))
+    P.sync()
+    want_dec = [float(oracle.decode(int(s_), int(c_)))
+                for s_, c_ in zip(ps.reshape(-1).tolist(), cnt2.reshape(-1).cpu().tolist())]
+    assert dec.cpu().numpy().tolist() == want_dec
     # every cell (g and h) of the root: the oracle's product of the cell's ciphertexts
     rng = synth.rng_misc(22)
     cells = sample_cells(rng, [0], F, K, F * K * 2)

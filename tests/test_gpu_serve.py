@@ -1,5 +1,7 @@
 """GPU tests of the serving loop: concurrent (continuous-batching) execution
-gives every request the same bits as running it alone and as the direct API;
+gives every request the same bits as running it alone and as the direct API,
+with 1024-, 2048- and 3072-bit keys in one mix (the 3072-bit kernels overlap
+the 2048-bit ones);
 admission respects the HBM budget; queued requests can be cancelled; a bad
 request fails on its own without disturbing the others."""
 
@@ -35,12 +37,13 @@ def _dataset(n_bits, seed):
 
 @pytest.fixture(scope="module")
 def data():
-    return {1024: _dataset(1024, 1), 2048: _dataset(2048, 2)}
+    return {1024: _dataset(1024, 1), 2048: _dataset(2048, 2), 3072: _dataset(3072, 3)}
 
 
-REQUESTS = [  # (n_bits, M, F, K, use_node)
-    (1024, 3000, 6, 16, False), (2048, 1200, 4, 8, False), (1024, 17, 2, 8, True), (2048, 3000, 6, 16, True),
-    (1024, 2500, 5, 16, True), (2048, 1, 1, 8, False), (1024, 999, 3, 8, False), (2048, 2047, 6, 16, False),
+REQUESTS = [  # (n_bits, M, F, K, use_node); 3072-bit requests run beside 2048-bit ones (mixed key lengths)
+    (1024, 3000, 6, 16, False), (3072, 2000, 5, 16, True), (2048, 1200, 4, 8, False), (1024, 17, 2, 8, True),
+    (2048, 3000, 6, 16, True), (3072, 3000, 6, 8, False), (1024, 2500, 5, 16, True), (2048, 1, 1, 8, False),
+    (1024, 999, 3, 8, False), (2048, 2047, 6, 16, False), (3072, 1, 1, 8, False),
 ]
 
 

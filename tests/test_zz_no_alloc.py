@@ -33,7 +33,7 @@ def _noalloc(key, ct):
     return out
 
 
-@pytest.mark.parametrize("n_bits,seed", [(1024, 1), (2048, 2)])
+@pytest.mark.parametrize("n_bits,seed", [(1024, 1), (2048, 2), (3072, 5)])
 def test_noalloc_decrypt_equals_regular_on_two_calls(n_bits, seed):
     p, q = synth.gen_primes(n_bits, seed)
     key = P.Key.from_primes(n_bits, p, q)
