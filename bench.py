@@ -681,10 +681,9 @@ def run_horizontal(args, cfg):
                                 "sample": f"one client plaintext (encode + encrypt) and one aggregate (sum of "
                                           f"{clients}, decrypt + decode), scaled to the round's {clients * msgs} "
                                           f"and {msgs}; {wall:.1f} s wall"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return line if rank == 0 else None
 
 
 def run_reference_horizontal(args, cfg):
@@ -706,6 +705,129 @@ def run_reference_horizontal(args, cfg):
         "e2e": {"value": rate, "unit": "rounds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_sharded(args, cfg):
+    """N > 1: one level job split over the ranks (paper_2504_03909_b300.shard):
+    rank k encrypts samples [k M / N, (k + 1) M / N), an NCCL all-gather hands
+    every ciphertext to every rank, rank k aggregates and decrypts the features
+    [k F / N, (k + 1) F / N), and the decrypted sums are gathered.  The total
+    work is that of one level whatever N (strong scaling)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2504_03909_b300 import native, paillier as P, shard
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    M, F, K, n_bits = cfg["M"], cfg["F"], cfg["K"], cfg["n_bits"]
+    L = n_bits // 32
+    p, q, gh, r, bins = make_inputs(cfg)
+    key = P.Key.from_primes(n_bits, p, q)
+    s_lo, s_hi = shard.block_range(M, world, rank)
+    f_lo, f_hi = shard.block_range(F, world, rank)
+    ms_, fk = s_hi - s_lo, f_hi - f_lo
+    # this rank's inputs: its samples' g/h and randomness, its features' bins (all samples)
+    h_v = torch.from_numpy(np.concatenate([gh[0, s_lo:s_hi], gh[1, s_lo:s_hi]])).pin_memory()
+    r32 = r.view(np.int32).reshape(2 * M, L)
+    h_r = torch.from_numpy(np.concatenate([r32[s_lo:s_hi], r32[M + s_lo:M + s_hi]])).pin_memory()
+    h_bins = torch.from_numpy(np.ascontiguousarray(bins[f_lo:f_hi])).pin_memory()
+    h_node = torch.zeros(M, dtype=torch.int32).pin_memory()
+    v, r_d, bins_d, node = h_v.to(dev), h_r.to(dev), h_bins.to(dev), h_node.to(dev)
+    ct_loc = torch.empty((2 * ms_, 2 * L), dtype=torch.int32, device=dev)
+    hist = torch.empty((1, fk, K, 2, 2 * L), dtype=torch.int32, device=dev)
+    cnt = torch.empty((1, fk, K), dtype=torch.int32, device=dev)
+    sums = torch.empty((1, fk, K, 2), dtype=torch.int64, device=dev)
+    cnt2 = torch.empty((1, fk, K, 2), dtype=torch.int32, device=dev)
+    out = torch.empty((1, fk, K, 2), dtype=torch.float64, device=dev)
+    h_out = torch.empty(out.shape, dtype=torch.float64).pin_memory()
+
+    def encrypt(_range):
+        P.encrypt(key, P.encode(v), r_d, out=ct_loc)
+        return ct_loc.view(2, ms_, 2 * L)
+
+    def prepare(ct):
+        return P.ct_prepare(key, ct.reshape(2 * M, 2 * L)).view(2, M, 2 * L)
+
+    def aggregate(ctm, a, b):
+        return P.hist_aggregate(key, ctm, bins_d, node, 1, K, hist=hist, count=cnt)
+
+    def decrypt(h):
+        P.decrypt_u64(key, h.view(-1, 2 * L), out=sums.view(-1))
+        cnt2.copy_(cnt.unsqueeze(-1).expand(1, fk, K, 2))
+        P.decode(sums, cnt2, out=out)
+        return sums
+
+    ops = shard.LevelOps(encrypt=encrypt, prepare=prepare, aggregate=aggregate, decrypt=decrypt,
+                         empty_rows=lambda n: torch.empty((2, n, 2 * L), dtype=torch.int32, device=dev))
+
+    def step():
+        return shard.run_level(ops, dist, world, rank, M, F)
+
+    def barrier():
+        torch.cuda.synchronize()
+        dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    P.sync()
+    n0 = native.lib().paillier_launch_count()
+    barrier()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            full = step()[0]
+        e1.record()
+        barrier()
+    launches = native.lib().paillier_launch_count() - n0
+    elapsed = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
+    P.sync()
+    # untimed: the gathered sums equal the plaintext sums of every feature
+    v_all = torch.from_numpy(gh.reshape(-1).copy()).to(dev)
+    want, _ = plaintext_root_sums(P, torch, v_all, torch.from_numpy(bins).to(dev), M, F, K)
+    if not torch.equal(full.view(F * K, 2), want):
+        raise RuntimeError("sharded sums differ from the plaintext sums")
+    # end to end: each rank's input slices in from pinned host memory, its decoded block out
+    h2d_rank = h_v.numel() * 4 + h_r.numel() * 4 + h_bins.numel() + h_node.numel() * 4
+    d2h_rank = h_out.numel() * 8
+    tot = torch.tensor([h2d_rank, d2h_rank], dtype=torch.float64, device=dev)
+    dist.all_reduce(tot)
+    barrier()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for _ in range(args.steps):
+        v.copy_(h_v, non_blocking=True)
+        r_d.copy_(h_r, non_blocking=True)
+        bins_d.copy_(h_bins, non_blocking=True)
+        node.copy_(h_node, non_blocking=True)
+        step()
+        h_out.copy_(out, non_blocking=True)
+    e3.record()
+    barrier()
+    e2e_s = max_over_ranks(e2.elapsed_time(e3) / 1e3, dist, dev)
+    launches_max = max_over_ranks(float(launches), dist, dev)
+    line = {
+        "metric": METRIC, "value": 2 * M * args.steps / elapsed, "unit": "enc/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded: logistic g/h, Bernoulli(0.3) labels, N(0,1) features quantile-binned)",
+        "config": dict(workload_config(args.config, cfg),
+                       parallelism=f"sharded over {world} GPUs: samples for encryption, NCCL all-gather of the "
+                                   "ciphertext rows, features for aggregation and decryption, gather of the sums"),
+        "clocks": clk.summary(),
+        "e2e": {"value": 2 * M * args.steps / e2e_s, "unit": "enc/s", "h2d_bytes_per_step": int(tot[0].item()),
+                "d2h_bytes_per_step": int(tot[1].item())},
+        "gpu_launches": int(launches_max * world),
+        "verified": f"gathered sums == plaintext sums of the encoded values, all {F * K * 2} cells (untimed)",
+    }
+    dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def workload_config(name, cfg):
@@ -975,17 +1097,17 @@ def run_ours(args, cfg):
             "value": rate, "unit": "enc/s", "cores": cores, "kind": "oracle",
             "sample": f"{samples} samples of the workload: {2 * samples} encryptions, {2 * samples * F} histogram "
                       f"products, {ndec} decryptions (lambda form); {wall:.1f} s wall"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return line if rank == 0 else None
 
 
-def run_batched(args, cfg):
+def run_batched(args, cfg, emit=True):
     """Depth-6 tree on the level data: encrypt once, then for every level the
     batched histogram (one captured graph, replayed per level) and the CRT
     decryption of all the level's cells; the per-node launch path is timed on
-    the same levels as the comparator."""
+    the same levels as the comparator.  Returns the JSON line (printed when
+    emit)."""
     import torch
     from paper_2504_03909_b300 import native, paillier as P
 
@@ -1191,11 +1313,12 @@ def run_batched(args, cfg):
         "verified": f"root histogram of the step's ciphertexts, decrypted, == plaintext sums of the encoded "
                     f"values, all {F * K * 2} cells and counts (untimed)",
     }
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
+    return line
 
 
-def run_serving(args, cfg):
+def run_serving(args, cfg, emit=True):
     """Four simulated passive parties send Poisson-arriving histogram + decrypt
     requests (M log-uniform in [1e3, 1e6], F uniform in [8, 64], K uniform on
     {64, 96, ..., 256}, 2048- or 3072-bit key with p = 0.5) to one server; the
@@ -1292,10 +1415,12 @@ def run_serving(args, cfg):
             if dt > 0:
                 time.sleep(dt)
             tickets.append(submit(srv, rq)[0])
-        for t in tickets:
+        done_rq = []
+        for t, rq in zip(tickets, reqs):
             st, lat = srv.wait(t)
             if st == native.REQ_DONE:
                 done_lat.append(lat)
+                done_rq.append(rq)
             srv.release(t)
         wall = time.perf_counter() - t_start
     stats = srv.stats()
@@ -1313,12 +1438,68 @@ def run_serving(args, cfg):
                    "hbm_budget_bytes": budget, "offered_load": args.load, "requests": args.requests,
                    "pack_bits": args.pack_bits, "gh_bits": args.gh_bits},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "by_size": serving_classes(done_rq, lat, work),
         "mean_ms": float(lat.mean()), "throughput_req_per_s": len(lat) / wall,
         "capacity_req_per_s": capacity, "arrival_rate_req_per_s": rate,
         "ct_mults_per_s": work_mults / wall, "decrypts_per_s": work_cells / wall,
         "server": stats, "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def serving_classes(reqs, lat, work):
+    """p50/p99 latency per request size class (thirds of the modelled work
+    distribution's log range: small, medium, large), beside each class's
+    median modelled work."""
+    if not reqs:
+        return {}
+    wk = np.array([work(rq) for rq in reqs], dtype=np.float64)
+    lw = np.log(wk)
+    edges = np.quantile(lw, [1 / 3, 2 / 3])
+    out = {}
+    for name, sel in (("small", lw <= edges[0]), ("medium", (lw > edges[0]) & (lw <= edges[1])),
+                      ("large", lw > edges[1])):
+        if sel.any():
+            out[name] = {"n": int(sel.sum()), "p50_ms": float(np.percentile(lat[sel], 50)),
+                         "p99_ms": float(np.percentile(lat[sel], 99)),
+                         "median_work_TIMAD": float(np.median(wk[sel])) / 1e12}
+    return out
+
+
+def run_legs(args, line):
+    """The other two parts of the metric, measured after the level headline in
+    the same run (one GPU): the batched depth-6 tree (one captured graph per
+    level, autotuned launch configurations) against the plain per-node launch
+    path, and the serving loop's p50/p99 request latency at offered load 0.7."""
+    import torch
+    torch.cuda.empty_cache()
+    ba = argparse.Namespace(**vars(args))
+    ba.config, ba.steps, ba.warmup, ba.autotune = "batched", 2, 1, True
+    ba.gh_bits, ba.pack_bits, ba.splits, ba.subtract, ba.no_compare = 0, 0, "beta", False, False
+    b = run_batched(ba, synth.CONFIGS["batched"], emit=False)
+    line["batched"] = {
+        "workload": b["config"]["workload"], "autotuned": b["config"]["autotuned"],
+        "configs": b["config"]["configs"],
+        "hist_batched_ms_per_tree": b["hist_batched_ms_per_tree"],
+        "hist_per_node_ms_per_tree": b["hist_per_node_ms_per_tree"],
+        "speedup_vs_per_node": b["batched_speedup_vs_per_node"],
+        "ct_mults_per_s_batched": b["value"], "tree_ms": b["tree_ms"], "phases_ms_per_tree": b["phases_ms_per_tree"],
+        "steps": ba.steps, "warmup": ba.warmup, "clocks": b["clocks"], "verified": b["verified"],
+    }
+    torch.cuda.empty_cache()
+    sa = argparse.Namespace(**vars(args))
+    sa.config, sa.requests, sa.load, sa.slots = "serving", args.serve_requests, 0.7, 8
+    sa.gh_bits, sa.pack_bits = args.serve_gh_bits, args.serve_pack_bits
+    sv = run_serving(sa, synth.CONFIGS.get("serving", {}), emit=False)
+    line["serving"] = {
+        "workload": sv["config"]["workload"], "offered_load": sa.load, "requests": sa.requests, "slots": sa.slots,
+        "gh_bits": sa.gh_bits, "pack_bits": sa.pack_bits,
+        "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "mean_ms": sv["mean_ms"], "by_size": sv["by_size"],
+        "throughput_req_per_s": sv["throughput_req_per_s"], "capacity_req_per_s": sv["capacity_req_per_s"],
+        "server": sv["server"], "clocks": sv["clocks"],
+    }
 
 
 def main():
@@ -1344,6 +1525,11 @@ def main():
                     help="g/h packing, one plaintext enc(g) + 2^B enc(h) per sample (B bits; 0 = off): tree and "
                          "serving modes use it instead of two ciphertexts per sample; the level mode reports it "
                          "beside the headline (default 45 there, 0 elsewhere)")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="level: skip the batched-tree and serving legs measured after the headline")
+    ap.add_argument("--serve-requests", type=int, default=300, help="serving leg of the level run: timed requests")
+    ap.add_argument("--serve-gh-bits", type=int, default=0, help="serving leg: g/h packing bits (0 = two arrays)")
+    ap.add_argument("--serve-pack-bits", type=int, default=46, help="serving leg: ciphertext packing bits")
     args = ap.parse_args()
     cfg = synth.CONFIGS.get(args.config, {})
     if args.gh_bits is None:
@@ -1362,8 +1548,14 @@ def main():
         run_serving(args, cfg)
     elif args.config == "large":
         run_batched(args, cfg)
+    elif int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.config == "level":
+        run_sharded(args, cfg)
     else:
-        run_ours(args, cfg)
+        line = run_ours(args, cfg)
+        if line is not None:
+            if args.gpus == 1 and not args.no_legs and args.config == "level":
+                run_legs(args, line)
+            print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -64,7 +64,9 @@ __global__ void k_decode(const uint64_t* __restrict__ s, const int32_t* __restri
 // acc: the base in Montgomery form on entry, base^e in Montgomery form on exit,
 // e given by its schedule op[0..nop) (layout in ModexpParams).  tbl: this
 // group's table of 2^(w-1) entries of S*T limbs (the odd powers); bs: its
-// shared-memory column.  Every op is one Montgomery product.
+// shared-memory column.  Every op is one Montgomery product (mont_mul, the
+// squarings included: the balanced squaring mont_sqr forms 18 % fewer
+// instructions here but runs slower in this loop, see mp.cuh).
 template <int S, int T>
 PL_DEV void window_exp(uint32_t (&acc)[S], const uint32_t (&n)[S], uint32_t np, const uint8_t* op, int nop, int w,
                        uint32_t* tbl, uint32_t* bs, int st, int k) {

@@ -74,6 +74,54 @@ def test_mont_mul_random_and_edges(limbs, lanes):
         assert not bad, f"N={N:#x} first bad index {bad[0]}: a={A[bad[0]]:#x} b={B[bad[0]]:#x}"
 
 
+SQR_LANES = [(32, 2), (32, 4), (64, 4), (64, 8), (96, 4), (96, 8)]
+
+
+def _sqr_gpu(limbs, lanes, N, A):
+    a = _dev(synth.ints_to_limbs(A, limbs))
+    out = torch.empty_like(a)
+    Nl = synth.int_to_limbs(N, limbs)
+    native.call("paillier_test_mont_sqr", limbs, lanes, Nl.ctypes.data, a.data_ptr(), len(A), out.data_ptr(),
+                torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return synth.limbs_to_ints(P.from_limb_tensor(out))
+
+
+@pytest.mark.parametrize("limbs,lanes", SQR_LANES)
+def test_mont_sqr_random_and_edges(limbs, lanes):
+    """The squaring path of the exponentiations (each cross product formed
+    once, chunk products spread over the lanes) equals a^2 R^-1 mod N on the
+    moduli and edge inputs of the product test: all-ones limbs (N = R - 1, so
+    (P + M N) / R reaches its 2N bound), top limb 1 or 2, a composite N with
+    squares = 0 mod N, long carry chains, and values with all-ones or zero
+    chunks (every lane's share of the cross products at its extremes)."""
+    rng = random.Random(limbs * 1000 + lanes)
+    R = 1 << (32 * limbs)
+    S = limbs // lanes
+    p = rng.randrange(1 << (16 * limbs - 2), 1 << (16 * limbs - 1)) | 1
+    q = rng.randrange(1 << (16 * limbs), 1 << (16 * limbs + 1)) | 1
+    moduli = [rng.randrange(R // 2, R) | 1, R - 1, rng.randrange(1 << (32 * limbs - 31), 1 << (32 * limbs - 30)) | 1,
+              p * q]
+    for N in moduli:
+        A = [0, 1, 2, N - 1, N - 2, N // 2, (1 << 32) - 1, R // 2 % N, (R - 1) % N, (N - 1) // 3]
+        if N == p * q:
+            # multiples of q and of p: squares sharing a factor with N
+            A += [q * rng.randrange(1, p) for _ in range(32)]
+            A += [N - p * rng.randrange(1, q) for _ in range(32)]
+        # one lane's chunk all ones, the others zero (and the complement)
+        for k in range(lanes):
+            chunk = ((1 << (32 * S)) - 1) << (32 * S * k)
+            A += [chunk % N, (R - 1 - chunk) % N]
+        for s in (1, limbs // 2, limbs - 1):
+            A.append(((1 << (32 * s)) - 1) % N)
+        A += [rng.randrange(N) for _ in range(1500)]
+        got = _sqr_gpu(limbs, lanes, N, A)
+        Rinv = pow(R, -1, N)
+        want = [a * a * Rinv % N for a in A]
+        bad = [i for i in range(len(A)) if got[i] != want[i]]
+        assert not bad, f"N={N:#x} first bad index {bad[0]}: a={A[bad[0]]:#x}"
+
+
 # ---------------------------------------------------------------------------
 # toy workload (1,000 samples, 8 features x 16 bins, 1024-bit n): full parity
 
