@@ -94,6 +94,37 @@ pl_status pl_server_request_bytes(const pl_request* req, size_t* bytes);
 /* Cancels a request that is still queued (PL_EINVAL if it was admitted). */
 pl_status pl_server_cancel(pl_server* srv, uint64_t ticket);
 
+/* Device scheduling and admission policy of the server (this project's
+ * serving design; the paper has no serving loop).
+ *   * Launches of bounded work.  The exponentiation and histogram kernels are
+ *     persistent, so one launch of a large request holds every SM until it
+ *     ends.  A request's work is issued as launches of at most chunk_imad
+ *     modelled 32-bit multiply-add halves each: the histogram of a request
+ *     without a node array by groups of features, packing and decryption by
+ *     ranges of ciphertexts (a decryption launch takes at least 2,048).
+ *   * Size classes.  A request whose whole modelled work is below small_imad
+ *     is small, above large_imad large, else medium.  Each class runs on a
+ *     stream of its own priority (small highest), so at every launch boundary
+ *     the device schedules the smaller classes' pending blocks first.
+ *   * Admission.  FIFO within each class: a request that cannot start (no
+ *     budget, or no slot for its class) holds back only the later requests of
+ *     its class.  Medium and large requests together hold at most
+ *     slots - reserved_slots slots, so small requests find a slot in time.
+ * Results do not depend on the policy (every launch forms the same cells).
+ * Defaults: chunk_imad = small_imad = 3e11 and large_imad = 3e12 (about 25 ms
+ * and 250 ms of work on a B300), reserved_slots = max(1, slots / 4) (0 for one
+ * slot).  Applies to requests submitted after the call.  PL_EINVAL unless
+ * chunk_imad > 0, 0 <= small_imad <= large_imad and 0 <= reserved_slots < slots. */
+pl_status pl_server_set_policy(pl_server* srv, double chunk_imad, double small_imad, double large_imad,
+                               int reserved_slots);
+
+/* Policy counters: per_class[3] requests admitted per size class (small,
+ * medium, large; may be NULL), launch groups issued (histogram feature groups,
+ * packing and decryption ranges), and the peak number of medium and large
+ * requests running at once. */
+pl_status pl_server_policy_stats(pl_server* srv, long long* per_class, long long* launch_groups,
+                                 int* peak_nonsmall);
+
 /* Counters: submitted, completed, failed, cancelled, peak concurrently
  * running requests, peak bytes in flight. */
 pl_status pl_server_stats(pl_server* srv, long long* submitted, long long* completed, long long* failed,

@@ -1,9 +1,32 @@
 // Continuous-batching request loop: FIFO admission by free slot and HBM
 // budget, concurrent execution on per-slot streams, completion by event query.
+//
+// Scheduling on the device.  The exponentiation and segmented-product kernels
+// are persistent (a grid of the resident blocks loops over the work), so one
+// launch of a large request holds every SM until it ends; a small request that
+// arrives meanwhile waits for it (measured before this policy: requests of
+// about 5 ms of work had a p50 of 159 ms and a p99 of 1.8 s at offered load
+// 0.7).  Two rules bound that wait:
+//   * a request's work is issued as launches of at most `chunk_imad` modelled
+//     multiply-adds each (the histogram by groups of features, packing and
+//     decryption by ranges of ciphertexts), so the GPU changes hands at least
+//     every few tens of milliseconds; every launch computes the same cells as
+//     one launch would, so the results are the same bits;
+//   * requests run on a stream of their size class's priority (small: below
+//     `small_imad`; large: above `large_imad`; medium between): at each such
+//     boundary the block scheduler takes the pending blocks of the smaller
+//     class first.
+// Admission: FIFO within each class, so a small request may pass a medium or
+// large one that cannot start; medium and large requests together hold at most
+// slots - `reserved` slots, so that small requests always find one free in
+// time (measured with FIFO admission over all classes: small requests had a
+// p99 of 1.8 s, waiting for one of 8 slots held by long requests).
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <functional>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -20,6 +43,7 @@ double now_ms() {
 
 struct Req {
   pl_request r{};
+  int cls = 0;  // size class: 0 small, 1 medium, 2 large
   int state = PL_REQ_QUEUED;
   int err = PL_OK;
   double t_submit = 0, latency = -1;
@@ -27,7 +51,18 @@ struct Req {
 };
 
 struct Slot {
-  cudaStream_t s = nullptr;
+  cudaStream_t cs[3] = {};  // one stream per size class, in decreasing priority
+  cudaStream_t s = nullptr;  // the stream of the request it runs
+  int cls = 0;               // that request's class
+  // the request's launch groups, issued by the server loop at most two ahead of
+  // the device (step_ev[i & 1] is recorded after group i); `last` copies the
+  // results out, frees the request's memory and records `done`
+  std::vector<std::function<pl_status()>> plan;
+  std::function<void(pl_status)> last;
+  size_t next = 0;
+  bool issued_all = false;
+  pl_status err = PL_OK;
+  cudaEvent_t step_ev[2] = {};
   cudaEvent_t done = nullptr;
   bool busy = false;
   uint64_t req = 0;
@@ -60,6 +95,45 @@ size_t request_bytes(const pl_request& r) {
   return b;
 }
 
+// modelled multiply-adds (IMAD: one 32-bit half of a limb product) of the pieces of a request
+double mont_imad(double nl) { return 4 * nl * nl + nl; }
+double dec_imad(const pl_key* key) {
+  // two CRT halves, about n_bits / 2 (1 + 1/6) products on L limbs each (sliding 6-bit windows)
+  const double L = key->L;
+  return 2.0 * (key->n_bits / 2.0) * (7.0 / 6.0) * mont_imad(L);
+}
+struct Work {
+  double hist_per_feature, pack_per_ct, dec_per_ct, total;
+};
+Work request_work(const pl_request& r) {
+  const double L2 = 2.0 * r.key->L;
+  const int ngh = r.gh_bits ? 1 : 2;
+  const double hcells = (double)r.num_nodes * r.F * r.K * ngh;
+  Work w{};
+  w.hist_per_feature = (double)ngh * (double)r.M * mont_imad(L2);
+  w.dec_per_ct = dec_imad(r.key);
+  double dec_cts = hcells;
+  if (r.pack_bits > 0) {
+    const int slot_bits = r.gh_bits ? 2 * r.gh_bits : r.pack_bits;
+    const double slots = (double)((r.key->n_bits - 2) / slot_bits);
+    w.pack_per_ct = slots * (slot_bits + 1) * mont_imad(L2);
+    dec_cts = std::ceil(hcells / slots);
+    w.total += dec_cts * w.pack_per_ct;
+  }
+  w.total += r.F * w.hist_per_feature + dec_cts * w.dec_per_ct;
+  return w;
+}
+
+// smallest decryption launch of a split request: about half a wave of the
+// 3072-bit exponentiation kernel, so that splitting costs little throughput
+constexpr size_t kDecryptLaunchMin = 2048;
+
+// items per launch so that one launch stays within `budget` (at least `floor_items`)
+size_t per_launch(double budget, double per_item, size_t floor_items) {
+  const double n = per_item > 0 ? std::floor(budget / per_item) : 1e18;
+  return std::max<size_t>(floor_items, (size_t)std::max(1.0, std::min(n, 1e15)));
+}
+
 }  // namespace
 
 struct pl_server {
@@ -75,8 +149,20 @@ struct pl_server {
   uint64_t next_id = 1;
   long long n_sub = 0, n_done = 0, n_fail = 0, n_cancel = 0;
   int running = 0, peak_running = 0;
+  // launch-size, priority and admission policy (see the top of this file)
+  double chunk_imad = 0.3e12, small_imad = 0.3e12, large_imad = 3e12;
+  int reserved = 0;
+  long long n_class[3] = {0, 0, 0}, n_launch_groups = 0;
+  int running_cls[3] = {0, 0, 0};
+  int peak_nonsmall = 0;
+
+  int classify(const pl_request& r) const {
+    const double w = request_work(r).total;
+    return w < small_imad ? 0 : (w <= large_imad ? 1 : 2);
+  }
 
   void finish(Slot& sl, int err) {
+    if (err == PL_OK) err = sl.err;
     Req& q = reqs[sl.req];
     q.latency = now_ms() - q.t_submit;
     if (err == PL_OK && *sl.h_status != 0) err = (*sl.h_status & pl::kStatusRange) ? PL_ERANGE : PL_EDEVICE;
@@ -86,20 +172,30 @@ struct pl_server {
     in_flight -= q.bytes;
     sl.busy = false;
     --running;
+    --running_cls[sl.cls];
     done_cv.notify_all();
   }
 
-  // enqueue one request on a slot's stream; returns a status (the slot stays
-  // busy until its completion event, even after a launch error, so that
-  // stream-ordered frees have run before the slot is reused)
-  pl_status launch(Slot& sl, Req& q) {
+  // Sets up one request on a slot: its stream, its memory and its plan of
+  // launch groups (issued later by `issue`).  The slot stays busy until its
+  // completion event, even after an error, so that the stream-ordered frees
+  // have run before the slot is reused.
+  void launch(Slot& sl, Req& q) {
     using namespace pl;
-    const pl_request& r = q.r;
+    const pl_request r = q.r;
     pl_key* key = const_cast<pl_key*>(r.key);
     const size_t L = (size_t)key->L;
     const size_t ncell = (size_t)r.num_nodes * r.F * r.K;
     const size_t cells = ncell * 2;
+    const Work wk = request_work(r);
+    sl.cls = q.cls;
+    sl.s = sl.cs[q.cls];
+    sl.plan.clear();
+    sl.next = 0;
+    sl.issued_all = false;
+    sl.err = PL_OK;
     cudaStream_t s = sl.s;
+    Slot* slp = &sl;
     for (auto& a : sl.allocs) a = nullptr;
     pl_status rc = PL_OK;
     auto amalloc = [&](int i, size_t bytes) -> void* {
@@ -117,79 +213,145 @@ struct pl_server {
     auto* sums = static_cast<uint64_t*>(amalloc(2, cells * 8));
     const int32_t* node = r.d_node;
     if (!node) node = static_cast<int32_t*>(amalloc(3, r.M * 4));
-    if (rc == PL_OK) {
-      cudaMemsetAsync(sl.d_status, 0, sizeof(int), s);
-      if (!r.d_node) cudaMemsetAsync(const_cast<int32_t*>(node), 0, r.M * 4, s);
-      rc = launch_hist(key, r.d_ctm, r.M, r.gh_stride, r.d_bins, r.bins_stride, r.F, r.K, node, r.num_nodes, hist,
-                       counts, false, sl.d_status, s, &sl.scratch, ngh);
+    const int slot_bits = r.pack_bits > 0 ? (r.gh_bits ? 2 * r.gh_bits : r.pack_bits) : 0;
+    const int slots = slot_bits ? (key->n_bits - 2) / slot_bits : 0;
+    const size_t npacked = slots ? (hcells + slots - 1) / slots : 0;
+    uint32_t* packed = nullptr;
+    uint32_t* plain = nullptr;
+    if (slots) {
+      packed = static_cast<uint32_t*>(amalloc(4, npacked * 2 * L * 4));
+      plain = static_cast<uint32_t*>(amalloc(5, npacked * L * 4));
+    } else if (r.gh_bits) {
+      plain = static_cast<uint32_t*>(amalloc(5, hcells * L * 4));
     }
-    if (rc == PL_OK && r.pack_bits > 0) {
-      const int slot_bits = r.gh_bits ? 2 * r.gh_bits : r.pack_bits;
-      const int slots = (key->n_bits - 2) / slot_bits;
-      const size_t npacked = (hcells + slots - 1) / slots;
-      auto* packed = static_cast<uint32_t*>(amalloc(4, npacked * 2 * L * 4));
-      auto* plain = static_cast<uint32_t*>(amalloc(5, npacked * L * 4));
-      if (rc == PL_OK) rc = launch_pack(key, hist, hcells, slots, slot_bits, packed, s);
-      if (rc == PL_OK) rc = launch_decrypt(key, packed, npacked, plain, false, sl.d_status, s, &sl.scratch);
-      if (rc == PL_OK)  // g/h cells: each 2B-bit slot is two B-bit sums
-        rc = r.gh_bits ? launch_unpack(plain, (int)L, cells, 2 * slots, r.gh_bits, sums, sl.d_status, s)
-                       : launch_unpack(plain, (int)L, cells, slots, r.pack_bits, sums, sl.d_status, s);
-    } else if (rc == PL_OK && r.gh_bits) {
-      auto* plain = static_cast<uint32_t*>(amalloc(5, hcells * L * 4));
-      if (rc == PL_OK) rc = launch_decrypt(key, hist, hcells, plain, false, sl.d_status, s, &sl.scratch);
-      if (rc == PL_OK) rc = launch_unpack(plain, (int)L, cells, 2, r.gh_bits, sums, sl.d_status, s);
-    } else if (rc == PL_OK) {
-      rc = launch_decrypt(key, hist, cells, sums, true, sl.d_status, s, &sl.scratch);
+    // results out, memory freed, completion recorded (run once, after the last group or an error)
+    sl.last = [slp, r, s, sums, counts, cells, ncell](pl_status err) {
+      if (err == PL_OK) {
+        cudaMemcpyAsync(r.h_sums, sums, cells * 8, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(r.h_counts, counts, ncell * 4, cudaMemcpyDeviceToHost, s);
+      }
+      cudaMemcpyAsync(slp->h_status, slp->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+      for (auto& a : slp->allocs)
+        if (a) cudaFreeAsync(a, s);
+      slp->scratch.release(s);
+      cudaEventRecord(slp->done, s);
+    };
+    if (rc != PL_OK) {
+      sl.err = rc;
+      return;
     }
-    if (rc == PL_OK) {
-      cudaMemcpyAsync(r.h_sums, sums, cells * 8, cudaMemcpyDeviceToHost, s);
-      cudaMemcpyAsync(r.h_counts, counts, ncell * 4, cudaMemcpyDeviceToHost, s);
+    cudaMemsetAsync(sl.d_status, 0, sizeof(int), s);
+    if (!r.d_node) cudaMemsetAsync(const_cast<int32_t*>(node), 0, r.M * 4, s);
+    auto& plan = sl.plan;
+    // the histogram: a root-only request in groups of features (its cells are
+    // contiguous per feature); with a node array, one group
+    const size_t fg = r.num_nodes == 1 ? per_launch(chunk_imad, wk.hist_per_feature, 1) : (size_t)r.F;
+    for (size_t f0 = 0; f0 < (size_t)r.F; f0 += fg) {
+      const int nf = (int)std::min(fg, (size_t)r.F - f0);
+      plan.push_back([=]() {
+        return launch_hist(key, r.d_ctm, r.M, r.gh_stride, r.d_bins + f0 * r.bins_stride, r.bins_stride, nf, r.K,
+                           node, r.num_nodes, hist + f0 * r.K * ngh * 2 * L, counts + f0 * r.K, false,
+                           slp->d_status, s, &slp->scratch, ngh);
+      });
     }
-    cudaMemcpyAsync(sl.h_status, sl.d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
-    for (auto& a : sl.allocs)
-      if (a) cudaFreeAsync(a, s);
-    sl.scratch.release(s);
-    cudaEventRecord(sl.done, s);
-    return rc;
+    // decryption of n ciphertexts at `in` in ranges of bounded work (at least
+    // kDecryptLaunchMin per launch); u64: 64-bit outputs, else L-limb plaintexts
+    auto decrypt_ranges = [&](const uint32_t* in, size_t n, void* out, bool u64) {
+      const size_t step = per_launch(chunk_imad, wk.dec_per_ct, kDecryptLaunchMin);
+      for (size_t c0 = 0; c0 < n; c0 += step) {
+        const size_t nc = std::min(step, n - c0);
+        void* o = u64 ? static_cast<void*>(static_cast<uint64_t*>(out) + c0)
+                      : static_cast<void*>(static_cast<uint32_t*>(out) + c0 * L);
+        const uint32_t* src = in + c0 * 2 * L;
+        plan.push_back([=]() { return launch_decrypt(key, src, nc, o, u64, slp->d_status, s, &slp->scratch); });
+      }
+    };
+    if (slots) {
+      // packing in ranges of whole packed ciphertexts
+      const size_t pstep = per_launch(chunk_imad, wk.pack_per_ct, 1);
+      for (size_t p0 = 0; p0 < npacked; p0 += pstep) {
+        const size_t np_ = std::min(pstep, npacked - p0);
+        const size_t c0 = p0 * (size_t)slots;
+        const size_t nc = std::min(np_ * (size_t)slots, hcells - c0);
+        plan.push_back([=]() {
+          return launch_pack(key, hist + c0 * 2 * L, nc, slots, slot_bits, packed + p0 * 2 * L, s);
+        });
+      }
+      decrypt_ranges(packed, npacked, plain, false);
+      // g/h cells: each 2B-bit slot is two B-bit sums
+      const int uslots = r.gh_bits ? 2 * slots : slots;
+      const int ubits = r.gh_bits ? r.gh_bits : r.pack_bits;
+      plan.push_back([=]() { return launch_unpack(plain, (int)L, cells, uslots, ubits, sums, slp->d_status, s); });
+    } else if (r.gh_bits) {
+      decrypt_ranges(hist, hcells, plain, false);
+      plan.push_back([=]() { return launch_unpack(plain, (int)L, cells, 2, r.gh_bits, sums, slp->d_status, s); });
+    } else {
+      decrypt_ranges(hist, cells, sums, true);
+    }
+    n_launch_groups += (long long)plan.size();
+  }
+
+  // Issues the slot's next launch groups while at most two are in flight on
+  // the device; after the last group (or an error) runs `last`.
+  void issue(Slot& sl) {
+    while (!sl.issued_all) {
+      if (sl.err != PL_OK || sl.next == sl.plan.size()) {
+        sl.last(sl.err);
+        sl.issued_all = true;
+        break;
+      }
+      if (sl.next >= 2 && cudaEventQuery(sl.step_ev[sl.next & 1]) == cudaErrorNotReady) break;
+      const pl_status rc = sl.plan[sl.next]();
+      cudaEventRecord(sl.step_ev[sl.next & 1], sl.s);
+      ++sl.next;
+      if (rc != PL_OK) sl.err = rc;
+    }
   }
 
   void loop() {
     cudaSetDevice(device);
-    std::unordered_map<int, pl_status> launch_err;  // slot -> error of its launch
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
-      // completions
-      for (size_t i = 0; i < slots.size(); ++i) {
-        Slot& sl = slots[i];
-        if (!sl.busy) continue;
+      // launch groups of the running requests, then completions
+      for (auto& sl : slots)
+        if (sl.busy) issue(sl);
+      for (auto& sl : slots) {
+        if (!sl.busy || !sl.issued_all) continue;
         const cudaError_t e = cudaEventQuery(sl.done);
         if (e == cudaErrorNotReady) continue;
-        int err = e == cudaSuccess ? PL_OK : PL_ECUDA;
-        auto it = launch_err.find((int)i);
-        if (it != launch_err.end()) {
-          if (err == PL_OK) err = it->second;
-          launch_err.erase(it);
-        }
-        finish(sl, err);
+        finish(sl, e == cudaSuccess ? PL_OK : PL_ECUDA);
       }
       if (stop && queue.empty() && running == 0) break;
-      // admissions: FIFO, the head waits for a slot and for budget
-      while (!queue.empty() && !stop) {
+      // admissions: FIFO within each size class; a request that cannot start
+      // (no budget, or a medium/large one finding its share of the slots taken)
+      // holds back the later requests of its class only
+      bool blocked[3] = {false, false, false};
+      for (auto it = queue.begin(); it != queue.end() && !stop;) {
         auto fs = std::find_if(slots.begin(), slots.end(), [](const Slot& x) { return !x.busy; });
         if (fs == slots.end()) break;
-        Req& q = reqs[queue.front()];
-        if (in_flight + q.bytes > budget) break;
-        const uint64_t id = queue.front();
-        queue.pop_front();
+        Req& q = reqs[*it];
+        const int c = q.cls;
+        bool ok = !blocked[c] && in_flight + q.bytes <= budget;
+        if (ok && c != 0 && running - running_cls[0] >= (int)slots.size() - reserved) ok = false;
+        if (!ok) {
+          blocked[c] = true;
+          ++it;
+          continue;
+        }
+        const uint64_t id = *it;
+        it = queue.erase(it);
         q.state = PL_REQ_RUNNING;
         in_flight += q.bytes;
         peak_bytes = std::max(peak_bytes, in_flight);
         fs->busy = true;
         fs->req = id;
         ++running;
+        ++running_cls[c];
+        ++n_class[c];
         peak_running = std::max(peak_running, running);
-        const pl_status rc = launch(*fs, q);
-        if (rc != PL_OK) launch_err[(int)(fs - slots.begin())] = rc;
+        peak_nonsmall = std::max(peak_nonsmall, running - running_cls[0]);
+        launch(*fs, q);
+        issue(*fs);
       }
       if (running == 0 && queue.empty()) {
         if (stop) break;
@@ -221,11 +383,23 @@ pl_status pl_server_create(int slots, size_t hbm_budget, pl_server** out) {
   }
   srv->budget = hbm_budget;
   srv->slots.resize((size_t)slots);
+  srv->reserved = slots >= 2 ? std::max(1, slots / 4) : 0;
+  int prio_least = 0, prio_greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) {
+    cudaGetLastError();
+    prio_least = prio_greatest = 0;
+  }
+  // lower numbers are higher priorities: small, medium, large
+  const int prio[3] = {prio_greatest, (prio_least + prio_greatest) / 2, prio_least};
   for (auto& sl : srv->slots) {
     sl.scratch.async = true;
     sl.scratch.device = srv->device;
-    if (cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaStreamCreateWithPriority(&sl.cs[0], cudaStreamNonBlocking, prio[0]) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&sl.cs[1], cudaStreamNonBlocking, prio[1]) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&sl.cs[2], cudaStreamNonBlocking, prio[2]) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.step_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.step_ev[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&sl.d_status, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&sl.h_status, sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
@@ -233,6 +407,7 @@ pl_status pl_server_create(int slots, size_t hbm_budget, pl_server** out) {
       return fail(PL_ECUDA, "slot set-up failed");
     }
     *sl.h_status = 0;
+    sl.s = sl.cs[2];
   }
   srv->th = std::thread([srv] { srv->loop(); });
   *out = srv;
@@ -265,6 +440,7 @@ pl_status pl_server_submit(pl_server* srv, const pl_request* req, uint64_t* tick
   q.r = r;
   q.bytes = request_bytes(r);
   std::lock_guard<std::mutex> lock(srv->mu);
+  q.cls = srv->classify(r);
   if (q.bytes > srv->budget) return fail(PL_EBUSY, "request needs more device memory than the whole budget");
   q.t_submit = now_ms();
   const uint64_t id = srv->next_id++;
@@ -319,6 +495,35 @@ pl_status pl_server_cancel(pl_server* srv, uint64_t ticket) {
   return PL_OK;
 }
 
+pl_status pl_server_set_policy(pl_server* srv, double chunk_imad, double small_imad, double large_imad,
+                               int reserved_slots) {
+  using namespace pl;
+  clear_error();
+  if (!srv) return fail(PL_EINVAL, "server is NULL");
+  if (!(chunk_imad > 0) || !(small_imad >= 0) || !(large_imad >= small_imad))
+    return fail(PL_EINVAL, "need chunk_imad > 0 and 0 <= small_imad <= large_imad");
+  std::lock_guard<std::mutex> lock(srv->mu);
+  if (reserved_slots < 0 || reserved_slots >= (int)srv->slots.size())
+    return fail(PL_EINVAL, "reserved_slots must be in [0, slots)");
+  srv->chunk_imad = chunk_imad;
+  srv->small_imad = small_imad;
+  srv->large_imad = large_imad;
+  srv->reserved = reserved_slots;
+  return PL_OK;
+}
+
+pl_status pl_server_policy_stats(pl_server* srv, long long* per_class, long long* launch_groups,
+                                 int* peak_nonsmall) {
+  using namespace pl;
+  if (!srv) return fail(PL_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lock(srv->mu);
+  if (per_class)
+    for (int c = 0; c < 3; ++c) per_class[c] = srv->n_class[c];
+  if (launch_groups) *launch_groups = srv->n_launch_groups;
+  if (peak_nonsmall) *peak_nonsmall = srv->peak_nonsmall;
+  return PL_OK;
+}
+
 pl_status pl_server_stats(pl_server* srv, long long* submitted, long long* completed, long long* failed,
                           long long* cancelled, int* peak_running, size_t* peak_bytes) {
   using namespace pl;
@@ -349,11 +554,15 @@ void pl_server_destroy(pl_server* srv) {
   if (srv->th.joinable()) srv->th.join();
   cudaSetDevice(srv->device);
   for (auto& sl : srv->slots) {
-    if (sl.s) cudaStreamSynchronize(sl.s);
+    for (auto st : sl.cs)
+      if (st) cudaStreamSynchronize(st);
     if (sl.done) cudaEventDestroy(sl.done);
+    for (auto ev : sl.step_ev)
+      if (ev) cudaEventDestroy(ev);
     if (sl.d_status) cudaFree(sl.d_status);
     if (sl.h_status) cudaFreeHost(sl.h_status);
-    if (sl.s) cudaStreamDestroy(sl.s);
+    for (auto st : sl.cs)
+      if (st) cudaStreamDestroy(st);
   }
   delete srv;
 }

@@ -29,7 +29,7 @@ def _dataset(n_bits, seed):
     # the same g/h values packed one plaintext per sample (B = 38 covers 3000 samples)
     g_d, h_d = torch.from_numpy(gh[0].copy()).cuda(), torch.from_numpy(gh[1].copy()).cuda()
     ctm_gh = P.ct_prepare(key, P.encrypt_gh(key, P.encode_gh(g_d, h_d, GH_BITS), P.to_limb_tensor(r[:MFULL])))
-    bins = {K: torch.from_numpy(synth.gen_bins_uniform(FFULL, MFULL, K, seed + K)).cuda() for K in (8, 16)}
+    bins = {K: torch.from_numpy(synth.gen_bins_uniform(FFULL, MFULL, K, seed + K)).cuda() for K in (8, 16, 256)}
     node = torch.from_numpy(synth.gen_tree_levels(MFULL, 3, seed)[2]).cuda()
     P.sync()
     return dict(key=key, ctm=ctm, ctm_gh=ctm_gh, bins=bins, node=node, m=m.cpu().numpy().view(np.uint64))
@@ -180,3 +180,63 @@ def test_cancel_and_isolated_failure(data):
     assert st["failed"] == 1 and st["cancelled"] == 1 and st["completed"] == 2
     srv.close()
     P.sync()  # the library's own status word is untouched by served requests
+
+
+def test_split_launches_and_priorities_give_the_same_bits(data):
+    """The device scheduling policy (launches of bounded work, one stream
+    priority per size class) changes when the GPU changes hands, not what is
+    computed: with a budget small enough to split every request into one
+    launch per feature, packing range and decryption range (2,048 ciphertexts
+    at least), and requests in all three classes, every request gives the bits
+    of the default policy alone and of the direct API."""
+    reqs = REQUESTS + [(1024, 3000, 6, 256, False), (2048, 2500, 5, 256, False), (3072, 2000, 4, 256, False)]
+    split = P.Server(slots=4, hbm_budget=8 << 30, chunk_imad=1e7, small_imad=2e11, large_imad=2.5e11)
+    tickets = [_submit(split, data, rq) for rq in reqs]
+    nb, M, F, K, use_node = reqs[-2]
+    d = data[nb]
+    packed = split.submit(d["key"], d["ctm"], M, F, K, d["bins"][K], gh_stride=MFULL, bins_stride=MFULL,
+                          pack_bits=40)
+    gh = split.submit(d["key"], d["ctm_gh"], M, F, K, d["bins"][K], bins_stride=MFULL, gh_bits=GH_BITS,
+                      pack_bits=1)
+    got = []
+    for t, s_, c_ in tickets + [packed, gh]:
+        assert split.wait(t)[0] == native.REQ_DONE
+        got.append((s_.clone(), c_.clone()))
+    pol = split.policy_stats()
+    split.close()
+    # every root-only request split into one launch per feature, plus its decryption ranges (two or
+    # more where it has over 2,048 cells); some requests ran at high priority, not all
+    want_groups = sum((1 if use_node else F_) + -(-2 * F_ * K_ * (4 if use_node else 1) // 2048)
+                      for _, _, F_, K_, use_node in reqs)
+    cls = pol["per_class"]
+    assert pol["launch_groups"] >= want_groups and sum(cls) == len(reqs) + 2 and cls[0] > 0 and cls[2] > 0
+    alone = P.Server(slots=1, hbm_budget=8 << 30)
+    for rq, (sm, cm) in zip(reqs, got):
+        t, s_, c_ = _submit(alone, data, rq)
+        assert alone.wait(t)[0] == native.REQ_DONE
+        assert torch.equal(s_, sm) and torch.equal(c_, cm)
+        sd, cd = _direct(data, rq)
+        assert torch.equal(s_, sd) and torch.equal(c_, cd)
+    # the packed and g/h-packed requests against their two-array twin
+    assert torch.equal(got[-2][0], got[len(reqs) - 2][0]) and torch.equal(got[-1][0], got[len(reqs) - 2][0])
+    alone.close()
+
+
+def test_reserved_slots_hold_back_large_requests_only(data):
+    """Admission by size class: with 3 slots and 1 reserved for small
+    requests, at most 2 large requests run at once; small requests submitted
+    behind queued large ones still complete, with the right bits."""
+    srv = P.Server(slots=3, hbm_budget=8 << 30, small_imad=1e9, large_imad=1e9, reserved_slots=1)
+    big = (2048, 3000, 6, 16, False)   # modelled work well above 1e9: large
+    small = (1024, 17, 2, 8, True)     # below 1e9: small
+    ts = [_submit(srv, data, big) for _ in range(5)] + [_submit(srv, data, small) for _ in range(3)]
+    for t, _, _ in ts:
+        assert srv.wait(t)[0] == native.REQ_DONE
+    pol = srv.policy_stats()
+    srv.close()
+    assert pol["peak_nonsmall"] <= 2 and pol["per_class"] == [3, 0, 5]
+    sd, cd = _direct(data, small)
+    for t, s_, c_ in ts[5:]:
+        assert torch.equal(s_, sd) and torch.equal(c_, cd)
+    with pytest.raises(native.PaillierError):
+        P.Server(slots=2, hbm_budget=1 << 30, reserved_slots=2)
