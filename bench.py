@@ -322,7 +322,7 @@ def run_oracle_rates(args):
                                                   2 * lv["M"] * lv["F"] / r2["mult"]["all_cores_per_s"] +
                                                   lv["F"] * lv["K"] * 2 / r2["decrypt"]["all_cores_per_s"])
     out["note"] = "oracle as it stands (lambda-form decrypt is the definition); bounded samples; context only"
-    print(json.dumps(out), flush=True)
+    emit_json(out)
 
 
 def run_reference(args, cfg):
@@ -343,7 +343,7 @@ def run_reference(args, cfg):
         "cpu_baseline": {"value": rate, "unit": "enc/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": rate, "unit": "enc/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit_json(line)
 
 
 # ----------------------------------------------------------------------------
@@ -704,7 +704,7 @@ def run_reference_horizontal(args, cfg):
         "cpu_baseline": {"value": rate, "unit": "rounds/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": rate, "unit": "rounds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit_json(line)
 
 
 def run_sharded(args, cfg):
@@ -719,8 +719,11 @@ def run_sharded(args, cfg):
 
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
-    dist.init_process_group("nccl")
+    if "MASTER_ADDR" not in os.environ:  # one rank started without torchrun (--shard)
+        os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(29500 + os.getpid() % 1000), RANK="0",
+                          WORLD_SIZE="1")
     dev = torch.device("cuda", local)
+    dist.init_process_group("nccl", device_id=dev)
     M, F, K, n_bits = cfg["M"], cfg["F"], cfg["K"], cfg["n_bits"]
     L = n_bits // 32
     p, q, gh, r, bins = make_inputs(cfg)
@@ -773,6 +776,7 @@ def run_sharded(args, cfg):
     for _ in range(args.warmup):
         step()
     P.sync()
+    native.call("paillier_profile", 1)
     n0 = native.lib().paillier_launch_count()
     barrier()
     with ClockSampler(local) as clk:
@@ -784,7 +788,20 @@ def run_sharded(args, cfg):
         e1.record()
         barrier()
     launches = native.lib().paillier_launch_count() - n0
+    prof = {}
+    for kname in ("modexp_enc1", "modexp_enc"):
+        tot_ms, cnt_l = native.C.c_double(0), native.C.c_longlong(0)
+        native.call("paillier_profile_read", kname.encode(), native.C.byref(tot_ms), native.C.byref(cnt_l))
+        prof[kname] = (tot_ms.value, cnt_l.value)
+    native.call("paillier_profile", 0)
     elapsed = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
+    # roofline of the dominant launch (the second encryption stage) on this rank's share, slowest rank
+    w = P.get_config(key, native.OP_ENCRYPT)[1]
+    imad1, imad2 = enc_imad_stages(n_bits, w, p, q)
+    split = prof["modexp_enc1"][1] > 0
+    launch_ms = max_over_ranks(prof["modexp_enc"][0] / max(1, prof["modexp_enc"][1]), dist, dev)
+    imad_launch = 2 * ms_ * (imad2 if split else imad1 + imad2)
+    peak = imad_peak_derived(sm_count_of(dev))
     P.sync()
     # untimed: the gathered sums equal the plaintext sums of every feature
     v_all = torch.from_numpy(gh.reshape(-1).copy()).to(dev)
@@ -823,11 +840,19 @@ def run_sharded(args, cfg):
         "e2e": {"value": 2 * M * args.steps / e2e_s, "unit": "enc/s", "h2d_bytes_per_step": int(tot[0].item()),
                 "d2h_bytes_per_step": int(tot[1].item())},
         "gpu_launches": int(launches_max * world),
+        "roofline": {"bound": "alu",
+                     "kernel": "k_modexp (encryption, second stage: z^x mod x^2)" if split else "k_modexp (encryption)",
+                     "achieved": imad_launch / (launch_ms * 1e-3) / 1e12, "peak": peak / 1e12, "unit": "TIMAD/s",
+                     "frac": imad_launch / (launch_ms * 1e-3) / peak,
+                     "traffic": 2 * ms_ * TRAFFIC_PER_ENC[(n_bits, w)] if (n_bits, w) in TRAFFIC_PER_ENC else None,
+                     "peak_source": "derived: SMs x 64 IMAD lanes/clk/SM (4 sub-partitions x 16) x 2032 MHz max SM "
+                                    "clock", "launch_ms": launch_ms, "imad_per_launch": imad_launch,
+                     "note": "per rank (its share of the encryptions), slowest rank's launch"},
         "verified": f"gathered sums == plaintext sums of the encoded values, all {F * K * 2} cells (untimed)",
     }
     dist.destroy_process_group()
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit_json(line)
 
 
 def workload_config(name, cfg):
@@ -1314,7 +1339,7 @@ def run_batched(args, cfg, emit=True):
                     f"values, all {F * K * 2} cells and counts (untimed)",
     }
     if rank == 0 and emit:
-        print(json.dumps(line), flush=True)
+        emit_json(line)
     return line
 
 
@@ -1445,7 +1470,7 @@ def run_serving(args, cfg, emit=True):
         "server": stats, "clocks": clk.summary(),
     }
     if emit:
-        print(json.dumps(line), flush=True)
+        emit_json(line)
     return line
 
 
@@ -1502,7 +1527,29 @@ def run_legs(args, line):
     }
 
 
+# The result line goes to the process's original standard output; everything
+# else (libraries that print banners, e.g. NCCL's version line) goes to stderr.
+_JSON_OUT = None
+
+
+def reserve_stdout():
+    """Keeps a private handle on standard output for the JSON line and points
+    file descriptor 1 at stderr for the rest of the process."""
+    global _JSON_OUT
+    if _JSON_OUT is None:
+        sys.stdout.flush()
+        _JSON_OUT = os.fdopen(os.dup(1), "w")
+        os.dup2(2, 1)
+
+
+def emit_json(obj):
+    out = _JSON_OUT if _JSON_OUT is not None else sys.stdout
+    out.write(json.dumps(obj) + "\n")
+    out.flush()
+
+
 def main():
+    reserve_stdout()
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -1525,6 +1572,8 @@ def main():
                     help="g/h packing, one plaintext enc(g) + 2^B enc(h) per sample (B bits; 0 = off): tree and "
                          "serving modes use it instead of two ciphertexts per sample; the level mode reports it "
                          "beside the headline (default 45 there, 0 elsewhere)")
+    ap.add_argument("--shard", action="store_true",
+                    help="level: run the sharded job (the N > 1 path) even on one rank")
     ap.add_argument("--no-legs", action="store_true",
                     help="level: skip the batched-tree and serving legs measured after the headline")
     ap.add_argument("--serve-requests", type=int, default=300, help="serving leg of the level run: timed requests")
@@ -1548,14 +1597,14 @@ def main():
         run_serving(args, cfg)
     elif args.config == "large":
         run_batched(args, cfg)
-    elif int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.config == "level":
+    elif (int(os.environ.get("WORLD_SIZE", "1")) > 1 or args.shard) and args.config == "level":
         run_sharded(args, cfg)
     else:
         line = run_ours(args, cfg)
         if line is not None:
             if args.gpus == 1 and not args.no_legs and args.config == "level":
                 run_legs(args, line)
-            print(json.dumps(line), flush=True)
+            emit_json(line)
 
 
 if __name__ == "__main__":

@@ -335,6 +335,7 @@ struct pl_server {
         if (ok && c != 0 && running - running_cls[0] >= (int)slots.size() - reserved) ok = false;
         if (!ok) {
           blocked[c] = true;
+          if (blocked[0] && blocked[1] && blocked[2]) break;  // nothing further can start now
           ++it;
           continue;
         }

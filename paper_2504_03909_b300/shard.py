@@ -100,10 +100,11 @@ def run_level(ops: LevelOps, dist, world: int, rank: int, M: int, F: int, gather
     s_lo, s_hi = block_range(M, world, rank)
     f_lo, f_hi = block_range(F, world, rank)
     local = ops.encrypt((s_lo, s_hi))
-    ct = gather_rows(dist, local, M, world) if world > 1 else local
+    # with a process group the exchange runs even on one rank (the same code path)
+    ct = gather_rows(dist, local, M, world) if dist is not None else local
     ctm = ops.prepare(ct)
     hist, count = ops.aggregate(ctm, f_lo, f_hi)
     sums = ops.decrypt(hist)
-    if gather_sums and world > 1:
+    if gather_sums and dist is not None:
         sums = gather_features(dist, sums, F, world)
     return sums, count, (f_lo, f_hi)
