@@ -1603,7 +1603,12 @@ def main():
         line = run_ours(args, cfg)
         if line is not None:
             if args.gpus == 1 and not args.no_legs and args.config == "level":
-                run_legs(args, line)
+                try:
+                    run_legs(args, line)
+                except Exception as exc:  # a failed leg must not cost the headline line
+                    import traceback
+                    traceback.print_exc()
+                    line["legs_error"] = f"{type(exc).__name__}: {exc}"
             emit_json(line)
 
 
