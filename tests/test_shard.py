@@ -1,5 +1,5 @@
-"""The sharded level step of paper_2504_03909_b300.shard on CPU: two gloo ranks
-(world_size 2) run the partition (samples for encryption, features for
+"""The sharded level step of paper_2504_03909_b300.shard on CPU: two and three
+gloo ranks run the partition (samples for encryption, features for
 aggregation and decryption) and the exchange (all-gather of the ciphertext
 rows, gather of the decrypted feature blocks) with the oracle doing the
 arithmetic on each rank; the merged result must equal the single-rank
@@ -21,7 +21,7 @@ if ROOT not in sys.path:
 
 from paper_2504_03909_b300 import shard, synth  # noqa: E402
 
-M, F, K, N_BITS, SEED, NODES = 90, 5, 8, 1024, 1, 2
+M, F, K, N_BITS, SEED, NODES = 91, 5, 8, 1024, 1, 2  # 91 samples: ragged blocks over 2 and 3 ranks
 
 
 def test_block_range_partitions():
@@ -111,21 +111,22 @@ def _worker(rank, world, port, out):
     dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_equal_one_rank():
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_equal_one_rank(world):
     import oracle
-    port = 29600 + os.getpid() % 1000
+    port = 29600 + (os.getpid() + 7 * world) % 1000
     out = mp.Manager().dict()
-    mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
+    mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     # the single-rank job of the same workload
     pub, priv, m, r, bins, node = _workload()
     ops = _ops(pub, priv, m, r, bins, node)
     sums1, count1, _ = shard.run_level(ops, None, 1, 0, M, F)
     ct1 = ops.encrypt((0, M))
     hist1, _ = ops.aggregate(ct1, 0, F)
-    for rank in (0, 1):
+    for rank in range(world):
         o = out[rank]
         f_lo, f_hi = o["frange"]
-        assert (f_lo, f_hi) == shard.block_range(F, 2, rank)
+        assert (f_lo, f_hi) == shard.block_range(F, world, rank)
         assert np.array_equal(o["ct"], ct1.numpy())                   # every ciphertext row, gathered
         assert np.array_equal(o["hist"], hist1[:, f_lo:f_hi].numpy())  # this rank's cells
         assert np.array_equal(o["sums"], sums1.numpy())               # every decrypted sum, merged
