@@ -1,5 +1,6 @@
-// Continuous-batching request loop: FIFO admission by free slot and HBM
-// budget, concurrent execution on per-slot streams, completion by event query.
+// Continuous-batching request loop: admission by free slot, HBM budget and
+// size class, concurrent execution on per-slot streams, launch groups issued
+// by the loop as the device consumes them, completion by event query.
 //
 // Scheduling on the device.  The exponentiation and segmented-product kernels
 // are persistent (a grid of the resident blocks loops over the work), so one
