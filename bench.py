@@ -1413,7 +1413,7 @@ def run_serving(args, cfg, emit=True):
             dec = cells * dec_imad(rq["nb"], w)
         return ngh * rq["M"] * rq["F"] * mont_imad(2 * L) + dec
 
-    srv = P.Server(slots=args.slots, hbm_budget=budget)
+    srv = P.Server(slots=args.slots, hbm_budget=budget, promote_ms=args.promote_ms)
     # warm-up, then the closed-loop capacity in work units (every slot busy)
     warm = [draw() for _ in range(max(4 * args.slots, 32))]
     for rq in warm[:args.slots]:
@@ -1461,6 +1461,7 @@ def run_serving(args, cfg, emit=True):
                                "M log-uniform [1e3, 1e6], F uniform [8, 64], K uniform {64..256 step 32}, "
                                "2048/3072-bit keys p = 0.5, resident ciphertexts", "slots": args.slots,
                    "hbm_budget_bytes": budget, "offered_load": args.load, "requests": args.requests,
+                   "promote_ms": args.promote_ms,
                    "pack_bits": args.pack_bits, "gh_bits": args.gh_bits},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "by_size": serving_classes(done_rq, lat, work),
@@ -1559,6 +1560,8 @@ def main():
     ap.add_argument("--requests", type=int, default=300, help="serving: timed requests")
     ap.add_argument("--slots", type=int, default=8, help="serving: concurrent request slots")
     ap.add_argument("--load", type=float, default=0.7, help="serving: offered load / measured capacity")
+    ap.add_argument("--promote-ms", type=float, default=None,
+                    help="serving: aging threshold of large requests (the library's default when omitted)")
     ap.add_argument("--autotune", action="store_true", help="autotune the launch configurations first (batched)")
     ap.add_argument("--no-compare", action="store_true", help="batched/large: skip the per-node comparator")
     ap.add_argument("--pack-bits", type=int, default=0, help="batched/large: pack cells into B-bit slots before decryption")

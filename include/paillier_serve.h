@@ -118,12 +118,20 @@ pl_status pl_server_cancel(pl_server* srv, uint64_t ticket);
 pl_status pl_server_set_policy(pl_server* srv, double chunk_imad, double small_imad, double large_imad,
                                int reserved_slots);
 
+/* Aging: a large request that has run for promote_ms milliseconds issues its
+ * remaining launch groups at the medium priority (ordered after its earlier
+ * groups by an event), so that it stops yielding to every medium request.
+ * promote_ms <= 0 turns aging off.  Default 250.  Results do not depend on it.
+ * Applies to launch groups issued after the call. */
+pl_status pl_server_set_aging(pl_server* srv, double promote_ms);
+
 /* Policy counters: per_class[3] requests admitted per size class (small,
  * medium, large; may be NULL), launch groups issued (histogram feature groups,
- * packing and decryption ranges), and the peak number of medium and large
- * requests running at once. */
+ * packing and decryption ranges), the peak number of medium and large
+ * requests running at once, and the requests promoted by aging.  Every output
+ * pointer may be NULL. */
 pl_status pl_server_policy_stats(pl_server* srv, long long* per_class, long long* launch_groups,
-                                 int* peak_nonsmall);
+                                 int* peak_nonsmall, long long* promoted);
 
 /* Counters: submitted, completed, failed, cancelled, peak concurrently
  * running requests, peak bytes in flight. */

@@ -16,7 +16,9 @@
 //   * requests run on a stream of their size class's priority (small: below
 //     `small_imad`; large: above `large_imad`; medium between): at each such
 //     boundary the block scheduler takes the pending blocks of the smaller
-//     class first.
+//     class first; a large request that has run for `promote_ms` continues at
+//     the medium priority (its later groups ordered after its earlier ones by
+//     an event), which bounds how long it keeps yielding.
 // Admission: FIFO within each class, so a small request may pass a medium or
 // large one that cannot start; medium and large requests together hold at most
 // slots - `reserved` slots, so that small requests always find one free in
@@ -64,6 +66,9 @@ struct Slot {
   bool issued_all = false;
   pl_status err = PL_OK;
   cudaEvent_t step_ev[2] = {};
+  cudaEvent_t xfer = nullptr;  // orders a promoted request's next groups after its earlier ones
+  double t_start = 0;          // when the request was admitted (ms)
+  int prio = 0;                // the priority level its groups run at now (0 highest)
   cudaEvent_t done = nullptr;
   bool busy = false;
   uint64_t req = 0;
@@ -156,6 +161,8 @@ struct pl_server {
   long long n_class[3] = {0, 0, 0}, n_launch_groups = 0;
   int running_cls[3] = {0, 0, 0};
   int peak_nonsmall = 0;
+  double promote_ms = 250;  // a large request running longer moves up to the medium priority (<= 0: never)
+  long long n_promoted = 0;
 
   int classify(const pl_request& r) const {
     const double w = request_work(r).total;
@@ -190,6 +197,8 @@ struct pl_server {
     const size_t cells = ncell * 2;
     const Work wk = request_work(r);
     sl.cls = q.cls;
+    sl.prio = q.cls;
+    sl.t_start = now_ms();
     sl.s = sl.cs[q.cls];
     sl.plan.clear();
     sl.next = 0;
@@ -226,16 +235,17 @@ struct pl_server {
       plain = static_cast<uint32_t*>(amalloc(5, hcells * L * 4));
     }
     // results out, memory freed, completion recorded (run once, after the last group or an error)
-    sl.last = [slp, r, s, sums, counts, cells, ncell](pl_status err) {
+    sl.last = [slp, r, sums, counts, cells, ncell](pl_status err) {
+      cudaStream_t st = slp->s;  // the stream of the request's last group (it may have been promoted)
       if (err == PL_OK) {
-        cudaMemcpyAsync(r.h_sums, sums, cells * 8, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(r.h_counts, counts, ncell * 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(r.h_sums, sums, cells * 8, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(r.h_counts, counts, ncell * 4, cudaMemcpyDeviceToHost, st);
       }
-      cudaMemcpyAsync(slp->h_status, slp->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(slp->h_status, slp->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
       for (auto& a : slp->allocs)
-        if (a) cudaFreeAsync(a, s);
-      slp->scratch.release(s);
-      cudaEventRecord(slp->done, s);
+        if (a) cudaFreeAsync(a, st);
+      slp->scratch.release(st);
+      cudaEventRecord(slp->done, st);
     };
     if (rc != PL_OK) {
       sl.err = rc;
@@ -252,7 +262,7 @@ struct pl_server {
       plan.push_back([=]() {
         return launch_hist(key, r.d_ctm, r.M, r.gh_stride, r.d_bins + f0 * r.bins_stride, r.bins_stride, nf, r.K,
                            node, r.num_nodes, hist + f0 * r.K * ngh * 2 * L, counts + f0 * r.K, false,
-                           slp->d_status, s, &slp->scratch, ngh);
+                           slp->d_status, slp->s, &slp->scratch, ngh);
       });
     }
     // decryption of n ciphertexts at `in` in ranges of bounded work (at least
@@ -264,7 +274,7 @@ struct pl_server {
         void* o = u64 ? static_cast<void*>(static_cast<uint64_t*>(out) + c0)
                       : static_cast<void*>(static_cast<uint32_t*>(out) + c0 * L);
         const uint32_t* src = in + c0 * 2 * L;
-        plan.push_back([=]() { return launch_decrypt(key, src, nc, o, u64, slp->d_status, s, &slp->scratch); });
+        plan.push_back([=]() { return launch_decrypt(key, src, nc, o, u64, slp->d_status, slp->s, &slp->scratch); });
       }
     };
     if (slots) {
@@ -275,17 +285,19 @@ struct pl_server {
         const size_t c0 = p0 * (size_t)slots;
         const size_t nc = std::min(np_ * (size_t)slots, hcells - c0);
         plan.push_back([=]() {
-          return launch_pack(key, hist + c0 * 2 * L, nc, slots, slot_bits, packed + p0 * 2 * L, s);
+          return launch_pack(key, hist + c0 * 2 * L, nc, slots, slot_bits, packed + p0 * 2 * L, slp->s);
         });
       }
       decrypt_ranges(packed, npacked, plain, false);
       // g/h cells: each 2B-bit slot is two B-bit sums
       const int uslots = r.gh_bits ? 2 * slots : slots;
       const int ubits = r.gh_bits ? r.gh_bits : r.pack_bits;
-      plan.push_back([=]() { return launch_unpack(plain, (int)L, cells, uslots, ubits, sums, slp->d_status, s); });
+      plan.push_back([=]() { return launch_unpack(plain, (int)L, cells, uslots, ubits, sums, slp->d_status, slp->s); });
     } else if (r.gh_bits) {
       decrypt_ranges(hist, hcells, plain, false);
-      plan.push_back([=]() { return launch_unpack(plain, (int)L, cells, 2, r.gh_bits, sums, slp->d_status, s); });
+      plan.push_back([=]() {
+        return launch_unpack(plain, (int)L, cells, 2, r.gh_bits, sums, slp->d_status, slp->s);
+      });
     } else {
       decrypt_ranges(hist, cells, sums, true);
     }
@@ -302,6 +314,15 @@ struct pl_server {
         break;
       }
       if (sl.next >= 2 && cudaEventQuery(sl.step_ev[sl.next & 1]) == cudaErrorNotReady) break;
+      // aging: a large request that has run for promote_ms continues at the
+      // medium priority, so that it stops yielding to every medium request
+      if (sl.prio == 2 && promote_ms > 0 && now_ms() - sl.t_start > promote_ms) {
+        cudaEventRecord(sl.xfer, sl.s);
+        cudaStreamWaitEvent(sl.cs[1], sl.xfer, 0);
+        sl.s = sl.cs[1];
+        sl.prio = 1;
+        ++n_promoted;
+      }
       const pl_status rc = sl.plan[sl.next]();
       cudaEventRecord(sl.step_ev[sl.next & 1], sl.s);
       ++sl.next;
@@ -402,6 +423,7 @@ pl_status pl_server_create(int slots, size_t hbm_budget, pl_server** out) {
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.step_ev[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.step_ev[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.xfer, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&sl.d_status, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&sl.h_status, sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
@@ -514,8 +536,17 @@ pl_status pl_server_set_policy(pl_server* srv, double chunk_imad, double small_i
   return PL_OK;
 }
 
+pl_status pl_server_set_aging(pl_server* srv, double promote_ms) {
+  using namespace pl;
+  clear_error();
+  if (!srv) return fail(PL_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lock(srv->mu);
+  srv->promote_ms = promote_ms;
+  return PL_OK;
+}
+
 pl_status pl_server_policy_stats(pl_server* srv, long long* per_class, long long* launch_groups,
-                                 int* peak_nonsmall) {
+                                 int* peak_nonsmall, long long* promoted) {
   using namespace pl;
   if (!srv) return fail(PL_EINVAL, "server is NULL");
   std::lock_guard<std::mutex> lock(srv->mu);
@@ -523,6 +554,7 @@ pl_status pl_server_policy_stats(pl_server* srv, long long* per_class, long long
     for (int c = 0; c < 3; ++c) per_class[c] = srv->n_class[c];
   if (launch_groups) *launch_groups = srv->n_launch_groups;
   if (peak_nonsmall) *peak_nonsmall = srv->peak_nonsmall;
+  if (promoted) *promoted = srv->n_promoted;
   return PL_OK;
 }
 
@@ -561,6 +593,7 @@ void pl_server_destroy(pl_server* srv) {
     if (sl.done) cudaEventDestroy(sl.done);
     for (auto ev : sl.step_ev)
       if (ev) cudaEventDestroy(ev);
+    if (sl.xfer) cudaEventDestroy(sl.xfer);
     if (sl.d_status) cudaFree(sl.d_status);
     if (sl.h_status) cudaFreeHost(sl.h_status);
     for (auto st : sl.cs)

@@ -97,7 +97,9 @@ SIGNATURES.update({
     "pl_server_cancel": (_i, [_vp, C.c_uint64]),
     "pl_server_request_bytes": (_i, [C.POINTER(Request), C.POINTER(_sz)]),
     "pl_server_set_policy": (_i, [_vp, C.c_double, C.c_double, C.c_double, _i]),
-    "pl_server_policy_stats": (_i, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(_i)]),
+    "pl_server_set_aging": (_i, [_vp, C.c_double]),
+    "pl_server_policy_stats": (_i, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(_i),
+                                    C.POINTER(C.c_longlong)]),
     "pl_server_stats": (_i, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                              C.POINTER(C.c_longlong), C.POINTER(_i), C.POINTER(_sz)]),
     "pl_server_destroy": (None, [_vp]),

@@ -263,10 +263,11 @@ class Server:
 
     def __init__(self, slots: int, hbm_budget: int, chunk_imad: float | None = None,
                  small_imad: float | None = None, large_imad: float | None = None,
-                 reserved_slots: int | None = None):
+                 reserved_slots: int | None = None, promote_ms: float | None = None):
         """chunk_imad, small_imad, large_imad, reserved_slots: the scheduling
-        and admission policy (pl_server_set_policy); None keeps the library's
-        default of that setting."""
+        and admission policy (pl_server_set_policy); promote_ms: aging of large
+        requests (pl_server_set_aging); None keeps the library's default of
+        that setting."""
         out = C.c_void_p()
         call("pl_server_create", slots, hbm_budget, C.byref(out))
         self._h = out
@@ -276,12 +277,15 @@ class Server:
             call("pl_server_set_policy", self._h, float(chunk_imad if chunk_imad is not None else 3e11), small,
                  float(large_imad if large_imad is not None else max(3e12, small)),
                  int(reserved_slots if reserved_slots is not None else (max(1, slots // 4) if slots >= 2 else 0)))
+        if promote_ms is not None:
+            call("pl_server_set_aging", self._h, float(promote_ms))
 
     def policy_stats(self):
         per_class = (C.c_longlong * 3)()
-        groups, peak = C.c_longlong(), C.c_int()
-        call("pl_server_policy_stats", self._h, per_class, C.byref(groups), C.byref(peak))
-        return {"per_class": list(per_class), "launch_groups": groups.value, "peak_nonsmall": peak.value}
+        groups, peak, promoted = C.c_longlong(), C.c_int(), C.c_longlong()
+        call("pl_server_policy_stats", self._h, per_class, C.byref(groups), C.byref(peak), C.byref(promoted))
+        return {"per_class": list(per_class), "launch_groups": groups.value, "peak_nonsmall": peak.value,
+                "promoted": promoted.value}
 
     def submit(self, key: Key, ctm: torch.Tensor, M: int, F: int, K: int, bins: torch.Tensor,
                node: torch.Tensor | None = None, num_nodes: int = 1, gh_stride: int | None = None,

@@ -187,10 +187,13 @@ def test_split_launches_and_priorities_give_the_same_bits(data):
     priority per size class) changes when the GPU changes hands, not what is
     computed: with a budget small enough to split every request into one
     launch per feature, packing range and decryption range (2,048 ciphertexts
-    at least), and requests in all three classes, every request gives the bits
-    of the default policy alone and of the direct API."""
+    at least), requests in all three classes, and every large request moved to
+    the medium-priority stream mid-request by aging, every request gives the
+    bits of the default policy alone and of the direct API."""
     reqs = REQUESTS + [(1024, 3000, 6, 256, False), (2048, 2500, 5, 256, False), (3072, 2000, 4, 256, False)]
-    split = P.Server(slots=4, hbm_budget=8 << 30, chunk_imad=1e7, small_imad=2e11, large_imad=2.5e11)
+    # promote_ms ~0: every large request moves to the medium stream before its second launch group
+    split = P.Server(slots=4, hbm_budget=8 << 30, chunk_imad=1e7, small_imad=2e11, large_imad=2.5e11,
+                     promote_ms=1e-6)
     tickets = [_submit(split, data, rq) for rq in reqs]
     nb, M, F, K, use_node = reqs[-2]
     d = data[nb]
@@ -210,6 +213,7 @@ def test_split_launches_and_priorities_give_the_same_bits(data):
                       for _, _, F_, K_, use_node in reqs)
     cls = pol["per_class"]
     assert pol["launch_groups"] >= want_groups and sum(cls) == len(reqs) + 2 and cls[0] > 0 and cls[2] > 0
+    assert pol["promoted"] == cls[2]  # aging moved every large request to the medium stream
     alone = P.Server(slots=1, hbm_budget=8 << 30)
     for rq, (sm, cm) in zip(reqs, got):
         t, s_, c_ = _submit(alone, data, rq)
