@@ -183,7 +183,7 @@ pl_status paillier_decrypt_u64(const pl_key* key, const uint32_t* d_ct, size_t c
  * not acceptable, or an embedding application that forbids allocation after
  * start-up.  This call allocates nothing: its scratch (the CRT half results
  * and the window tables) is one fixed device array inside the library, about
- * 35 MB, which every GPU that loads the library holds until the process exits.
+ * 21 MB, which every GPU that loads the library holds until the process exits.
  *   - count must be <= 8192 ciphertexts per call (else PL_EINVAL, nothing is
  *     launched); every supported key size is accepted.
  *   - The first call on a device looks up the array's device address on that
