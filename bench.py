@@ -79,28 +79,91 @@ def exp_montmuls(e: int, w: int, pre: int = 2, post: int = 1) -> int:
     return pre + (1 << (w - 1)) + (sliding_ops(e, w) - 1) + post
 
 
-def enc_imad_stages(n_bits: int, w: int, p: int, q: int):
+def schedule_split(e: int, w: int):
+    """(squarings, products) of the sliding-window schedule after its leading window."""
+    i, sq, pr, first = e.bit_length() - 1, 0, 0, True
+    while i >= 0:
+        if not (e >> i) & 1:
+            sq, i = sq + 1, i - 1
+            continue
+        j = max(i - w + 1, 0)
+        while not (e >> j) & 1:
+            j += 1
+        if first:
+            first = False
+        else:
+            sq, pr = sq + (i - j + 1), pr + 1
+        i = j - 1
+    return sq, pr
+
+
+def sos_shape(nl: int, lanes: int) -> bool:
+    """Whether the exponentiation kernel at nl limbs and `lanes` lanes runs its
+    schedule through the separated-form body (a multiple of 4 limbs per lane, at
+    most 24, 2 to 16 lanes)."""
+    s = nl // lanes
+    return nl % lanes == 0 and s % 4 == 0 and 4 <= s <= 24 and 2 <= lanes <= 16 and lanes & (lanes - 1) == 0
+
+
+def sos_square_imad(nl: int, lanes: int) -> int:
+    """One separated-form squaring on nl limbs over `lanes` lanes of s limbs:
+    per lane (lanes/2 - 1) s^2 limb products in the pair rounds, s^2/2 in the
+    half round and s^2 in the diagonal round, then the reduction rows (nl^2 limb
+    products + nl mul.lo over the instance).  A product through the same body
+    forms lanes s^2 per lane: mont_imad(nl), as CIOS."""
+    s = nl // lanes
+    per_lane = (lanes // 2 - 1) * s * s + s * s // 2 + s * s
+    return 2 * lanes * per_lane + 2 * nl * nl + nl
+
+
+def exp_imad(e: int, w: int, nl: int, lanes: int, pre: int = 2, post: int = 1) -> int:
+    """Multiply-add halves one exponentiation executes: CIOS products to enter
+    Montgomery form, for the odd-power table and to leave it; the schedule's
+    squarings and products through the separated-form body where the shape has
+    it (else CIOS)."""
+    sq, pr = schedule_split(e, w)
+    cios = (pre + (1 << (w - 1)) + post) * mont_imad(nl)
+    if sos_shape(nl, lanes):
+        return cios + sq * sos_square_imad(nl, lanes) + pr * mont_imad(nl)
+    return cios + (sq + pr) * mont_imad(nl)
+
+
+def enc_split(L: int, lanes: int) -> bool:
+    """Whether encryption runs as two launches (first stage at half the lanes)."""
+    return (L, lanes) in ((64, 4), (96, 8))
+
+
+def enc_imad_stages(n_bits: int, w: int, p: int, q: int, lanes: int = 4, cios: bool = False):
     """One encryption as the kernels run it, per CRT half (prime x, other prime
     x'): first stage mod x (L/2 limbs) with exponent x' mod (x - 1), second stage
-    mod x^2 (L limbs) with exponent x.  Returns (first, second)."""
+    mod x^2 (L limbs) with exponent x; `lanes` is the second stage's lane count
+    (the first stage runs at half of it when split, else at the same).  cios:
+    every product counted at the CIOS cost (the count before squarings formed
+    cross products once).  Returns (first, second)."""
     L = n_bits // 32
-    first = sum(exp_montmuls(xo % (x - 1), w) for x, xo in ((p, q), (q, p))) * mont_imad(L // 2)
-    second = sum(exp_montmuls(x, w) for x in (p, q)) * mont_imad(L)
+    if cios:
+        first = sum(exp_montmuls(xo % (x - 1), w) for x, xo in ((p, q), (q, p))) * mont_imad(L // 2)
+        second = sum(exp_montmuls(x, w) for x in (p, q)) * mont_imad(L)
+        return first, second
+    l1 = lanes // 2 if enc_split(L, lanes) else lanes
+    first = sum(exp_imad(xo % (x - 1), w, L // 2, l1) for x, xo in ((p, q), (q, p)))
+    second = sum(exp_imad(x, w, L, lanes) for x in (p, q))
     return first, second
 
 
-def enc_imad(n_bits: int, w: int, p: int, q: int) -> int:
-    return sum(enc_imad_stages(n_bits, w, p, q))
+def enc_imad(n_bits: int, w: int, p: int, q: int, lanes: int = 4, cios: bool = False) -> int:
+    return sum(enc_imad_stages(n_bits, w, p, q, lanes, cios))
 
 
-def dec_imad(n_bits: int, w: int, p: int | None = None, q: int | None = None) -> int:
+def dec_imad(n_bits: int, w: int, p: int | None = None, q: int | None = None, lanes: int | None = None) -> int:
     """One CRT decryption: c^(x - 1) mod x^2 per half.  Without the primes, an
-    exponent of n_bits/2 bits with half its bits set stands in."""
+    exponent of n_bits/2 bits with half its bits set stands in; without lanes,
+    every product at the CIOS cost."""
     L = n_bits // 32
-    if p is None:
-        e = int("10" * (n_bits // 4), 2)
-        return 2 * exp_montmuls(e, w) * mont_imad(L)
-    return sum(exp_montmuls(x - 1, w) for x in (p, q)) * mont_imad(L)
+    es = [int("10" * (n_bits // 4), 2)] * 2 if p is None else [p - 1, q - 1]
+    if lanes is None:
+        return sum(exp_montmuls(e, w) for e in es) * mont_imad(L)
+    return sum(exp_imad(e, w, L, lanes) for e in es)
 
 
 # ----------------------------------------------------------------------------
@@ -796,8 +859,8 @@ def run_sharded(args, cfg):
     native.call("paillier_profile", 0)
     elapsed = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist, dev)
     # roofline of the dominant launch (the second encryption stage) on this rank's share, slowest rank
-    w = P.get_config(key, native.OP_ENCRYPT)[1]
-    imad1, imad2 = enc_imad_stages(n_bits, w, p, q)
+    lanes_enc, w = P.get_config(key, native.OP_ENCRYPT)
+    imad1, imad2 = enc_imad_stages(n_bits, w, p, q, lanes_enc)
     split = prof["modexp_enc1"][1] > 0
     launch_ms = max_over_ranks(prof["modexp_enc"][0] / max(1, prof["modexp_enc"][1]), dist, dev)
     imad_launch = 2 * ms_ * (imad2 if split else imad1 + imad2)
@@ -1035,13 +1098,17 @@ def run_ours(args, cfg):
         "decode": ms("decode"),
     }
     phase = {k: v_ / args.steps for k, v_ in phase.items()}  # ms per step
-    w = P.get_config(key, native.OP_ENCRYPT)[1]
+    lanes_enc, w = P.get_config(key, native.OP_ENCRYPT)
     # encryption runs as one launch, or as two (first stage mod x, then the second mod x^2,
-    # which dominates the step): the roofline is that of the dominant launch
-    imad1, imad2 = enc_imad_stages(n_bits, w, p, q)
+    # which dominates the step): the roofline is that of the dominant launch; the work is the
+    # multiply-adds the kernels execute (squarings form each cross product once), the CIOS
+    # count of the same schedules beside it
+    imad1, imad2 = enc_imad_stages(n_bits, w, p, q, lanes_enc)
+    cios1, cios2 = enc_imad_stages(n_bits, w, p, q, lanes_enc, cios=True)
     split = prof["modexp_enc1"][1] > 0
     enc_launch_ms = prof["modexp_enc"][0] / max(1, prof["modexp_enc"][1])
     imad_launch = units * (imad2 if split else imad1 + imad2)
+    imad_launch_cios = units * (cios2 if split else cios1 + cios2)
     achieved = imad_launch / (enc_launch_ms * 1e-3)
     peak = imad_peak_derived(sm_count_of(dev))
     best_mix = max(peaks.values())
@@ -1102,6 +1169,11 @@ def run_ours(args, cfg):
             "measured_note": "project microbenchmark paillier_imad_peak in the same run: carry_rows is the "
                              "instruction mix of the kernel's Montgomery rows",
             "imad_per_launch": imad_launch,
+            "imad_per_launch_cios_count": imad_launch_cios,
+            "frac_cios_count": imad_launch_cios / (enc_launch_ms * 1e-3) / peak,
+            "imad_note": "imad_per_launch counts the multiply-add halves the kernel executes (separated-form "
+                         "squarings form each cross product once); imad_per_launch_cios_count is the same schedule "
+                         "at 4 L^2 + L per product",
             "launch_ms": enc_launch_ms,
             "first_stage": first_stage,
         },

@@ -25,17 +25,18 @@ extern "C" {
 int paillier_test_mont_mul(int limbs, int lanes, const uint32_t* h_N, const uint32_t* d_a,
                            const uint32_t* d_b, size_t count, uint32_t* d_out, void* stream);
 
-/* Montgomery squaring of the exponentiation kernels (each cross product formed
- * once; the squarings of the sliding-window schedule run through it):
- *   d_out[i] = d_a[i]^2 * 2^(-32 limbs) mod N     (canonical)
- * for `count` values d_a[i] < N; d_a, d_out are [count][limbs] uint32 on the
- * device (they may be the same buffer), h_N is the odd modulus (host, `limbs`
- * limbs, top limb non-zero).  (limbs, lanes) must be one of the compiled
- * pairs: (32,2) (32,4) (64,4) (64,8) (96,4) (96,8) (a multiple of 4 limbs
- * per lane, at most 24); others return PL_EINVAL (the exponentiations take
- * the product path there).  Asynchronous on `stream`. */
-int paillier_test_mont_sqr(int limbs, int lanes, const uint32_t* h_N, const uint32_t* d_a, size_t count,
-                           uint32_t* d_out, void* stream);
+/* The separated-form (SOS) Montgomery product of the exponentiation kernels,
+ * one code body for products and squarings (a square forms every cross
+ * product once):
+ *   d_out[i] = d_a[i] * d_b[i] * 2^(-32 limbs) mod N      (d_b non-NULL)
+ *   d_out[i] = d_a[i]^2 * 2^(-32 limbs) mod N             (d_b NULL)
+ * canonical, for `count` values d_a[i], d_b[i] < N; d_a, d_b, d_out are
+ * [count][limbs] uint32 on the device (d_out may be d_a), h_N is the odd
+ * modulus (host, `limbs` limbs, top limb non-zero).  (limbs, lanes) must be
+ * one of (32,2) (32,4) (64,4) (64,8) (96,4) (96,8) (a multiple of 4 limbs per
+ * lane, at most 24); others return PL_EINVAL.  Asynchronous on `stream`. */
+int paillier_test_mont_sos(int limbs, int lanes, const uint32_t* h_N, const uint32_t* d_a, const uint32_t* d_b,
+                           size_t count, uint32_t* d_out, void* stream);
 
 /* Lengths of the key's key-fixed exponentiation schedules (host only, no
  * device work), for the CRT halves h = 0 (prime p) and 1 (prime q): nop[h] is

@@ -64,9 +64,11 @@ __global__ void k_decode(const uint64_t* __restrict__ s, const int32_t* __restri
 // acc: the base in Montgomery form on entry, base^e in Montgomery form on exit,
 // e given by its schedule op[0..nop) (layout in ModexpParams).  tbl: this
 // group's table of 2^(w-1) entries of S*T limbs (the odd powers); bs: its
-// shared-memory column.  Every op is one Montgomery product (mont_mul, the
-// squarings included: the balanced squaring mont_sqr forms 18 % fewer
-// instructions here but runs slower in this loop, see mp.cuh).
+// shared-memory column.  Every op is one Montgomery product: where the shape
+// has it, the separated-form body mont_sos for squarings and products alike
+// (one routine's code in the loop; a square forms each cross product once),
+// else mont_mul with the multiplier staged in shared memory.  The table build
+// runs once per exponentiation and keeps mont_mul.
 template <int S, int T>
 PL_DEV void window_exp(uint32_t (&acc)[S], const uint32_t (&n)[S], uint32_t np, const uint8_t* op, int nop, int w,
                        uint32_t* tbl, uint32_t* bs, int st, int k) {
@@ -95,7 +97,17 @@ PL_DEV void window_exp(uint32_t (&acc)[S], const uint32_t (&n)[S], uint32_t np, 
   auto entry = [&](int v) { return PL_BOUNDS((v >> 1) < nent, kBoundsTable) ? (v >> 1) : 0; };
   load_slice_rw<S>(a, tbl + (size_t)entry(op[0]) * NL, k);
   for (int i = 1; i < nop; ++i) {
-    const int v = op[i];
+    const int v = op[i];  // the same for every instance of the warp
+    if constexpr (kHaveSos<S, T>) {
+      if (v != 0) {
+        load_slice_rw<S>(t, tbl + (size_t)entry(v) * NL, k);
+      } else {
+#pragma unroll
+        for (int j = 0; j < S; ++j) t[j] = a[j];
+      }
+      mont_sos<S, T>(a, a, t, n, np, k, v == 0);
+      continue;
+    }
     __syncwarp();
     if (v == 0) {
       stage<S>(bs, st, a, k);

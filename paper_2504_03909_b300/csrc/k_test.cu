@@ -43,16 +43,19 @@ __global__ void __launch_bounds__(kBlock) k_test_mont_mul(const __grid_constant_
   }
 }
 
-// d_out = a^2 R^-1 mod N through the squaring path (mont_sqr)
+// d_out = a b R^-1 mod N (or a^2 R^-1 mod N when B is null) through the SOS
+// body of the exponentiations (mont_sos)
 template <int S, int T>
-__global__ void __launch_bounds__(kBlock) k_test_mont_sqr(const __grid_constant__ N2Const P,
-                                                          const uint32_t* __restrict__ A, size_t count,
+__global__ void __launch_bounds__(kBlock) k_test_mont_sos(const __grid_constant__ N2Const P,
+                                                          const uint32_t* __restrict__ A,
+                                                          const uint32_t* __restrict__ B, size_t count,
                                                           uint32_t* __restrict__ out) {
   constexpr int NL = S * T;
   constexpr int IPW = 32 / T;
   const int lane = threadIdx.x & 31, k = lane % T, gw = lane / T;
-  uint32_t n[S], a[S];
+  uint32_t n[S], a[S], b[S];
   const_slice<S>(n, P.N, k);
+  const bool square = B == nullptr;
   const size_t nchunk = (count + IPW - 1) / IPW;
   const size_t warp0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
@@ -61,17 +64,23 @@ __global__ void __launch_bounds__(kBlock) k_test_mont_sqr(const __grid_constant_
     const bool valid = i < count;
     const size_t ii = valid ? i : count - 1;
     load_slice<S>(a, A + ii * NL, k);
-    mont_sqr<S, T>(a, a, n, P.np, k);
+    if (square) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) b[j] = a[j];
+    } else {
+      load_slice<S>(b, B + ii * NL, k);
+    }
+    mont_sos<S, T>(a, a, b, n, P.np, k, square);
     if (valid) store_slice<S>(out + ii * NL, a, k);
   }
 }
 
 template <int S, int T>
-int run_sqr(const N2Const& P, const uint32_t* a, size_t count, uint32_t* out, cudaStream_t s) {
+int run_sos(const N2Const& P, const uint32_t* a, const uint32_t* b, size_t count, uint32_t* out, cudaStream_t s) {
   const size_t ipw = 32 / T;
   const size_t blocks = ((count + ipw - 1) / ipw + (kBlock / 32) - 1) / (kBlock / 32);
   const int grid = (int)std::min<size_t>(blocks, 4096);
-  k_test_mont_sqr<S, T><<<grid, kBlock, 0, s>>>(P, a, count, out);
+  k_test_mont_sos<S, T><<<grid, kBlock, 0, s>>>(P, a, b, count, out);
   PL_CUDA_TRY(cudaGetLastError());
   return PL_OK;
 }
@@ -111,8 +120,8 @@ extern "C" int paillier_test_mont_mul(int limbs, int lanes, const uint32_t* h_N,
   return fail(PL_EINVAL, "no compiled kernel for this (limbs, lanes) pair");
 }
 
-extern "C" int paillier_test_mont_sqr(int limbs, int lanes, const uint32_t* h_N, const uint32_t* d_a, size_t count,
-                                      uint32_t* d_out, void* stream) {
+extern "C" int paillier_test_mont_sos(int limbs, int lanes, const uint32_t* h_N, const uint32_t* d_a,
+                                      const uint32_t* d_b, size_t count, uint32_t* d_out, void* stream) {
   using namespace pl;
   clear_error();
   if (!h_N || limbs < 1 || limbs > kMaxL || !(h_N[0] & 1u) || h_N[limbs - 1] == 0)
@@ -125,10 +134,10 @@ extern "C" int paillier_test_mont_sqr(int limbs, int lanes, const uint32_t* h_N,
   P.np = plh::neg_inv32(h_N[0]);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 #define PL_CASE(LL, TT) \
-  if (limbs == LL && lanes == TT) return run_sqr<LL / TT, TT>(P, d_a, count, d_out, s);
+  if (limbs == LL && lanes == TT) return run_sos<LL / TT, TT>(P, d_a, d_b, count, d_out, s);
   PL_CASE(32, 2) PL_CASE(32, 4) PL_CASE(64, 4) PL_CASE(64, 8) PL_CASE(96, 4) PL_CASE(96, 8)
 #undef PL_CASE
-  return fail(PL_EINVAL, "no compiled squaring kernel for this (limbs, lanes) pair");
+  return fail(PL_EINVAL, "no compiled SOS kernel for this (limbs, lanes) pair");
 }
 
 #ifdef PL_CHECKED

@@ -215,43 +215,34 @@ PL_DEV void mont_mul(uint32_t (&r)[S], const uint32_t (&a)[S], const uint32_t* b
 }
 
 // ---------------------------------------------------------------------------
-// Montgomery squaring: r = a^2 R^-1 mod N for canonical a (a < N), with every
-// cross product a_i a_j (i != j) formed once instead of twice.
+// Montgomery products and squarings in separated form (SOS), one code body
+// for both: r = a b R^-1 mod N, or r = a^2 R^-1 mod N with every cross product
+// a_i a_j (i != j) formed once.
 //
-// First the square P = a^2 (2 NL limbs) is built in chunks of S limbs; lane k
-// ends with chunk k ("lo", a part of P mod R) and chunk k + T ("hi", a part of
-// P div R).  With A_k lane k's chunk of a and X = 2^(32 S),
-//     P = sum_k A_k^2 X^(2k) + 2 sum_{k < l} A_k A_l X^(k + l),
-// and the chunk products are spread so that every lane does the same work:
-//   * round "diag": lane k forms the cross products of its own chunk,
-//     sum_{i < j} a_i a_j (a triangle of S (S - 1) / 2 limb products), at chunk 2k;
-//   * rounds d = 1 .. T/2 - 1: lane k forms A_k A_((k + d) mod T) (S^2 limb
-//     products) at chunk k + ((k + d) mod T): every pair at cyclic distance d once;
-//   * round "half" (d = T/2): the pair {k, k + T/2} is split between its two
-//     lanes by the halves of the upper chunk (the lower lane multiplies the
-//     lower chunk by its low half, the upper lane by its high half), S^2 / 2
-//     each, both at chunk 2 (k mod T/2) + T/2.
-// A lane forms S^2 T / 2 - S / 2 limb products, half of a product's S^2 T
-// multiplication-row products.  A round's 2S-limb result Q lands at chunk c
-// (its low half) and c + 1 (its high half), and in every round c = 2k + d mod
-// T (d = 0 for "diag"), so each lane receives exactly two halves of the same
-// kind, with two shuffles in which every sending lane serves one receiver (a
-// lane below T/2 sends its low half first, a lane above its high half).  The
-// sums of cross products are doubled, then the squares a_i^2 are added; the
-// carries out of a chunk stay in that chunk's carry word.
+// First the product P (2 NL limbs) is built in chunks of S limbs; lane k ends
+// with chunk k ("lo", a part of P mod R) and chunk k + T ("hi", a part of
+// P div R).  With A_k, B_k lane k's chunks of a and b and X = 2^(32 S), P is a
+// sum of chunk products A_k B_l X^(k + l), formed in rounds in which every
+// lane does the same work:
+//   * product: rounds D = 0 .. T - 1, lane k forming A_k B_((k + D) mod T);
+//   * square: P = sum_k A_k^2 X^(2k) + 2 sum_{k < l} A_k A_l X^(k + l):
+//     rounds D = 1 .. T/2 - 1 (lane k forms A_k A_((k + D) mod T): every pair
+//     at cyclic distance d once), the round "half" (the pair {k, k + T/2}
+//     split between its two lanes by the halves of the upper chunk: the lower
+//     lane multiplies the lower chunk by its low half, the upper lane by its
+//     high half, S^2 / 2 each), then the sum so far is doubled and the round
+//     D = 0 adds the diagonal chunks A_k^2.
+// A square forms (T / 2 + 1/2) S^2 limb products per lane against T S^2 for a
+// product.  A round's 2S-limb result lands at chunk c (low half) and c + 1
+// (high half) with c = 2k + D mod T, so each lane receives exactly two halves
+// of the same kind, with two shuffles in which every sending lane serves one
+// receiver (a lane below T/2 sends its low half first, a lane above its high
+// half).  Carries out of a chunk stay in that chunk's carry word.
 // The reduction is the second half of the CIOS steps (m = t_0 N'; t += m N;
 // shift) on the low half of P, after which the high half is added: the value
-// (P + M N) / R is below 2N, and one conditional subtraction makes it
-// canonical.  Steps that are the same for every lane run on every lane.
-//
-// Measured on a B300 in the exponentiation loop (second encryption stage,
-// 2048-bit, 4 lanes of 16 limbs), against mont_mul for every op: 18 % fewer
-// executed instructions, but 1.2x the time -- the fully unrolled rounds put
-// about three times the code of one mont_mul block in the loop (the warps'
-// "no instruction" stall went from 0.1 to 2.9 cycles per issue) and its
-// registers allow 3 instead of 4 blocks per SM.  The exponentiations therefore
-// keep mont_mul; this routine stays limb-exact under test
-// (paillier_test_mont_sqr).
+// (P + M N) / R is below 2N (P < N^2), and one conditional subtraction makes it
+// canonical.  The rounds run in a loop, so an exponentiation's loop holds one
+// routine's code whether an op squares or multiplies.
 
 // t += a[j] * b for j = J, J + 2, ... < S: lo into logical limb j, hi into
 // j + 1 (logical limb S is x1); the carry out of the chain goes into x1, x2.
@@ -292,11 +283,11 @@ PL_DEV void row_from(uint32_t (&t)[S], uint32_t& x1, uint32_t& x2, const uint32_
   chain_from<S, ROT, J0 + 1>(t, x1, x2, a, b);
 }
 
-// shift of a lane-local window by one limb: logical limb U leaves into out
-template <int S, int U>
-PL_DEV void leave(uint32_t (&w)[S], uint32_t& x1, uint32_t& x2, uint32_t& out) {
-  out = w[U % S];
-  w[U % S] = x1;
+// shift of a lane-local window of SW limbs by one limb: logical limb I leaves into out
+template <int SW, int I>
+PL_DEV void leave_w(uint32_t (&w)[SW], uint32_t& x1, uint32_t& x2, uint32_t& out) {
+  out = w[I % SW];
+  w[I % SW] = x1;
   x1 = x2;
   x2 = 0;
 }
@@ -310,36 +301,26 @@ PL_DEV int after(int v, uint32_t dep) {
   return v;
 }
 
-// lo, w = sum_{i < j} a_i a_j 2^(32 (i + j)) (low and high S limbs)
-template <int S, int... I>
-PL_DEV void sq_diag(uint32_t (&lo)[S], uint32_t (&w)[S], const uint32_t (&a)[S], std::integer_sequence<int, I...>) {
-  uint32_t x1 = 0, x2 = 0;
-#pragma unroll
-  for (int j = 0; j < S; ++j) w[j] = 0;
-  ((row_from<S, I % S, I + 1>(w, x1, x2, a, a[I]), leave<S, I>(w, x1, x2, lo[I])), ...);
-}
+// z: zero, computed from the previous round's carry words (a carry word counts
+// a few carries, far below 2^31).  Adding it to a round's shuffle lane makes the
+// round wait for the previous one: otherwise the compiler may overlap the
+// rounds' independent rows and hold all their limbs at once.
+PL_DEV int seq_zero(uint32_t carry_word) { return (int)(carry_word >> 31); }
 
-// lo, w = A_k A_p (p = the partner lane; its limbs arrive by shuffle row by row)
+// lo, w = A_k * (partner p's chunk of src): S rows over this lane's a, the
+// multiplier limbs arriving from lane p by shuffle, row by row
 template <int S, int T, int... I>
-PL_DEV void sq_pair(uint32_t (&lo)[S], uint32_t (&w)[S], const uint32_t (&a)[S], int p, unsigned mask,
-                    std::integer_sequence<int, I...>) {
+PL_DEV void sos_pair(uint32_t (&lo)[S], uint32_t (&w)[S], const uint32_t (&a)[S], const uint32_t (&src)[S], int p,
+                     unsigned mask, std::integer_sequence<int, I...>) {
   uint32_t x1 = 0, x2 = 0;
 #pragma unroll
   for (int j = 0; j < S; ++j) w[j] = 0;
-  ((row_from<S, I % S, 0>(w, x1, x2, a, __shfl_sync(mask, a[I], after(p, x1), T)), leave<S, I>(w, x1, x2, lo[I])),
+  ((row_from<S, I % S, 0>(w, x1, x2, a, __shfl_sync(mask, src[I], after(p, x1), T)),
+    leave_w<S, I>(w, x1, x2, lo[I])),
    ...);
 }
 
-// shift of a lane-local window of SW limbs by one limb: logical limb I leaves into out
-template <int SW, int I>
-PL_DEV void leave_w(uint32_t (&w)[SW], uint32_t& x1, uint32_t& x2, uint32_t& out) {
-  out = w[I % SW];
-  w[I % SW] = x1;
-  x1 = x2;
-  x2 = 0;
-}
-
-// row I of sq_half: multiplier = limb I of the pair's lower chunk (this lane's
+// row I of sos_half: multiplier = limb I of the pair's lower chunk (this lane's
 // own limb on the lower lane, the partner's on the upper lane; every lane
 // takes part in the shuffle)
 template <int S, int T, int I>
@@ -356,8 +337,8 @@ PL_DEV void half_row(uint32_t (&w)[S / 2], uint32_t& x1, uint32_t& x2, uint32_t 
 // upper chunk, the upper lane A_j times its high half (then shifted up by S/2
 // limbs); both are S rows (the limbs of A_j) over an S/2-limb multiplicand.
 template <int S, int T, int... I>
-PL_DEV void sq_half(uint32_t (&lo)[S], uint32_t (&hi)[S], const uint32_t (&a)[S], int k, int z, unsigned mask,
-                    std::integer_sequence<int, I...>) {
+PL_DEV void sos_half(uint32_t (&lo)[S], uint32_t (&hi)[S], const uint32_t (&a)[S], int k, int z, unsigned mask,
+                     std::integer_sequence<int, I...>) {
   constexpr int H = S / 2;
   const int p = (k ^ (T / 2)) + z;
   const bool up = k >= T / 2;
@@ -392,28 +373,26 @@ PL_DEV void add_masked(uint32_t (&R)[S], uint32_t& c, const uint32_t (&v)[S], ui
   addc(c, 0u);
 }
 
-// Chunk of lane s's product in a squaring round (RK 0: diag, 1: pair at
-// distance D, 2: half).
-template <int T, int RK, int D>
-PL_DEV int sq_chunk(int s) {
-  if constexpr (RK == 0) return 2 * s;
-  else if constexpr (RK == 1) return s + ((s + D) & (T - 1));
-  else return 2 * (s & (T / 2 - 1)) + T / 2;
+// Chunk of lane s's product in a round: pair rounds at distance D (D = 0: the
+// diagonal chunks), or the half round.
+template <int T>
+PL_DEV int sos_chunk(int s, bool half, int D) {
+  return half ? 2 * (s & (T / 2 - 1)) + T / 2 : s + ((s + D) & (T - 1));
 }
 
 // Adds to this lane's chunks (Rl: chunk k, Rh: chunk k + T) the halves of the
 // round's products (lo, w of every lane) that land there; lo, w are clobbered.
-template <int S, int T, int RK, int D>
-PL_DEV void sq_route(uint32_t (&lo)[S], uint32_t (&w)[S], uint32_t (&Rl)[S], uint32_t& cl, uint32_t (&Rh)[S],
-                     uint32_t& ch, int k, unsigned mask) {
-  constexpr int dp = (RK == 0) ? 0 : D;
-  const int r = (k - dp) & (T - 1);
+// D is the round's distance (T/2 for the half round).
+template <int S, int T>
+PL_DEV void sos_route(uint32_t (&lo)[S], uint32_t (&w)[S], uint32_t (&Rl)[S], uint32_t& cl, uint32_t (&Rh)[S],
+                      uint32_t& ch, int k, bool half, int D, unsigned mask) {
+  const int r = (k - D) & (T - 1);
   const int high = r & 1;  // this lane receives high halves (else low halves)
   const int base = r >> 1;
   const int sx = base + (high ? T / 2 : 0);
   const int sy = base + (high ? 0 : T / 2);
-  const bool xhi = sq_chunk<T, RK, D>(sx) + high >= T;
-  const bool yhi = sq_chunk<T, RK, D>(sy) + high >= T;
+  const bool xhi = sos_chunk<T>(sx, half, D) + high >= T;
+  const bool yhi = sos_chunk<T>(sy, half, D) + high >= T;
   const bool lowside = k < T / 2;
 #pragma unroll
   for (int u = 0; u < S; ++u) {
@@ -429,23 +408,6 @@ PL_DEV void sq_route(uint32_t (&lo)[S], uint32_t (&w)[S], uint32_t (&Rl)[S], uin
   add_masked<S>(Rh, ch, w, ~myl);
 }
 
-// z: zero, computed from the previous round's carry word (a carry word counts a
-// few carries, far below 2^31).  Adding it to the round's shuffle lane makes the
-// round wait for the previous one: without it the compiler interleaves the
-// rounds' independent product rows and holds all their limbs at once.
-PL_DEV int seq_zero(uint32_t carry_word) { return (int)(carry_word >> 31); }
-
-template <int S, int T, int D>
-PL_DEV void sq_pair_rounds(uint32_t (&Rl)[S], uint32_t& cl, uint32_t (&Rh)[S], uint32_t& ch, const uint32_t (&a)[S],
-                           int k, unsigned mask) {
-  if constexpr (D < T / 2) {
-    uint32_t lo[S], w[S];
-    sq_pair<S, T>(lo, w, a, ((k + D) & (T - 1)) + seq_zero(cl | ch), mask, std::make_integer_sequence<int, S>{});
-    sq_route<S, T, 1, D>(lo, w, Rl, cl, Rh, ch, k, mask);
-    sq_pair_rounds<S, T, D + 1>(Rl, cl, Rh, ch, a, k, mask);
-  }
-}
-
 // R, c = 2 (R + c X) in carry-save form
 template <int S>
 PL_DEV void dbl(uint32_t (&R)[S], uint32_t& c) {
@@ -453,19 +415,6 @@ PL_DEV void dbl(uint32_t (&R)[S], uint32_t& c) {
 #pragma unroll
   for (int j = S - 1; j > 0; --j) R[j] = __funnelshift_l(R[j - 1], R[j], 1);
   R[0] <<= 1;
-}
-
-// R += sum_u v_u^2 2^(64 u) (S/2 squares over S limbs), carry into c
-template <int S>
-PL_DEV void add_squares(uint32_t (&R)[S], uint32_t& c, const uint32_t (&v)[S / 2]) {
-  mad_lo_cc(R[0], v[0], v[0]);
-  madc_hi_cc(R[1], v[0], v[0]);
-#pragma unroll
-  for (int u = 1; u < S / 2; ++u) {
-    madc_lo_cc(R[2 * u], v[u], v[u]);
-    madc_hi_cc(R[2 * u + 1], v[u], v[u]);
-  }
-  addc(c, 0u);
 }
 
 // one reduction step at rotation U: m = t_0 N'; t += m N; shift by one limb
@@ -495,56 +444,42 @@ PL_DEV void redc_block(uint32_t (&t)[S], uint32_t& x1, uint32_t& x2, const uint3
   (redc_step<S, T, U>(t, x1, x2, n, np, k, mask), ...);
 }
 
-// Whether mont_sqr is compiled for this shape (it holds about 6 S limbs per
-// lane at once; wider slices keep to mont_mul).
+// Whether mont_sos is compiled for this shape (the half round's S/2-limb rows
+// need an even S/2; it holds about 7 S limbs per lane at once, so wider slices
+// keep to mont_mul).
 template <int S, int T>
-constexpr bool kHaveSqr = (S % 4 == 0) && (S <= 24) && (T >= 2) && (T <= 16) && ((T & (T - 1)) == 0);
+constexpr bool kHaveSos = (S % 4 == 0) && (S <= 24) && (T >= 2) && (T <= 16) && ((T & (T - 1)) == 0);
 
-// r = a^2 R^-1 mod N (canonical), a canonical (this lane's slice); r may alias a.
+// r = a src R^-1 mod N (square: src is a, and r = a^2 R^-1 mod N), canonical;
+// a, src canonical (this lane's slices).  r may alias a or src.
 template <int S, int T>
-PL_DEV void mont_sqr(uint32_t (&r)[S], const uint32_t (&a)[S], const uint32_t (&n)[S], uint32_t np, int k,
-                     unsigned mask = kFull) {
-  static_assert(kHaveSqr<S, T>, "no squaring for this shape");
+PL_DEV void mont_sos(uint32_t (&r)[S], const uint32_t (&a)[S], const uint32_t (&src)[S], const uint32_t (&n)[S],
+                     uint32_t np, int k, bool square, unsigned mask = kFull) {
+  static_assert(kHaveSos<S, T>, "no SOS product for this shape");
   uint32_t Rl[S], Rh[S], cl = 0, ch = 0;
 #pragma unroll
   for (int j = 0; j < S; ++j) {
     Rl[j] = 0;
     Rh[j] = 0;
   }
-  {
-    uint32_t lo[S], w[S];
-    sq_diag<S>(lo, w, a, std::make_integer_sequence<int, S>{});
-    sq_route<S, T, 0, 0>(lo, w, Rl, cl, Rh, ch, k, mask);
-  }
-  sq_pair_rounds<S, T, 1>(Rl, cl, Rh, ch, a, k, mask);
-  {
-    uint32_t lo[S], w[S];
-    sq_half<S, T>(lo, w, a, k, seq_zero(cl | ch), mask, std::make_integer_sequence<int, S>{});
-    sq_route<S, T, 2, T / 2>(lo, w, Rl, cl, Rh, ch, k, mask);
-  }
-  dbl<S>(Rl, cl);
-  dbl<S>(Rh, ch);
-  {
-    // the squares of the limbs in this lane's chunks: chunk k holds those of
-    // half (k & 1) of lane k >> 1, chunk k + T those of the same half of lane
-    // (k + T) >> 1; two shuffles, each sending lane serving one receiver
-    const bool even = (k & 1) == 0;
-    const bool lowside = k < T / 2;
-    const int z = seq_zero(cl | ch);
-    const int sa = (even ? (k >> 1) : ((k + T) >> 1)) + z;
-    const int sb = (even ? ((k + T) >> 1) : (k >> 1)) + z;
-    uint32_t vl[S / 2], vh[S / 2];
-#pragma unroll
-    for (int u = 0; u < S / 2; ++u) {
-      const uint32_t x = lowside ? a[u] : a[u + S / 2];
-      const uint32_t y = lowside ? a[u + S / 2] : a[u];
-      const uint32_t vx = __shfl_sync(mask, x, sa, T);
-      const uint32_t vy = __shfl_sync(mask, y, sb, T);
-      vl[u] = even ? vx : vy;
-      vh[u] = even ? vy : vx;
+  const int nround = square ? T / 2 + 1 : T;
+#pragma unroll 1
+  for (int rd = 0; rd < nround; ++rd) {
+    // square: rounds D = 1 .. T/2 - 1, the half round, then (after doubling) D = 0; product: D = rd
+    const bool half = square && rd == T / 2 - 1;
+    const int D = square ? (half ? T / 2 : (rd == T / 2 ? 0 : rd + 1)) : rd;
+    if (square && rd == T / 2) {
+      dbl<S>(Rl, cl);
+      dbl<S>(Rh, ch);
     }
-    add_squares<S>(Rl, cl, vl);
-    add_squares<S>(Rh, ch, vh);
+    const int z = seq_zero(cl | ch);
+    uint32_t lo[S], w[S];
+    if (half) {
+      sos_half<S, T>(lo, w, a, k, z, mask, std::make_integer_sequence<int, S>{});
+    } else {
+      sos_pair<S, T>(lo, w, a, src, ((k + D) & (T - 1)) + z, mask, std::make_integer_sequence<int, S>{});
+    }
+    sos_route<S, T>(lo, w, Rl, cl, Rh, ch, k, half, D, mask);
   }
   // reduction of the low half, then the high half added
   uint32_t x1 = cl, x2 = 0;

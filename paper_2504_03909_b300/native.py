@@ -46,7 +46,7 @@ SIGNATURES = {
     "paillier_sync": (_i, [_vp, C.POINTER(_i)]),
     "paillier_last_error": (C.c_char_p, []),
     "paillier_test_mont_mul": (_i, [_i, _i, _vp, _vp, _vp, _sz, _vp, _vp]),
-    "paillier_test_mont_sqr": (_i, [_i, _i, _vp, _vp, _sz, _vp, _vp]),
+    "paillier_test_mont_sos": (_i, [_i, _i, _vp, _vp, _vp, _sz, _vp, _vp]),
     "paillier_test_bounds_report": (_i, [_i, _vp]),
     "paillier_test_schedule_ops": (_i, [_vp, _i, _i, _vp, _vp]),
     "paillier_imad_peak": (_i, [_i, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),

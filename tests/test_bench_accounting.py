@@ -72,11 +72,45 @@ def test_montgomery_and_exponentiation_counts():
 def test_encryption_totals_add_over_stages_and_halves():
     p, q = 0xF7E3_5A1B_C2D4_E6F9, 0xE1C3_A5B7_99DB_FD13  # odd numbers standing in for the primes
     n_bits, w = 128, 5
-    first, second = bench.enc_imad_stages(n_bits, w, p, q)
     L = n_bits // 32
-    assert first == sum(bench.exp_montmuls(xo % (x - 1), w) for x, xo in ((p, q), (q, p))) * bench.mont_imad(L // 2)
-    assert second == sum(bench.exp_montmuls(x, w) for x in (p, q)) * bench.mont_imad(L)
-    assert bench.enc_imad(n_bits, w, p, q) == first + second
+    for cios in (False, True):  # 4 limbs on 4 lanes: no separated-form shape, every product at the CIOS cost
+        first, second = bench.enc_imad_stages(n_bits, w, p, q, 4, cios)
+        assert first == sum(bench.exp_montmuls(xo % (x - 1), w) for x, xo in ((p, q), (q, p))) * bench.mont_imad(L // 2)
+        assert second == sum(bench.exp_montmuls(x, w) for x in (p, q)) * bench.mont_imad(L)
+        assert bench.enc_imad(n_bits, w, p, q, 4, cios) == first + second
+
+
+@pytest.mark.parametrize("w", [2, 5, 6])
+def test_schedule_split_counts_the_squarings_and_products(w):
+    """schedule_split separates the schedule after its leading window into the
+    squarings and the products by a table entry, as the worked schedule lists them."""
+    rng = random.Random(10 + w)
+    for bits in (1, 2, 64, 1024):
+        e = rng.getrandbits(bits) | (1 << (bits - 1))
+        ops = sliding_schedule(e, w)[1:]
+        assert bench.schedule_split(e, w) == (sum(o[0] == "sq" for o in ops), sum(o[0] == "mul" for o in ops))
+    assert bench.schedule_split(0b1011, 2) == (3, 1)
+
+
+@pytest.mark.parametrize("nl,lanes", [(32, 2), (32, 4), (64, 4), (64, 8), (96, 4), (96, 8)])
+def test_separated_form_square_count(nl, lanes):
+    """A separated-form square forms every unordered pair of lane chunks once
+    (T (T - 1) / 2 pairs of s^2 limb products) and every diagonal chunk once
+    (T s^2), then reduces like a product (nl^2 limb products + nl mul.lo): the
+    round-by-round count of the bench equals this pair count, and a product is
+    the CIOS count."""
+    s = nl // lanes
+    assert bench.sos_shape(nl, lanes)
+    pairs = lanes * (lanes - 1) // 2 * s * s + lanes * s * s
+    assert bench.sos_square_imad(nl, lanes) == 2 * pairs + 2 * nl * nl + nl
+    assert bench.sos_square_imad(nl, lanes) < bench.mont_imad(nl)
+    # shapes the kernels keep on CIOS
+    assert not bench.sos_shape(96, 16) and not bench.sos_shape(64, 2) and not bench.sos_shape(4, 4)
+    # an exponentiation: the schedule's squarings at the separated-form cost, the rest CIOS
+    e, w = (1 << 1023) | 0x1234567, 6
+    sq, pr = bench.schedule_split(e, w)
+    cios = bench.exp_montmuls(e, w) * bench.mont_imad(nl)
+    assert bench.exp_imad(e, w, nl, lanes) == cios - sq * (bench.mont_imad(nl) - bench.sos_square_imad(nl, lanes))
 
 
 @pytest.mark.parametrize("w", [4, 5, 6, 7])

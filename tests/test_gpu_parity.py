@@ -74,27 +74,30 @@ def test_mont_mul_random_and_edges(limbs, lanes):
         assert not bad, f"N={N:#x} first bad index {bad[0]}: a={A[bad[0]]:#x} b={B[bad[0]]:#x}"
 
 
-SQR_LANES = [(32, 2), (32, 4), (64, 4), (64, 8), (96, 4), (96, 8)]
+SOS_LANES = [(32, 2), (32, 4), (64, 4), (64, 8), (96, 4), (96, 8)]
 
 
-def _sqr_gpu(limbs, lanes, N, A):
+def _sos_gpu(limbs, lanes, N, A, B=None):
     a = _dev(synth.ints_to_limbs(A, limbs))
+    b = _dev(synth.ints_to_limbs(B, limbs)) if B is not None else None
     out = torch.empty_like(a)
     Nl = synth.int_to_limbs(N, limbs)
-    native.call("paillier_test_mont_sqr", limbs, lanes, Nl.ctypes.data, a.data_ptr(), len(A), out.data_ptr(),
+    native.call("paillier_test_mont_sos", limbs, lanes, Nl.ctypes.data, a.data_ptr(),
+                b.data_ptr() if b is not None else None, len(A), out.data_ptr(),
                 torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     return synth.limbs_to_ints(P.from_limb_tensor(out))
 
 
-@pytest.mark.parametrize("limbs,lanes", SQR_LANES)
-def test_mont_sqr_random_and_edges(limbs, lanes):
-    """The squaring path of the exponentiations (each cross product formed
-    once, chunk products spread over the lanes) equals a^2 R^-1 mod N on the
-    moduli and edge inputs of the product test: all-ones limbs (N = R - 1, so
-    (P + M N) / R reaches its 2N bound), top limb 1 or 2, a composite N with
-    squares = 0 mod N, long carry chains, and values with all-ones or zero
-    chunks (every lane's share of the cross products at its extremes)."""
+@pytest.mark.parametrize("limbs,lanes", SOS_LANES)
+def test_mont_sos_products_and_squares(limbs, lanes):
+    """The separated-form Montgomery body of the exponentiations (chunk-pair
+    rounds over the lanes, products and squares in one routine) equals
+    a b R^-1 mod N and a^2 R^-1 mod N on the moduli and edge inputs of the
+    product test: all-ones limbs (N = R - 1, so (P + M N) / R reaches its 2N
+    bound), top limb 1 or 2, a composite N with results = 0 mod N, long carry
+    chains, and values with one lane's chunk all ones or zero (every lane's
+    share of the chunk products at its extremes)."""
     rng = random.Random(limbs * 1000 + lanes)
     R = 1 << (32 * limbs)
     S = limbs // lanes
@@ -105,7 +108,7 @@ def test_mont_sqr_random_and_edges(limbs, lanes):
     for N in moduli:
         A = [0, 1, 2, N - 1, N - 2, N // 2, (1 << 32) - 1, R // 2 % N, (R - 1) % N, (N - 1) // 3]
         if N == p * q:
-            # multiples of q and of p: squares sharing a factor with N
+            # multiples of q and of p: results sharing a factor with N (0 mod N for the products p x q)
             A += [q * rng.randrange(1, p) for _ in range(32)]
             A += [N - p * rng.randrange(1, q) for _ in range(32)]
         # one lane's chunk all ones, the others zero (and the complement)
@@ -115,11 +118,18 @@ def test_mont_sqr_random_and_edges(limbs, lanes):
         for s in (1, limbs // 2, limbs - 1):
             A.append(((1 << (32 * s)) - 1) % N)
         A += [rng.randrange(N) for _ in range(1500)]
-        got = _sqr_gpu(limbs, lanes, N, A)
+        B = [A[(i * 7 + 3) % len(A)] for i in range(len(A))]  # every edge against many partners
+        if N == p * q:
+            B[10:42] = [p * rng.randrange(1, q) for _ in range(32)]  # q-multiples x p-multiples = 0 mod N
         Rinv = pow(R, -1, N)
+        got = _sos_gpu(limbs, lanes, N, A, B)
+        want = [a * b * Rinv % N for a, b in zip(A, B)]
+        bad = [i for i in range(len(A)) if got[i] != want[i]]
+        assert not bad, f"product N={N:#x} first bad index {bad[0]}: a={A[bad[0]]:#x} b={B[bad[0]]:#x}"
+        got = _sos_gpu(limbs, lanes, N, A)
         want = [a * a * Rinv % N for a in A]
         bad = [i for i in range(len(A)) if got[i] != want[i]]
-        assert not bad, f"N={N:#x} first bad index {bad[0]}: a={A[bad[0]]:#x}"
+        assert not bad, f"square N={N:#x} first bad index {bad[0]}: a={A[bad[0]]:#x}"
 
 
 # ---------------------------------------------------------------------------
