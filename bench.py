@@ -44,7 +44,7 @@ METRIC = "2048-bit Paillier enc/s & encrypted-hist ct-mults/s; p50/p99 request m
 # DRAM bytes (read + write) per encryption of the current encryption kernel that dominates the
 # step (the second stage when encryption runs as two launches), from an ncu capture of
 # 16,384 encryptions of this kernel version, keyed by (n_bits, window)
-TRAFFIC_PER_ENC = {(2048, 6): (311.65e6 + 248.54e6) / 16384}
+TRAFFIC_PER_ENC = {(2048, 6): (164.205568e6 + 241.173760e6) / 16384}
 
 
 # ----------------------------------------------------------------------------
@@ -100,9 +100,9 @@ def schedule_split(e: int, w: int):
 def sos_shape(nl: int, lanes: int) -> bool:
     """Whether the exponentiation kernel at nl limbs and `lanes` lanes runs its
     schedule through the separated-form body (a multiple of 4 limbs per lane, at
-    most 24, 2 to 16 lanes)."""
+    most 24, 4 to 16 lanes)."""
     s = nl // lanes
-    return nl % lanes == 0 and s % 4 == 0 and 4 <= s <= 24 and 2 <= lanes <= 16 and lanes & (lanes - 1) == 0
+    return nl % lanes == 0 and s % 4 == 0 and 4 <= s <= 24 and 4 <= lanes <= 16 and lanes & (lanes - 1) == 0
 
 
 def sos_square_imad(nl: int, lanes: int) -> int:

@@ -64,8 +64,8 @@ __global__ void k_decode(const uint64_t* __restrict__ s, const int32_t* __restri
 // acc: the base in Montgomery form on entry, base^e in Montgomery form on exit,
 // e given by its schedule op[0..nop) (layout in ModexpParams).  tbl: this
 // group's table of 2^(w-1) entries of S*T limbs (the odd powers); bs: its
-// shared-memory column.  Every op is one Montgomery product: where the shape
-// has it, the separated-form body mont_sos for squarings and products alike
+// shared-memory column.  Every op is one Montgomery product: at 4 lanes and up,
+// the separated-form body mont_sos for squarings and products alike
 // (one routine's code in the loop; a square forms each cross product once),
 // else mont_mul with the multiplier staged in shared memory.  The table build
 // runs once per exponentiation and keeps mont_mul.
@@ -98,7 +98,7 @@ PL_DEV void window_exp(uint32_t (&acc)[S], const uint32_t (&n)[S], uint32_t np, 
   load_slice_rw<S>(a, tbl + (size_t)entry(op[0]) * NL, k);
   for (int i = 1; i < nop; ++i) {
     const int v = op[i];  // the same for every instance of the warp
-    if constexpr (kHaveSos<S, T>) {
+    if constexpr (kUseSos<S, T>) {
       if (v != 0) {
         load_slice_rw<S>(t, tbl + (size_t)entry(v) * NL, k);
       } else {

@@ -24,6 +24,12 @@
 // Row updates t += a * b_i use the PTX carry chain (mad.lo.cc / madc.hi.cc),
 // split into the even and odd products so that each chain writes every limb
 // once.
+//
+// The exponentiations run their schedules through a second form, mont_sos
+// (separated operand scanning): the whole product is formed first as chunk
+// products spread evenly over the lanes (a square forms each cross product
+// once), then reduced by the second half of the CIOS steps; it is defined
+// with its description further down.
 #pragma once
 
 #include <cstdint>
@@ -449,6 +455,13 @@ PL_DEV void redc_block(uint32_t (&t)[S], uint32_t& x1, uint32_t& x2, const uint3
 // keep to mont_mul).
 template <int S, int T>
 constexpr bool kHaveSos = (S % 4 == 0) && (S <= 24) && (T >= 2) && (T <= 16) && ((T & (T - 1)) == 0);
+
+// Whether the exponentiations use it at this shape: from 4 lanes up.  On 2
+// lanes a square saves only a quarter of the multiplication rows and, measured
+// on a B300, the separated form was slower there (1024-bit encryption 1.70M
+// against 1.86M/s, the first stage of 2048-bit encryption 397 against 391 ms).
+template <int S, int T>
+constexpr bool kUseSos = kHaveSos<S, T> && (T >= 4);
 
 // r = a src R^-1 mod N (square: src is a, and r = a^2 R^-1 mod N), canonical;
 // a, src canonical (this lane's slices).  r may alias a or src.

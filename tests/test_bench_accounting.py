@@ -92,7 +92,7 @@ def test_schedule_split_counts_the_squarings_and_products(w):
     assert bench.schedule_split(0b1011, 2) == (3, 1)
 
 
-@pytest.mark.parametrize("nl,lanes", [(32, 2), (32, 4), (64, 4), (64, 8), (96, 4), (96, 8)])
+@pytest.mark.parametrize("nl,lanes", [(32, 4), (64, 4), (64, 8), (96, 4), (96, 8)])
 def test_separated_form_square_count(nl, lanes):
     """A separated-form square forms every unordered pair of lane chunks once
     (T (T - 1) / 2 pairs of s^2 limb products) and every diagonal chunk once
@@ -105,7 +105,7 @@ def test_separated_form_square_count(nl, lanes):
     assert bench.sos_square_imad(nl, lanes) == 2 * pairs + 2 * nl * nl + nl
     assert bench.sos_square_imad(nl, lanes) < bench.mont_imad(nl)
     # shapes the kernels keep on CIOS
-    assert not bench.sos_shape(96, 16) and not bench.sos_shape(64, 2) and not bench.sos_shape(4, 4)
+    assert not any(bench.sos_shape(*x) for x in ((96, 16), (64, 2), (32, 2), (4, 4)))
     # an exponentiation: the schedule's squarings at the separated-form cost, the rest CIOS
     e, w = (1 << 1023) | 0x1234567, 6
     sq, pr = bench.schedule_split(e, w)
