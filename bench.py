@@ -1467,7 +1467,8 @@ def run_serving(args, cfg, emit=True):
 
     def submit(srv, rq):
         return srv.submit(keys[rq["nb"]], ctms[rq["nb"]], rq["M"], rq["F"], rq["K"], bins[rq["party"]][rq["K"]],
-                          gh_stride=MMAX, bins_stride=MMAX, pack_bits=args.pack_bits, gh_bits=args.gh_bits)
+                          gh_stride=MMAX, bins_stride=MMAX, pack_bits=args.pack_bits, gh_bits=args.gh_bits,
+                          pack_slots=args.pack_slots)
 
     ngh = 1 if args.gh_bits else 2
 
@@ -1478,8 +1479,10 @@ def run_serving(args, cfg, emit=True):
         w = 6 if rq["nb"] >= 2048 else 5
         cells = ngh * rq["F"] * rq["K"]
         slot_bits = 2 * args.gh_bits if args.gh_bits else args.pack_bits
-        if args.pack_bits:
-            slots = (rq["nb"] - 2) // slot_bits
+        # the cells per packed ciphertext the server chooses for this request
+        slots = P.Server.request_plan(keys[rq["nb"]], rq["M"], rq["F"], rq["K"], pack_bits=args.pack_bits,
+                                      gh_bits=args.gh_bits, pack_slots=args.pack_slots)[0]
+        if slots:
             dec = -(-cells // slots) * dec_imad(rq["nb"], w) + cells * (slot_bits + 2) * mont_imad(2 * L)
         else:
             dec = cells * dec_imad(rq["nb"], w)
@@ -1534,7 +1537,8 @@ def run_serving(args, cfg, emit=True):
                                "2048/3072-bit keys p = 0.5, resident ciphertexts", "slots": args.slots,
                    "hbm_budget_bytes": budget, "offered_load": args.load, "requests": args.requests,
                    "promote_ms": args.promote_ms,
-                   "pack_bits": args.pack_bits, "gh_bits": args.gh_bits},
+                   "pack_bits": args.pack_bits, "gh_bits": args.gh_bits,
+                   "pack_slots": args.pack_slots or "auto"},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "by_size": serving_classes(done_rq, lat, work),
         "mean_ms": float(lat.mean()), "throughput_req_per_s": len(lat) / wall,
@@ -1593,7 +1597,7 @@ def run_legs(args, line):
     sv = run_serving(sa, synth.CONFIGS.get("serving", {}), emit=False)
     line["serving"] = {
         "workload": sv["config"]["workload"], "offered_load": sa.load, "requests": sa.requests, "slots": sa.slots,
-        "gh_bits": sa.gh_bits, "pack_bits": sa.pack_bits,
+        "gh_bits": sa.gh_bits, "pack_bits": sa.pack_bits, "pack_slots": sa.pack_slots or "auto",
         "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "mean_ms": sv["mean_ms"], "by_size": sv["by_size"],
         "throughput_req_per_s": sv["throughput_req_per_s"], "capacity_req_per_s": sv["capacity_req_per_s"],
         "server": sv["server"], "clocks": sv["clocks"],
@@ -1654,6 +1658,9 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=300, help="serving leg of the level run: timed requests")
     ap.add_argument("--serve-gh-bits", type=int, default=0, help="serving leg: g/h packing bits (0 = two arrays)")
     ap.add_argument("--serve-pack-bits", type=int, default=46, help="serving leg: ciphertext packing bits")
+    ap.add_argument("--pack-slots", type=int, default=0,
+                    help="serving (and its leg): cells per packed ciphertext at most (0 = the server's rule, "
+                         "fewer for requests of little histogram work; a large value = as many as fit)")
     args = ap.parse_args()
     cfg = synth.CONFIGS.get(args.config, {})
     if args.gh_bits is None:

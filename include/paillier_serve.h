@@ -57,6 +57,17 @@ typedef struct pl_request {
    * paillier_ct_prepare; gh_stride is not used); the cells split into
    * (S_g, S_h) at bit G, and a nonzero pack_bits packs them in 2G-bit slots. */
   int gh_bits;
+  /* Cells per packed ciphertext when pack_bits > 0.  N > 0: at most N (the
+   * most that fit when N is larger).  0: chosen from the request -- the most
+   * that fit for a request whose histogram alone is modelled at 3e12
+   * multiply-adds or more (the default large_imad of pl_server_set_policy),
+   * else few enough to leave at least 1,024 packed ciphertexts.  Each packed ciphertext is a chain of
+   * (slots - 1) (B + 1) products mod n^2 run one after another, so for a
+   * request with few cells that chain, not the GPU's throughput, bounds the
+   * packing time; shorter chains cost more decryptions.  A choice of one
+   * cell per ciphertext decrypts the cells directly.  The sums do not depend
+   * on it. */
+  int pack_slots;
 } pl_request;
 
 #define PL_REQ_QUEUED    0
@@ -90,6 +101,12 @@ pl_status pl_server_wait(pl_server* srv, uint64_t ticket, int timeout_ms, int* s
 /* Device memory the server reserves against its budget while the request
  * runs (outputs and scratch), for sizing budgets. */
 pl_status pl_server_request_bytes(const pl_request* req, size_t* bytes);
+
+/* The server's plan for a request, without a server: *slots = cells per
+ * packed ciphertext (0: the cells are decrypted directly) and *work_imad =
+ * the modelled multiply-adds that classify it (see pl_server_set_policy).
+ * Either output may be NULL. */
+pl_status pl_server_request_plan(const pl_request* req, int* slots, double* work_imad);
 
 /* Cancels a request that is still queued (PL_EINVAL if it was admitted). */
 pl_status pl_server_cancel(pl_server* srv, uint64_t ticket);

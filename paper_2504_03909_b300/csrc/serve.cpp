@@ -80,6 +80,33 @@ struct Slot {
 
 size_t round_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+// modelled multiply-adds (IMAD: one 32-bit half of a limb product) of one Montgomery product on nl limbs
+double mont_imad(double nl) { return 4 * nl * nl + nl; }
+double hist_imad(const pl_request& r) {
+  return (r.gh_bits ? 1.0 : 2.0) * (double)r.M * r.F * mont_imad(2.0 * r.key->L);
+}
+
+// automatic packing: packed ciphertexts a request of little histogram work
+// keeps at least (packing stays latency-bound on the GPU up to about this many
+// chains), and the histogram work from which a request packs as many cells as fit
+constexpr size_t kPackChains = 1024;
+constexpr double kPackFullImad = 3e12;
+
+// cells per packed ciphertext of a request, 0: no packing (also when one cell
+// per ciphertext would be chosen: the cells are then decrypted directly)
+int request_slots(const pl_request& r) {
+  if (r.pack_bits <= 0) return 0;
+  const int slot_bits = r.gh_bits ? 2 * r.gh_bits : r.pack_bits;
+  int slots = (r.key->n_bits - 2) / slot_bits;
+  if (r.pack_slots > 0) {
+    slots = std::min(slots, r.pack_slots);
+  } else if (hist_imad(r) < kPackFullImad) {
+    const size_t hcells = (size_t)r.num_nodes * r.F * r.K * (r.gh_bits ? 1 : 2);
+    slots = (int)std::min<size_t>((size_t)slots, (hcells + kPackChains - 1) / kPackChains);
+  }
+  return slots >= 2 ? slots : 0;
+}
+
 // device memory one request needs while it runs
 size_t request_bytes(const pl_request& r) {
   const size_t L = (size_t)r.key->L;
@@ -89,9 +116,7 @@ size_t request_bytes(const pl_request& r) {
   if (!r.d_node) b += round_up(r.M * 4);
   const pl::HistLayout h = pl::hist_layout(r.M, r.F, r.num_nodes * r.K, r.key->agg_cfg.tile, (int)(2 * L));
   size_t dec_cells = hcells;
-  if (r.pack_bits > 0) {
-    const int slot_bits = r.gh_bits ? 2 * r.gh_bits : r.pack_bits;
-    const size_t slots = (size_t)(r.key->n_bits - 2) / (size_t)slot_bits;
+  if (const size_t slots = (size_t)request_slots(r)) {
     dec_cells = (hcells + slots - 1) / slots;
     b += round_up(dec_cells * 2 * L * 4) + round_up(dec_cells * L * 4);  // packed ciphertexts + plaintexts
   } else if (r.gh_bits) {
@@ -101,8 +126,7 @@ size_t request_bytes(const pl_request& r) {
   return b;
 }
 
-// modelled multiply-adds (IMAD: one 32-bit half of a limb product) of the pieces of a request
-double mont_imad(double nl) { return 4 * nl * nl + nl; }
+// modelled multiply-adds of the pieces of a request
 double dec_imad(const pl_key* key) {
   // two CRT halves, about n_bits / 2 (1 + 1/6) products on L limbs each (sliding 6-bit windows)
   const double L = key->L;
@@ -119,9 +143,9 @@ Work request_work(const pl_request& r) {
   w.hist_per_feature = (double)ngh * (double)r.M * mont_imad(L2);
   w.dec_per_ct = dec_imad(r.key);
   double dec_cts = hcells;
-  if (r.pack_bits > 0) {
+  if (const int islots = request_slots(r)) {
     const int slot_bits = r.gh_bits ? 2 * r.gh_bits : r.pack_bits;
-    const double slots = (double)((r.key->n_bits - 2) / slot_bits);
+    const double slots = islots;
     w.pack_per_ct = slots * (slot_bits + 1) * mont_imad(L2);
     dec_cts = std::ceil(hcells / slots);
     w.total += dec_cts * w.pack_per_ct;
@@ -223,8 +247,8 @@ struct pl_server {
     auto* sums = static_cast<uint64_t*>(amalloc(2, cells * 8));
     const int32_t* node = r.d_node;
     if (!node) node = static_cast<int32_t*>(amalloc(3, r.M * 4));
-    const int slot_bits = r.pack_bits > 0 ? (r.gh_bits ? 2 * r.gh_bits : r.pack_bits) : 0;
-    const int slots = slot_bits ? (key->n_bits - 2) / slot_bits : 0;
+    const int slots = request_slots(r);
+    const int slot_bits = slots ? (r.gh_bits ? 2 * r.gh_bits : r.pack_bits) : 0;
     const size_t npacked = slots ? (hcells + slots - 1) / slots : 0;
     uint32_t* packed = nullptr;
     uint32_t* plain = nullptr;
@@ -445,6 +469,17 @@ pl_status pl_server_request_bytes(const pl_request* req, size_t* bytes) {
   return PL_OK;
 }
 
+pl_status pl_server_request_plan(const pl_request* req, int* slots, double* work_imad) {
+  using namespace pl;
+  clear_error();
+  if (!req || !req->key || req->num_nodes < 1 || req->F < 1 || req->K < 1) return fail(PL_EINVAL, "bad request");
+  if (req->pack_bits < 0 || req->pack_bits > 64 || req->pack_slots < 0)
+    return fail(PL_EINVAL, "pack_bits must be 0..64 and pack_slots >= 0");
+  if (slots) *slots = request_slots(*req);
+  if (work_imad) *work_imad = request_work(*req).total;
+  return PL_OK;
+}
+
 pl_status pl_server_submit(pl_server* srv, const pl_request* req, uint64_t* ticket) {
   using namespace pl;
   clear_error();
@@ -460,6 +495,7 @@ pl_status pl_server_submit(pl_server* srv, const pl_request* req, uint64_t* tick
   if (reinterpret_cast<uintptr_t>(r.d_ctm) & 15u) return fail(PL_EINVAL, "d_ctm must be 16-byte aligned");
   if (!agg_supported(2 * r.key->L, r.key->agg_cfg.T)) return fail(PL_EINVAL, "key configuration not supported");
   if (r.pack_bits < 0 || r.pack_bits > 64) return fail(PL_EINVAL, "pack_bits must be 0..64");
+  if (r.pack_slots < 0) return fail(PL_EINVAL, "pack_slots must be >= 0");
   Req q;
   q.r = r;
   q.bytes = request_bytes(r);

@@ -71,7 +71,7 @@ class Request(C.Structure):
     _fields_ = [("key", C.c_void_p), ("d_ctm", C.c_void_p), ("gh_stride", C.c_size_t), ("M", C.c_size_t),
                 ("F", C.c_int), ("K", C.c_int), ("d_bins", C.c_void_p), ("bins_stride", C.c_size_t),
                 ("d_node", C.c_void_p), ("num_nodes", C.c_int), ("h_sums", C.c_void_p), ("h_counts", C.c_void_p),
-                ("pack_bits", C.c_int), ("gh_bits", C.c_int)]
+                ("pack_bits", C.c_int), ("gh_bits", C.c_int), ("pack_slots", C.c_int)]
 
 
 SIGNATURES.update({
@@ -96,6 +96,7 @@ SIGNATURES.update({
     "pl_server_wait": (_i, [_vp, C.c_uint64, _i, C.POINTER(_i), C.POINTER(C.c_double)]),
     "pl_server_cancel": (_i, [_vp, C.c_uint64]),
     "pl_server_request_bytes": (_i, [C.POINTER(Request), C.POINTER(_sz)]),
+    "pl_server_request_plan": (_i, [C.POINTER(Request), C.POINTER(_i), C.POINTER(C.c_double)]),
     "pl_server_set_policy": (_i, [_vp, C.c_double, C.c_double, C.c_double, _i]),
     "pl_server_set_aging": (_i, [_vp, C.c_double]),
     "pl_server_policy_stats": (_i, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(_i),

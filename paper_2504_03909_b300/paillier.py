@@ -289,18 +289,19 @@ class Server:
 
     def submit(self, key: Key, ctm: torch.Tensor, M: int, F: int, K: int, bins: torch.Tensor,
                node: torch.Tensor | None = None, num_nodes: int = 1, gh_stride: int | None = None,
-               bins_stride: int | None = None, pack_bits: int = 0, gh_bits: int = 0):
+               bins_stride: int | None = None, pack_bits: int = 0, gh_bits: int = 0, pack_slots: int = 0):
         """Queues a request over the first M samples / F features of resident
         arrays (ctm: g and h arrays gh_stride rows apart, or with gh_bits one
         g/h-packed array); returns (ticket, host sums [num_nodes, F, K, 2]
-        uint64 (pinned), host counts [num_nodes, F, K] int32 (pinned))."""
+        uint64 (pinned), host counts [num_nodes, F, K] int32 (pinned)).
+        pack_slots: cells per packed ciphertext at most (0: the server's rule)."""
         ghs = gh_stride if gh_stride is not None else M
         bst = bins_stride if bins_stride is not None else M
         pc, pb, pn = _request_ptrs(key, ctm, M, F, bins, node, ghs, bst, gh_bits)
         sums = torch.empty((num_nodes, F, K, 2), dtype=torch.int64).pin_memory()
         counts = torch.empty((num_nodes, F, K), dtype=torch.int32).pin_memory()
         req = native.Request(key.handle.value, pc, ghs, M, F, K, pb, bst, pn, num_nodes, sums.data_ptr(),
-                             counts.data_ptr(), pack_bits, gh_bits)
+                             counts.data_ptr(), pack_bits, gh_bits, pack_slots)
         t = C.c_uint64()
         call("pl_server_submit", self._h, C.byref(req), C.byref(t))
         self._keep[t.value] = (sums, counts, ctm, bins, node, key)
@@ -309,12 +310,24 @@ class Server:
     @staticmethod
     def request_bytes(key: Key, ctm: torch.Tensor, M: int, F: int, K: int, bins: torch.Tensor,
                       node: torch.Tensor | None = None, num_nodes: int = 1, pack_bits: int = 0,
-                      gh_bits: int = 0) -> int:
+                      gh_bits: int = 0, pack_slots: int = 0) -> int:
         pc, pb, pn = _request_ptrs(key, ctm, M, F, bins, node, M, M, gh_bits)
-        req = native.Request(key.handle.value, pc, M, M, F, K, pb, M, pn, num_nodes, 0, 0, pack_bits, gh_bits)
+        req = native.Request(key.handle.value, pc, M, M, F, K, pb, M, pn, num_nodes, 0, 0, pack_bits, gh_bits,
+                             pack_slots)
         b = C.c_size_t()
         call("pl_server_request_bytes", C.byref(req), C.byref(b))
         return b.value
+
+    @staticmethod
+    def request_plan(key: Key, M: int, F: int, K: int, num_nodes: int = 1, pack_bits: int = 0,
+                     gh_bits: int = 0, pack_slots: int = 0):
+        """(cells per packed ciphertext (0: none), modelled multiply-adds) that
+        the server would choose for such a request; no buffers needed."""
+        req = native.Request(key.handle.value, None, M, M, F, K, None, M, None, num_nodes, None, None, pack_bits,
+                             gh_bits, pack_slots)
+        sl, w = C.c_int(), C.c_double()
+        call("pl_server_request_plan", C.byref(req), C.byref(sl), C.byref(w))
+        return sl.value, w.value
 
     def poll(self, ticket: int):
         st, lat, err = C.c_int(), C.c_double(), C.c_int()

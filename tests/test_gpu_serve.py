@@ -89,17 +89,30 @@ def test_mix_equals_alone_equals_direct(data):
     alone.close()
 
 
+# cells per packed ciphertext: the server's rule (these requests have few cells,
+# so it decrypts them directly), short chains, one cell (no packing), as many as fit
+PACK_SLOTS = (0, 3, 1, 10_000)
+
+
 def test_packed_requests_equal_unpacked(data):
     srv = P.Server(slots=3, hbm_budget=8 << 30)
     for rq in REQUESTS[:4]:
         nb, M, F, K, use_node = rq
         d = data[nb]
         node = d["node"] if use_node else None
-        kw = dict(node=node, num_nodes=4 if use_node else 1, gh_stride=MFULL, bins_stride=MFULL)
+        nn = 4 if use_node else 1
+        kw = dict(node=node, num_nodes=nn, gh_stride=MFULL, bins_stride=MFULL)
         t1, s1, c1 = srv.submit(d["key"], d["ctm"], M, F, K, d["bins"][K], **kw)
-        t2, s2, c2 = srv.submit(d["key"], d["ctm"], M, F, K, d["bins"][K], pack_bits=40, **kw)
-        assert srv.wait(t1)[0] == native.REQ_DONE and srv.wait(t2)[0] == native.REQ_DONE
-        assert torch.equal(s1, s2) and torch.equal(c1, c2)
+        runs = [srv.submit(d["key"], d["ctm"], M, F, K, d["bins"][K], pack_bits=40, pack_slots=ps, **kw)
+                for ps in PACK_SLOTS]
+        most = (nb - 2) // 40
+        chosen = [P.Server.request_plan(d["key"], M, F, K, num_nodes=nn, pack_bits=40, pack_slots=ps)[0]
+                  for ps in PACK_SLOTS]
+        assert chosen == [0, 3, 0, most]
+        assert srv.wait(t1)[0] == native.REQ_DONE
+        for t2, s2, c2 in runs:
+            assert srv.wait(t2)[0] == native.REQ_DONE
+            assert torch.equal(s1, s2) and torch.equal(c1, c2)
     srv.close()
 
 
@@ -115,11 +128,14 @@ def test_gh_packed_requests_equal_unpacked(data):
         kw = dict(node=node, num_nodes=4 if use_node else 1, bins_stride=MFULL)
         t1, s1, c1 = srv.submit(d["key"], d["ctm"], M, F, K, d["bins"][K], gh_stride=MFULL, **kw)
         t2, s2, c2 = srv.submit(d["key"], d["ctm_gh"], M, F, K, d["bins"][K], gh_bits=GH_BITS, **kw)
-        t3, s3, c3 = srv.submit(d["key"], d["ctm_gh"], M, F, K, d["bins"][K], gh_bits=GH_BITS, pack_bits=1, **kw)
-        for t in (t1, t2, t3):
+        packed = [srv.submit(d["key"], d["ctm_gh"], M, F, K, d["bins"][K], gh_bits=GH_BITS, pack_bits=1,
+                             pack_slots=ps, **kw) for ps in PACK_SLOTS]
+        for t in (t1, t2):
             assert srv.wait(t)[0] == native.REQ_DONE
         assert torch.equal(s1, s2) and torch.equal(c1, c2)
-        assert torch.equal(s1, s3) and torch.equal(c1, c3)
+        for t3, s3, c3 in packed:
+            assert srv.wait(t3)[0] == native.REQ_DONE
+            assert torch.equal(s1, s3) and torch.equal(c1, c3)
     with pytest.raises(native.PaillierError):
         srv.submit(data[1024]["key"], data[1024]["ctm_gh"], 10, 1, 8, data[1024]["bins"][8], gh_bits=20)
     srv.close()
