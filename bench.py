@@ -1386,8 +1386,10 @@ def run_batched(args, cfg, emit=True):
         "metric": METRIC, "value": ct_mults / t_batched, "unit": "ct-mults/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tree, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"{args.config}: depth-{depth} tree ({(1 << depth) - 1} nodes, Beta(0.5,0.5) "
-                               f"splits) on {M:,} samples x {F} features x {K} bins, {n_bits}-bit n; step = encrypt "
+        "config": {"workload": f"{args.config}: depth-{depth} tree ({(1 << depth) - 1} nodes, "
+                               + ("Beta(0.5,0.5) splits" if args.splits == "beta" else
+                                  "splits found on the decrypted histograms")
+                               + f") on {M:,} samples x {F} features x {K} bins, {n_bits}-bit n; step = encrypt "
                                "+ per-level histograms + CRT decrypt of every level's cells",
                    "M": M, "F": F, "K": K, "n_bits": n_bits,
                    "depth": depth, "autotuned": bool(args.autotune),
@@ -1574,7 +1576,8 @@ def run_legs(args, line):
     """The other two parts of the metric, measured after the level headline in
     the same run (one GPU): the batched depth-6 tree (one captured graph per
     level, autotuned launch configurations) against the plain per-node launch
-    path, and the serving loop's p50/p99 request latency at offered load 0.7."""
+    path, the same tree as the secure tree with the decrypt-count reductions,
+    and the serving loop's p50/p99 request latency at offered load 0.7."""
     import torch
     torch.cuda.empty_cache()
     ba = argparse.Namespace(**vars(args))
@@ -1589,6 +1592,20 @@ def run_legs(args, line):
         "speedup_vs_per_node": b["batched_speedup_vs_per_node"],
         "ct_mults_per_s_batched": b["value"], "tree_ms": b["tree_ms"], "phases_ms_per_tree": b["phases_ms_per_tree"],
         "steps": ba.steps, "warmup": ba.warmup, "clocks": b["clocks"], "verified": b["verified"],
+    }
+    torch.cuda.empty_cache()
+    # the secure tree with the decrypt-count reductions: splits found on the
+    # decrypted histograms, histogram subtraction, g/h packing (B = 45) and
+    # ciphertext packing in 90-bit slots
+    st = argparse.Namespace(**vars(ba))
+    st.gh_bits, st.pack_bits, st.splits, st.subtract, st.no_compare = 45, 45, "data", True, True
+    t = run_batched(st, synth.CONFIGS["batched"], emit=False)
+    line["secure_tree"] = {
+        "workload": t["config"]["workload"], "gh_bits": t["gh_bits"], "slot_bits": t["pack_bits"],
+        "pack_slots": t["pack_slots"], "splits": t["splits"], "subtract": t["subtract"],
+        "encryptions_per_tree": t["encryptions_per_tree"], "tree_ms": t["tree_ms"],
+        "phases_ms_per_tree": t["phases_ms_per_tree"], "ct_mults_per_s_batched": t["value"],
+        "steps": st.steps, "warmup": st.warmup, "clocks": t["clocks"], "verified": t["verified"],
     }
     torch.cuda.empty_cache()
     sa = argparse.Namespace(**vars(args))
