@@ -116,6 +116,23 @@ def test_packed_requests_equal_unpacked(data):
     srv.close()
 
 
+def test_automatic_packing_of_larger_requests(data):
+    """Requests with enough cells that the server's rule packs them (3,072
+    cells: 3 per packed ciphertext at least 1,024 packed ciphertexts), at each
+    key size, give the unpacked request's sums."""
+    srv = P.Server(slots=4, hbm_budget=8 << 30)
+    for nb in (1024, 2048, 3072):
+        d = data[nb]
+        M, F, K = MFULL, FFULL, 256
+        assert P.Server.request_plan(d["key"], M, F, K, pack_bits=40)[0] == 3
+        kw = dict(gh_stride=MFULL, bins_stride=MFULL)
+        t1, s1, c1 = srv.submit(d["key"], d["ctm"], M, F, K, d["bins"][K], **kw)
+        t2, s2, c2 = srv.submit(d["key"], d["ctm"], M, F, K, d["bins"][K], pack_bits=40, **kw)
+        assert srv.wait(t1)[0] == native.REQ_DONE and srv.wait(t2)[0] == native.REQ_DONE
+        assert torch.equal(s1, s2) and torch.equal(c1, c2)
+    srv.close()
+
+
 def test_gh_packed_requests_equal_unpacked(data):
     """Requests over one g/h-packed ciphertext array (half the histogram
     products and decryptions) give the sums of the two-array requests, with
