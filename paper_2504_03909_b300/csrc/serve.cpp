@@ -24,6 +24,10 @@
 // slots - `reserved` slots, so that small requests always find one free in
 // time (measured with FIFO admission over all classes: small requests had a
 // p99 of 1.8 s, waiting for one of 8 slots held by long requests).
+// Packing: each packed ciphertext is a serial chain of (slots - 1)(B + 1)
+// products, so a request with few cells keeps at least kPackChains packed
+// ciphertexts (request_slots): shorter chains for a few more decryptions
+// (measured: small requests' p50 69 -> 48 ms for 2.5 % of capacity).
 #include <algorithm>
 #include <cmath>
 #include <chrono>
