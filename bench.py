@@ -1577,7 +1577,8 @@ def run_legs(args, line):
     the same run (one GPU): the batched depth-6 tree (one captured graph per
     level, autotuned launch configurations) against the plain per-node launch
     path, the same tree as the secure tree with the decrypt-count reductions,
-    and the serving loop's p50/p99 request latency at offered load 0.7."""
+    and the serving loop's p50/p99 request latency at offered load 0.7 (two
+    ciphertext arrays, then one g/h-packed array)."""
     import torch
     torch.cuda.empty_cache()
     ba = argparse.Namespace(**vars(args))
@@ -1618,6 +1619,19 @@ def run_legs(args, line):
         "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "mean_ms": sv["mean_ms"], "by_size": sv["by_size"],
         "throughput_req_per_s": sv["throughput_req_per_s"], "capacity_req_per_s": sv["capacity_req_per_s"],
         "server": sv["server"], "clocks": sv["clocks"],
+    }
+    # the same serving workload over one g/h-packed ciphertext per sample (half
+    # the histogram products and decryptions; 90-bit packing slots)
+    torch.cuda.empty_cache()
+    sg = argparse.Namespace(**vars(sa))
+    sg.gh_bits, sg.pack_bits = 45, 46
+    sv = run_serving(sg, synth.CONFIGS.get("serving", {}), emit=False)
+    line["serving_gh"] = {
+        "gh_bits": sg.gh_bits, "pack_bits": sg.pack_bits, "pack_slots": sg.pack_slots or "auto",
+        "offered_load": sg.load, "requests": sg.requests, "slots": sg.slots,
+        "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "mean_ms": sv["mean_ms"], "by_size": sv["by_size"],
+        "throughput_req_per_s": sv["throughput_req_per_s"], "capacity_req_per_s": sv["capacity_req_per_s"],
+        "clocks": sv["clocks"],
     }
 
 
