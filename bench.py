@@ -1248,25 +1248,43 @@ def run_batched(args, cfg, emit=True):
               if pack_bits else None)
     split_nodes = torch.zeros(M, dtype=torch.int32, device=dev)
 
+    level_slots = {}
+
+    def cells_per_packed(nc):
+        """Cells per packed ciphertext for a level of nc cells: each packed
+        ciphertext is a serial chain of (slots - 1)(B + 1) products, so a level
+        with few cells keeps at least 1,024 of them (the rule of the serving
+        loop); --pack-slots caps it instead.  1: decrypt the cells directly."""
+        if args.pack_slots:
+            s_ = min(slots, args.pack_slots)
+        else:
+            s_ = min(slots, -(-nc // 1024))
+        s_ = max(s_, -(-nc // packed.shape[0]))   # within the packed buffer
+        level_slots[nc] = s_
+        return s_
+
     def decrypt_level(nn):
         if B:
             cells = hist_gh[:nn].reshape(-1, 2 * L)
             nc = cells.shape[0]
             out = sums[:2 * nc].view(nc, 2)
-            if pack_bits:
-                npk = -(-nc // slots)
-                P.pack(key, cells, pack_bits, out=packed[:npk])
-                P.decrypt_packed_gh(key, packed[:npk], nc, B, out=out)
+            s_ = cells_per_packed(nc) if pack_bits else 1
+            if s_ > 1:
+                npk = -(-nc // s_)
+                P.pack(key, cells, pack_bits, out=packed[:npk], slots=s_)
+                P.decrypt_packed_gh(key, packed[:npk], nc, B, out=out, slots=s_)
             else:
                 P.decrypt_gh(key, cells, B, out=out)
             return
         cells = hist[:nn].reshape(-1, 2 * L)
-        if pack_bits:
-            npk = -(-cells.shape[0] // slots)
-            P.pack(key, cells, pack_bits, out=packed[:npk])
-            P.decrypt_packed_u64(key, packed[:npk], cells.shape[0], pack_bits, out=sums[:cells.shape[0]])
+        nc = cells.shape[0]
+        s_ = cells_per_packed(nc) if pack_bits else 1
+        if s_ > 1:
+            npk = -(-nc // s_)
+            P.pack(key, cells, pack_bits, out=packed[:npk], slots=s_)
+            P.decrypt_packed_u64(key, packed[:npk], nc, pack_bits, out=sums[:nc], slots=s_)
         else:
-            P.decrypt_u64(key, cells, out=sums[:cells.shape[0]])
+            P.decrypt_u64(key, cells, out=sums[:nc])
 
     plan_gh = P.LevelPlan(key, M, F, K, maxn, gh=True) if B else None
 
@@ -1404,7 +1422,9 @@ def run_batched(args, cfg, emit=True):
                                "pack": prof["pack"],
                                "decrypt": prof["modexp_dec"] + prof["dec_crt"] + prof["unpack"]},
         "decrypted_cells_per_tree": cells,
-        "pack_bits": pack_bits, "pack_slots": slots, "splits": args.splits, "subtract": bool(args.subtract),
+        "pack_bits": pack_bits, "pack_slots": slots,
+        "pack_slots_by_level_cells": {str(k): v for k, v in sorted(level_slots.items())},
+        "splits": args.splits, "subtract": bool(args.subtract),
         "gh_bits": B, "encryptions_per_tree": M if B else 2 * M,
         "cells_decoded_per_s": cells / ((prof["modexp_dec"] + prof["dec_crt"] + prof["unpack"] + prof["pack"]) * 1e-3),
         "graph": (plan_gh if B else plan).stats(),
@@ -1603,7 +1623,8 @@ def run_legs(args, line):
     t = run_batched(st, synth.CONFIGS["batched"], emit=False)
     line["secure_tree"] = {
         "workload": t["config"]["workload"], "gh_bits": t["gh_bits"], "slot_bits": t["pack_bits"],
-        "pack_slots": t["pack_slots"], "splits": t["splits"], "subtract": t["subtract"],
+        "pack_slots": t["pack_slots"], "pack_slots_by_level_cells": t["pack_slots_by_level_cells"],
+        "splits": t["splits"], "subtract": t["subtract"],
         "encryptions_per_tree": t["encryptions_per_tree"], "tree_ms": t["tree_ms"],
         "phases_ms_per_tree": t["phases_ms_per_tree"], "ct_mults_per_s_batched": t["value"],
         "steps": st.steps, "warmup": st.warmup, "clocks": t["clocks"], "verified": t["verified"],
@@ -1690,8 +1711,9 @@ def main():
     ap.add_argument("--serve-gh-bits", type=int, default=0, help="serving leg: g/h packing bits (0 = two arrays)")
     ap.add_argument("--serve-pack-bits", type=int, default=46, help="serving leg: ciphertext packing bits")
     ap.add_argument("--pack-slots", type=int, default=0,
-                    help="serving (and its leg): cells per packed ciphertext at most (0 = the server's rule, "
-                         "fewer for requests of little histogram work; a large value = as many as fit)")
+                    help="serving and tree modes: cells per packed ciphertext at most (0 = the rule: at least "
+                         "1,024 packed ciphertexts for a request of little histogram work or a tree level; a "
+                         "large value = as many as fit)")
     args = ap.parse_args()
     cfg = synth.CONFIGS.get(args.config, {})
     if args.gh_bits is None:

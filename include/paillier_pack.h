@@ -43,6 +43,20 @@ pl_status paillier_pack(const pl_key* key, const uint32_t* d_ct, size_t count, i
 pl_status paillier_decrypt_packed_u64(const pl_key* key, const uint32_t* d_packed, size_t count, int slot_bits,
                                       uint64_t* d_m, void* stream);
 
+/* The same two calls with fewer cells per packed ciphertext: `slots` in
+ * 1 .. paillier_pack_slots(key, slot_bits), 0 = the most that fit (what the
+ * calls above use); pack and decrypt must be given the same value.  Each
+ * packed ciphertext is one chain of (slots - 1) (B + 1) products mod n^2 run
+ * one after another, so when there are too few packed ciphertexts to fill the
+ * GPU, the chain's length sets the packing time; fewer slots shorten it at
+ * the cost of ceil(count / slots) decryptions instead of
+ * ceil(count / most).  The sums do not depend on it.  PL_EINVAL for slots
+ * outside that range. */
+pl_status paillier_pack_n(const pl_key* key, const uint32_t* d_ct, size_t count, int slot_bits, int slots,
+                          uint32_t* d_packed, void* stream);
+pl_status paillier_decrypt_packed_u64_n(const pl_key* key, const uint32_t* d_packed, size_t count, int slot_bits,
+                                        int slots, uint64_t* d_m, void* stream);
+
 /* ---- g/h packing: one plaintext per sample ----------------------------------
  * Sec. III.C has one encryption per g and per h (M x 2) because Paillier
  * encrypts a single number.  A Paillier plaintext has n_bits, so both fit:
@@ -82,6 +96,11 @@ pl_status paillier_decrypt_gh(const pl_key* key, const uint32_t* d_ct, size_t co
  * holds ceil(cells / slots) ciphertexts; d_sums [cells][2] as above. */
 pl_status paillier_decrypt_packed_gh(const pl_key* key, const uint32_t* d_packed, size_t cells, int B,
                                      uint64_t* d_sums, void* stream);
+
+/* As paillier_decrypt_packed_gh for cells packed by paillier_pack_n with
+ * slot_bits = 2B and the same `slots` (0 = the most that fit). */
+pl_status paillier_decrypt_packed_gh_n(const pl_key* key, const uint32_t* d_packed, size_t cells, int B, int slots,
+                                       uint64_t* d_sums, void* stream);
 
 #ifdef __cplusplus
 }

@@ -342,40 +342,59 @@ int paillier_pack_slots(const pl_key* key, int slot_bits) {
   return (key->n_bits - 2) / slot_bits;
 }
 
-pl_status paillier_pack(const pl_key* key, const uint32_t* d_ct, size_t count, int slot_bits, uint32_t* d_packed,
-                        void* stream) {
+// cells per packed ciphertext: `slots` (1 .. the most that fit), 0 = the most that fit; -1 if invalid
+static int resolve_slots(const pl_key* key, int slot_bits, int slots) {
+  const int most = paillier_pack_slots(key, slot_bits);
+  if (most < 1 || slots < 0 || slots > most) return -1;
+  return slots ? slots : most;
+}
+
+pl_status paillier_pack_n(const pl_key* key, const uint32_t* d_ct, size_t count, int slot_bits, int slots,
+                          uint32_t* d_packed, void* stream) {
   clear_error();
   if (!key) return fail(PL_EINVAL, "key is NULL");
-  const int slots = paillier_pack_slots(key, slot_bits);
-  if (slots < 1) return fail(PL_EINVAL, "slot_bits must be 1..128");
+  if (paillier_pack_slots(key, slot_bits) < 1) return fail(PL_EINVAL, "slot_bits must be 1..128");
+  const int s = resolve_slots(key, slot_bits, slots);
+  if (s < 1) return fail(PL_EINVAL, "slots must be 0..paillier_pack_slots(key, slot_bits)");
   if (count == 0) return PL_OK;
   if (!d_ct || !d_packed) return fail(PL_EINVAL, "NULL buffer");
   if (!aligned16(d_ct) || !aligned16(d_packed)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
   if (!current_status()) return fail(PL_ECUDA, "no usable CUDA device");
-  return launch_pack(key, d_ct, count, slots, slot_bits, d_packed, static_cast<cudaStream_t>(stream));
+  return launch_pack(key, d_ct, count, s, slot_bits, d_packed, static_cast<cudaStream_t>(stream));
 }
 
-pl_status paillier_decrypt_packed_u64(const pl_key* key, const uint32_t* d_packed, size_t count, int slot_bits,
-                                      uint64_t* d_m, void* stream) {
+pl_status paillier_pack(const pl_key* key, const uint32_t* d_ct, size_t count, int slot_bits, uint32_t* d_packed,
+                        void* stream) {
+  return paillier_pack_n(key, d_ct, count, slot_bits, 0, d_packed, stream);
+}
+
+pl_status paillier_decrypt_packed_u64_n(const pl_key* key, const uint32_t* d_packed, size_t count, int slot_bits,
+                                        int slots, uint64_t* d_m, void* stream) {
   clear_error();
   if (!key) return fail(PL_EINVAL, "key is NULL");
   if (!key->priv) return fail(PL_EINVAL, "decryption needs the private key");
-  const int slots = slot_bits <= 64 ? paillier_pack_slots(key, slot_bits) : 0;
-  if (slots < 1) return fail(PL_EINVAL, "slot_bits must be 1..64");
+  if (slot_bits < 1 || slot_bits > 64) return fail(PL_EINVAL, "slot_bits must be 1..64");
+  const int sl = resolve_slots(key, slot_bits, slots);
+  if (sl < 1) return fail(PL_EINVAL, "slots must be 0..paillier_pack_slots(key, slot_bits)");
   if (count == 0) return PL_OK;
   if (!d_packed || !d_m) return fail(PL_EINVAL, "NULL buffer");
   if (!aligned16(d_packed)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
   int* st = current_status();
   if (!st) return fail(PL_ECUDA, "no usable CUDA device");
   pl_key* k = const_cast<pl_key*>(key);
-  const size_t npacked = (count + slots - 1) / slots;
+  const size_t npacked = (count + sl - 1) / sl;
   Scratch* aux = k->scratch_for_current_device(true);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   auto* plain = static_cast<uint32_t*>(aux ? aux->get(npacked * key->L * sizeof(uint32_t), s) : nullptr);
   if (!plain) return fail(PL_ENOMEM, "scratch allocation failed");
   pl_status rc = launch_decrypt(k, d_packed, npacked, plain, false, st, s);
   if (rc) return rc;
-  return launch_unpack(plain, key->L, count, slots, slot_bits, d_m, st, s);
+  return launch_unpack(plain, key->L, count, sl, slot_bits, d_m, st, s);
+}
+
+pl_status paillier_decrypt_packed_u64(const pl_key* key, const uint32_t* d_packed, size_t count, int slot_bits,
+                                      uint64_t* d_m, void* stream) {
+  return paillier_decrypt_packed_u64_n(key, d_packed, count, slot_bits, 0, d_m, stream);
 }
 
 pl_status paillier_encode_gh(const float* d_g, const float* d_h, size_t count, int B, uint64_t* d_m, void* stream) {
@@ -451,19 +470,25 @@ pl_status paillier_decrypt_gh(const pl_key* key, const uint32_t* d_ct, size_t co
   return decrypt_split(key, d_ct, count, count, 1, B, d_sums, stream);
 }
 
-pl_status paillier_decrypt_packed_gh(const pl_key* key, const uint32_t* d_packed, size_t cells, int B,
-                                     uint64_t* d_sums, void* stream) {
+pl_status paillier_decrypt_packed_gh_n(const pl_key* key, const uint32_t* d_packed, size_t cells, int B, int slots,
+                                       uint64_t* d_sums, void* stream) {
   clear_error();
   if (!key) return fail(PL_EINVAL, "key is NULL");
   if (!key->priv) return fail(PL_EINVAL, "decryption needs the private key");
   if (B < 26 || B > 64) return fail(PL_EINVAL, "B must be 26..64");
-  const int slots = paillier_pack_slots(key, 2 * B);
-  if (slots < 1) return fail(PL_EINVAL, "no slot of 2B bits fits the key");
+  if (paillier_pack_slots(key, 2 * B) < 1) return fail(PL_EINVAL, "no slot of 2B bits fits the key");
+  const int sl = resolve_slots(key, 2 * B, slots);
+  if (sl < 1) return fail(PL_EINVAL, "slots must be 0..paillier_pack_slots(key, 2B)");
   if (cells == 0) return PL_OK;
   if (!d_packed || !d_sums) return fail(PL_EINVAL, "NULL buffer");
   if (!aligned16(d_packed)) return fail(PL_EINVAL, "buffers must be 16-byte aligned");
   if (cells > (size_t)1 << 30) return fail(PL_EINVAL, "count too large");
-  return decrypt_split(key, d_packed, (cells + slots - 1) / slots, cells, slots, B, d_sums, stream);
+  return decrypt_split(key, d_packed, (cells + sl - 1) / sl, cells, sl, B, d_sums, stream);
+}
+
+pl_status paillier_decrypt_packed_gh(const pl_key* key, const uint32_t* d_packed, size_t cells, int B,
+                                     uint64_t* d_sums, void* stream) {
+  return paillier_decrypt_packed_gh_n(key, d_packed, cells, B, 0, d_sums, stream);
 }
 
 }  // extern "C"

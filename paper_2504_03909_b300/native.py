@@ -83,6 +83,9 @@ SIGNATURES.update({
     "paillier_hist_aggregate_gh": (_i, [_vp, _vp, _sz, _vp, _i, _i, _vp, _i, _vp, _vp, _vp]),
     "paillier_decrypt_gh": (_i, [_vp, _vp, _sz, _i, _vp, _vp]),
     "paillier_decrypt_packed_gh": (_i, [_vp, _vp, _sz, _i, _vp, _vp]),
+    "paillier_pack_n": (_i, [_vp, _vp, _sz, _i, _i, _vp, _vp]),
+    "paillier_decrypt_packed_u64_n": (_i, [_vp, _vp, _sz, _i, _i, _vp, _vp]),
+    "paillier_decrypt_packed_gh_n": (_i, [_vp, _vp, _sz, _i, _i, _vp, _vp]),
     "paillier_split_find": (_i, [_vp, _vp, _i, _i, _i, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp, _vp]),
     "paillier_split_apply": (_i, [_vp, _sz, _i, _vp, _i, _vp, _vp, _vp, _vp]),
     "paillier_tree_decide": (_i, [_vp, _i, _i, _sz, _vp, _vp, _i, _vp, _vp]),

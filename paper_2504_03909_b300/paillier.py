@@ -369,36 +369,47 @@ def pack_slots(key: Key, slot_bits: int) -> int:
     return lib().paillier_pack_slots(key.handle, slot_bits)
 
 
-def pack(key: Key, ct: torch.Tensor, slot_bits: int, out: torch.Tensor | None = None, stream=None):
-    """Packed ciphertexts [ceil(count / slots), 2L] of cells ct [..., 2L]."""
+def _slots(key: Key, slot_bits: int, slots: int) -> int:
+    """Cells per packed ciphertext: `slots`, or the most that fit for 0."""
+    most = pack_slots(key, slot_bits)
+    if most < 1:
+        raise ValueError(f"no packing at {slot_bits}-bit slots for this key")
+    if not 0 <= slots <= most:
+        raise ValueError(f"slots must be 0..{most} at {slot_bits}-bit slots for this key")
+    return slots or most
+
+
+def pack(key: Key, ct: torch.Tensor, slot_bits: int, out: torch.Tensor | None = None, stream=None,
+         slots: int = 0):
+    """Packed ciphertexts [ceil(count / slots), 2L] of cells ct [..., 2L]
+    (slots: cells per packed ciphertext, 0 = the most that fit)."""
     count = _rows(ct, "ct", 2 * key.L)
     pc = _ptr(ct, "ct", torch.int32)
-    slots = pack_slots(key, slot_bits)
-    if slots < 1:
-        raise ValueError(f"no packing at {slot_bits}-bit slots for this key")
-    npk = (count + slots - 1) // slots
+    s = _slots(key, slot_bits, slots)
+    npk = (count + s - 1) // s
     if out is None:
         out = torch.empty((npk, 2 * key.L), dtype=torch.int32, device=ct.device)
-    call("paillier_pack", key.handle, pc, count, slot_bits, _ptr(out, "out", torch.int32, min_numel=npk * 2 * key.L),
-         _stream(stream))
+    call("paillier_pack_n", key.handle, pc, count, slot_bits, slots,
+         _ptr(out, "out", torch.int32, min_numel=npk * 2 * key.L), _stream(stream))
     return out
 
 
-def _packed_count(key: Key, cells: int, slot_bits: int) -> int:
-    slots = pack_slots(key, slot_bits)
-    if slots < 1 or cells < 0:
-        raise ValueError(f"no packing of {cells} cells at {slot_bits}-bit slots for this key")
-    return (cells + slots - 1) // slots
+def _packed_count(key: Key, cells: int, slot_bits: int, slots: int = 0) -> int:
+    s = _slots(key, slot_bits, slots)
+    if cells < 0:
+        raise ValueError(f"no packing of {cells} cells")
+    return (cells + s - 1) // s
 
 
 def decrypt_packed_u64(key: Key, packed: torch.Tensor, count: int, slot_bits: int,
-                       out: torch.Tensor | None = None, stream=None):
-    """The `count` cell plaintexts (int64 bits of uint64) of packed ciphertexts."""
-    pp = _ptr(packed, "packed", torch.int32, min_numel=_packed_count(key, count, slot_bits) * 2 * key.L)
+                       out: torch.Tensor | None = None, stream=None, slots: int = 0):
+    """The `count` cell plaintexts (int64 bits of uint64) of packed ciphertexts
+    (slots as given to pack)."""
+    pp = _ptr(packed, "packed", torch.int32, min_numel=_packed_count(key, count, slot_bits, slots) * 2 * key.L)
     if out is None:
         out = torch.empty(count, dtype=torch.int64, device=packed.device)
     po = _ptr(out, "out", torch.int64, min_numel=count)
-    call("paillier_decrypt_packed_u64", key.handle, pp, count, slot_bits, po, _stream(stream))
+    call("paillier_decrypt_packed_u64_n", key.handle, pp, count, slot_bits, slots, po, _stream(stream))
     return out
 
 
@@ -455,13 +466,13 @@ def decrypt_gh(key: Key, ct: torch.Tensor, B: int, out: torch.Tensor | None = No
 
 
 def decrypt_packed_gh(key: Key, packed: torch.Tensor, cells: int, B: int, out: torch.Tensor | None = None,
-                      stream=None):
-    """(S_g, S_h) [cells, 2] of g/h-packed cells packed with pack(slot_bits = 2B)."""
-    pp = _ptr(packed, "packed", torch.int32, min_numel=_packed_count(key, cells, 2 * B) * 2 * key.L)
+                      stream=None, slots: int = 0):
+    """(S_g, S_h) [cells, 2] of g/h-packed cells packed with pack(slot_bits = 2B, slots)."""
+    pp = _ptr(packed, "packed", torch.int32, min_numel=_packed_count(key, cells, 2 * B, slots) * 2 * key.L)
     if out is None:
         out = torch.empty((cells, 2), dtype=torch.int64, device=packed.device)
-    call("paillier_decrypt_packed_gh", key.handle, pp, cells, B, _ptr(out, "out", torch.int64, min_numel=2 * cells),
-         _stream(stream))
+    call("paillier_decrypt_packed_gh_n", key.handle, pp, cells, B, slots,
+         _ptr(out, "out", torch.int64, min_numel=2 * cells), _stream(stream))
     return out
 
 

@@ -40,6 +40,36 @@ def test_packed_decrypt_equals_per_cell(cells, B):
         assert got.cpu().numpy().tolist() == cells["m"][:c].tolist()
 
 
+@pytest.mark.parametrize("slots", [1, 2, 7])
+def test_fewer_slots_give_the_same_plaintexts(cells, slots):
+    """pack_n / decrypt_packed_u64_n with fewer cells per packed ciphertext
+    (shorter Horner chains): the same per-cell plaintexts, and a packed
+    ciphertext that decrypts to the Horner sum of its `slots` cells."""
+    key, B, count = cells["key"], 46, cells["count"]
+    for c in (count, slots + 1, 1):
+        packed = P.pack(key, cells["ct"][:c], B, slots=slots)
+        got = P.decrypt_packed_u64(key, packed, c, B, slots=slots)
+        P.sync()
+        assert packed.shape[0] == -(-c // slots)
+        assert got.cpu().numpy().tolist() == cells["m"][:c].tolist()
+    pt = P.decrypt(key, P.pack(key, cells["ct"][:slots], B, slots=slots))
+    P.sync()
+    assert synth.limbs_to_ints(P.from_limb_tensor(pt))[0] == sum(int(cells["m"][j]) << (B * j) for j in range(slots))
+
+
+def test_slots_out_of_range_are_refused(cells):
+    key, B = cells["key"], 46
+    most = P.pack_slots(key, B)
+    for bad in (-1, most + 1):
+        with pytest.raises(ValueError):
+            P.pack(key, cells["ct"][:4], B, slots=bad)
+        # and by the library itself, before any launch
+        with pytest.raises(native.PaillierError):
+            native.call("paillier_pack_n", key.handle, cells["ct"].data_ptr(), 4, B, bad,
+                        cells["ct"].data_ptr(), None)
+    assert P.pack(key, cells["ct"][:4], B, slots=most).shape[0] == 1
+
+
 def test_packed_plaintext_is_the_horner_sum(cells):
     # the packed ciphertext decrypts (full width) to sum_j m_j 2^(B j)
     key, B = cells["key"], 48
@@ -124,6 +154,12 @@ def test_gh_histogram_cells_and_sums(gh_case):
         P.sync()
         assert packed.shape[0] == -(-cnum // P.pack_slots(key, 2 * B))
         assert s2.cpu().numpy().tolist() == want.reshape(-1, 2)[:cnum].tolist()
+        # fewer cells per packed ciphertext
+        packed = P.pack(key, flat[:cnum], 2 * B, slots=3)
+        s3 = P.decrypt_packed_gh(key, packed, cnum, B, slots=3)
+        P.sync()
+        assert packed.shape[0] == -(-cnum // 3)
+        assert s3.cpu().numpy().tolist() == want.reshape(-1, 2)[:cnum].tolist()
 
 
 def test_gh_ranges(gh_case):
