@@ -1510,7 +1510,7 @@ def run_serving(args, cfg, emit=True):
             dec = cells * dec_imad(rq["nb"], w)
         return ngh * rq["M"] * rq["F"] * mont_imad(2 * L) + dec
 
-    srv = P.Server(slots=args.slots, hbm_budget=budget, promote_ms=args.promote_ms)
+    srv = P.Server(slots=args.slots, hbm_budget=budget, promote_ms=args.promote_ms, chunk_imad=args.chunk_imad)
     # warm-up, then the closed-loop capacity in work units (every slot busy)
     warm = [draw() for _ in range(max(4 * args.slots, 32))]
     for rq in warm[:args.slots]:
@@ -1558,7 +1558,7 @@ def run_serving(args, cfg, emit=True):
                                "M log-uniform [1e3, 1e6], F uniform [8, 64], K uniform {64..256 step 32}, "
                                "2048/3072-bit keys p = 0.5, resident ciphertexts", "slots": args.slots,
                    "hbm_budget_bytes": budget, "offered_load": args.load, "requests": args.requests,
-                   "promote_ms": args.promote_ms,
+                   "promote_ms": args.promote_ms, "chunk_imad": args.chunk_imad,
                    "pack_bits": args.pack_bits, "gh_bits": args.gh_bits,
                    "pack_slots": args.pack_slots or "auto"},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -1710,6 +1710,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=300, help="serving leg of the level run: timed requests")
     ap.add_argument("--serve-gh-bits", type=int, default=0, help="serving leg: g/h packing bits (0 = two arrays)")
     ap.add_argument("--serve-pack-bits", type=int, default=46, help="serving leg: ciphertext packing bits")
+    ap.add_argument("--chunk-imad", type=float, default=None,
+                    help="serving: modelled multiply-adds per launch (the library's default when omitted)")
     ap.add_argument("--pack-slots", type=int, default=0,
                     help="serving and tree modes: cells per packed ciphertext at most (0 = the rule: at least "
                          "1,024 packed ciphertexts for a request of little histogram work or a tree level; a "
