@@ -1130,6 +1130,20 @@ def run_ours(args, cfg):
         "dram_note": "ncu capture of the segmented product on 2 x 65,536 x 16 contributions: DRAM reads "
                      "about one pass over the ciphertexts, 3.6 GB/s, 0.05 % of peak: the pass is ALU-bound",
     }
+    # the CRT decryption of the level's cells: c^(x - 1) mod x^2 per half, the
+    # schedule's multiply-adds as executed and at the CIOS cost per product
+    lanes_dec, w_dec = P.get_config(key, native.OP_DECRYPT)
+    t_dec = prof["modexp_dec"][0] / max(1, prof["modexp_dec"][1])
+    ndec = F * K * 2
+    dec_exec = ndec * dec_imad(n_bits, w_dec, p, q, lanes_dec)
+    dec_cios = ndec * dec_imad(n_bits, w_dec, p, q)
+    decrypt_roofline = {
+        "bound": "alu", "kernel": "k_modexp (decryption: c^(x - 1) mod x^2 per CRT half)",
+        "achieved": dec_exec / (t_dec * 1e-3) / 1e12, "peak": peak / 1e12, "unit": "TIMAD/s",
+        "frac": dec_exec / (t_dec * 1e-3) / peak, "frac_cios_count": dec_cios / (t_dec * 1e-3) / peak,
+        "launch_ms": t_dec, "imad_per_launch": dec_exec, "imad_per_launch_cios_count": dec_cios,
+        "cells": ndec, "lanes": lanes_dec, "window": w_dec,
+    }
     line = {
         "metric": METRIC,
         "value": value,
@@ -1178,6 +1192,7 @@ def run_ours(args, cfg):
             "first_stage": first_stage,
         },
         "aggregate_roofline": aggregate_roofline,
+        "decrypt_roofline": decrypt_roofline,
         "clocks": clk.summary(),
         "e2e": {"value": whole_job_rate(units, e2e_steps, world, e2e_s), "unit": "enc/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
