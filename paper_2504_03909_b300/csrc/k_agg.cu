@@ -623,12 +623,18 @@ pl_status launch_pack(const pl_key* key, const uint32_t* ct, size_t count, int s
   if (!npacked) return PL_OK;
   const int NL = 2 * key->L;
   // each packed ciphertext is one long chain of products: with few of them,
-  // twice the lanes per instance (where that kernel exists) shortens the chain
+  // twice the lanes per instance (where that kernel exists) shortens the
+  // chain; at 2048-bit a 32-lane packing kernel (4 limbs per lane, packing
+  // only) takes the 16-lane calls that still leave the GPU half empty
+  // (measured: 13.5 against 18.6 ms for 500 packed ciphertexts, 25.5 against
+  // 27.8 ms for 1,776)
   int T = key->agg_cfg.T;
   if (agg_supported(NL, 2 * T) && double_lanes_pays(npacked, T)) T *= 2;
+  if (NL == 128 && T == 16 && double_lanes_pays(npacked, T)) T = 32;
 #define PL_CASE(LL, TT) \
   if (NL == LL && T == TT) return run_pack<LL / TT, TT>(key->n2c, ct, count, slots, B, packed, npacked, s);
   PL_N2_CASES(PL_CASE)
+  PL_CASE(128, 32)
 #undef PL_CASE
   return fail(PL_EINVAL, "no mod n^2 kernel for this (limbs, lanes) pair");
 }
